@@ -1,0 +1,222 @@
+"""CPU FP64 oracle for the modified Hermite integrators (Dittmann 2020).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The product library
+(``paper_2006_02501_gb300``) never imports, links or runs it, and the two share
+no code: the oracle is plain C (``mh_oracle.c``, compiled with gcc and
+``-ffp-contract=off``) plus the exact-rational algebra in ``coeffs.py``.
+
+Array conventions (all float64, C-contiguous):
+  m        (N,)
+  x, v     (N, 3)
+  derivs   (N, 2p, 3)    a^(0) .. a^(2p-1) of each particle
+  traj     (N, P+1, 3)   x, v, a, a-dot, ... fed to a direct-summation evaluation
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mh_oracle.c")
+_LIB = os.path.join(_HERE, "libmh_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (plain -O2, no FMA contraction, OpenMP over i)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+               "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def _lib_handle():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            i, d = ctypes.c_int, ctypes.c_double
+            lib.orc_beta.argtypes = [i]
+            lib.orc_beta.restype = d
+            lib.orc_corrector_weights.argtypes = [i, i, _D, _D]
+            lib.orc_hermite_interp.argtypes = [i, d, _D, _D, i, _D]
+            lib.orc_pair_derivs.argtypes = [i, _D, d, d, _D]
+            lib.orc_evaluate.argtypes = [i, i, _D, _D, d, d, i, i, _D]
+            lib.orc_initialise.argtypes = [i, i, _D, _D, _D, d, d, _D]
+            lib.orc_predict.argtypes = [i, i, d, _D, _D, _D, _D, _D, _D]
+            lib.orc_correct.argtypes = [i, i, i, d, _D, _D, _D, _D, _D, _D]
+            lib.orc_step.argtypes = [i, i, i, i, d, _D, d, d, _D, _D, _D]
+            lib.orc_run.argtypes = [i, i, i, i, d, i, _D, d, d, _D, _D, _D]
+            lib.orc_energy.argtypes = [i, _D, _D, _D, d, d]
+            lib.orc_energy.restype = d
+            lib.orc_ecc.argtypes = [i, _D, _D, _D, d, i, _D]
+            lib.orc_timestep_H.argtypes = [i, _D, _D, d, d]
+            lib.orc_timestep_H.restype = d
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def order_to_p(order: int) -> int:
+    """Order 2(p+1) -> p (Section 2: p derivatives of a give order 2(p+1))."""
+    if order not in (4, 6, 8):
+        raise ValueError("order must be 4, 6 or 8")
+    return order // 2 - 1
+
+
+# --------------------------------------------------------------------------- #
+# Hermite algebra (Section 2)
+# --------------------------------------------------------------------------- #
+
+def beta(p: int) -> float:
+    return _lib_handle().orc_beta(p)
+
+
+def corrector_weights(p: int, modified: bool = True):
+    """(cv, cx) on the F+- vectors, from solving the Eq. 8 system in double."""
+    cv = np.zeros(8)
+    cx = np.zeros(8)
+    _lib_handle().orc_corrector_weights(p, 0 if modified else 1, _p(cv), _p(cx))
+    return cv[:p + 1].copy(), cx[:p + 2].copy()
+
+
+def hermite_interp(p: int, dt: float, f0, f1, nout: int) -> np.ndarray:
+    """f^(0..nout-1) at the end of the step from f^(0..p) at both ends."""
+    f0, f1 = _f64(f0).reshape(p + 1, 3), _f64(f1).reshape(p + 1, 3)
+    out = np.zeros((nout, 3))
+    _lib_handle().orc_hermite_interp(p, dt, _p(f0), _p(f1), nout, _p(out))
+    return out
+
+
+# --------------------------------------------------------------------------- #
+# pair derivatives and direct summation (Section 3)
+# --------------------------------------------------------------------------- #
+
+def pair_derivs(P: int, r, eps: float, Gm: float) -> np.ndarray:
+    """Time derivatives 0..P of G m r (r.r+eps^2)^(-3/2); r: (P+1, 3) relative
+    trajectory derivatives."""
+    r = _f64(r).reshape(P + 1, 3)
+    out = np.zeros((P + 1, 3))
+    _lib_handle().orc_pair_derivs(P, _p(r), eps * eps, Gm, _p(out))
+    return out
+
+
+def evaluate(m, traj, eps: float, G: float = 1.0, i0: int = 0, i1: int | None = None) -> np.ndarray:
+    """Direct-summation derivatives a^(0..P) for particles i0..i1-1."""
+    m = _f64(m)
+    traj = _f64(traj)
+    N, K, _ = traj.shape
+    i1 = N if i1 is None else i1
+    out = np.zeros((i1 - i0, K, 3))
+    _lib_handle().orc_evaluate(N, K - 1, _p(m), _p(traj), eps, G, i0, i1, _p(out))
+    return out
+
+
+def initialise(order: int, m, x, v, eps: float, G: float = 1.0) -> np.ndarray:
+    """a^(0..2p-1) at t = 0 by explicit pair derivatives (Section 3 intro)."""
+    p = order_to_p(order)
+    m, x, v = _f64(m), _f64(x), _f64(v)
+    N = m.shape[0]
+    d = np.zeros((N, 2 * p, 3))
+    _lib_handle().orc_initialise(N, p, _p(m), _p(x), _p(v), eps, G, _p(d))
+    return d
+
+
+def predict(order: int, dt: float, x, v, derivs):
+    p = order_to_p(order)
+    x, v, derivs = _f64(x), _f64(v), _f64(derivs)
+    N = x.shape[0]
+    xp, vp = np.zeros((N, 3)), np.zeros((N, 3))
+    ap = np.zeros((N, max(p - 1, 1), 3))
+    _lib_handle().orc_predict(N, p, dt, _p(x), _p(v), _p(derivs), _p(xp), _p(vp), _p(ap))
+    return xp, vp, ap[:, :max(p - 1, 0)]
+
+
+def correct(order: int, dt: float, x0, v0, d0, d1, modified: bool = True):
+    """Corrector (Eqs. 5-7): d0, d1 are (N, p+1, 3) derivative stacks at t, t+dt."""
+    p = order_to_p(order)
+    x0, v0, d0, d1 = _f64(x0), _f64(v0), _f64(d0), _f64(d1)
+    N = x0.shape[0]
+    x1, v1 = np.zeros((N, 3)), np.zeros((N, 3))
+    _lib_handle().orc_correct(N, p, 0 if modified else 1, dt, _p(x0), _p(v0), _p(d0), _p(d1),
+                              _p(x1), _p(v1))
+    return x1, v1
+
+
+class State:
+    """A simulation state held by the oracle: x, v, derivs (a^(0..2p-1)), m."""
+
+    def __init__(self, order: int, m, x, v, eps: float, G: float = 1.0, derivs=None,
+                 modified: bool = True):
+        self.order = order
+        self.p = order_to_p(order)
+        self.m = _f64(m).copy()
+        self.x = _f64(x).copy()
+        self.v = _f64(v).copy()
+        self.eps = float(eps)
+        self.G = float(G)
+        self.modified = modified
+        self.t = 0.0
+        self.derivs = initialise(order, self.m, self.x, self.v, eps, G) if derivs is None \
+            else _f64(derivs).copy()
+
+    @property
+    def N(self) -> int:
+        return self.m.shape[0]
+
+    def step(self, dt: float, n_iter: int, nsteps: int = 1) -> None:
+        """nsteps shared P(EC)^n steps of constant dt (negative dt runs backward)."""
+        _lib_handle().orc_run(self.N, self.p, 0 if self.modified else 1, n_iter, dt, nsteps,
+                              _p(self.m), self.eps, self.G, _p(self.x), _p(self.v),
+                              _p(self.derivs))
+        self.t += dt * nsteps
+
+    def energy(self) -> float:
+        return energy(self.m, self.x, self.v, self.eps, self.G)
+
+    def ecc(self, central: int = 0) -> np.ndarray:
+        return ecc(self.m, self.x, self.v, self.G, central)
+
+    def copy(self) -> "State":
+        s = State.__new__(State)
+        s.__dict__.update({k: (v.copy() if isinstance(v, np.ndarray) else v)
+                           for k, v in self.__dict__.items()})
+        return s
+
+
+def energy(m, x, v, eps: float, G: float = 1.0) -> float:
+    m, x, v = _f64(m), _f64(x), _f64(v)
+    return _lib_handle().orc_energy(m.shape[0], _p(m), _p(x), _p(v), eps, G)
+
+
+def ecc(m, x, v, G: float = 1.0, central: int = 0) -> np.ndarray:
+    m, x, v = _f64(m), _f64(x), _f64(v)
+    e = np.zeros_like(x)
+    _lib_handle().orc_ecc(m.shape[0], _p(m), _p(x), _p(v), G, central, _p(e))
+    return e
+
+
+def timestep_H(m, x, eps: float, eta: float) -> float:
+    m, x = _f64(m), _f64(x)
+    return _lib_handle().orc_timestep_H(m.shape[0], _p(m), _p(x), eps, eta)
