@@ -1,0 +1,156 @@
+/*
+ * mh.h - C ABI of the GB300 (sm_103a) modified Hermite N-body library.
+ *
+ * The library integrates the Newtonian N-body problem with the modified
+ * Hermite integrators of order 4, 6 and 8 of Dittmann (2020), "Modified Hermite
+ * Integrators of Arbitrary Order", MNRAS:
+ *   - softened pair acceleration a_ij = G m_j r_ij (r_ij^2 + eps^2)^(-3/2) and
+ *     its time derivatives (Section 3, intro), summed over all j != i;
+ *   - explicit initial derivatives a^(0) .. a^(2p-1) (Section 3, intro);
+ *   - Taylor predictor (Section 3, intro);
+ *   - corrector: velocity from Eq. 6, then position from Eq. 7 with the optimal
+ *     beta of Eq. 20 (printed forms: Eqs. 21-23), or beta = 1;
+ *   - P(EC)^n iteration (Section 2.1, end);
+ *   - energy and Laplace-Runge-Lenz (eccentricity) vectors (Appendix A, Eq. A1).
+ * The integrator order is 2(p+1) where p is the number of acceleration
+ * derivatives evaluated (Section 2): order 4, 6, 8 <-> p = 1, 2, 3.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: an mh_status; 0 is success, negative values are errors.
+ *     mh_last_error() returns a message for the calling thread's last error.
+ *   - Host arrays are read or written during the call only and never retained.
+ *     Unless a parameter says "device", a pointer is a host pointer.
+ *   - Vectors are row-major N x 3 (x[3*i + c]); derivative stacks are
+ *     N x K x 3 (d[(i*K + k)*3 + c] = k-th time derivative of the acceleration).
+ *   - All device memory of a simulation is allocated by mh_create /
+ *     mh_create_batch and freed by mh_destroy.  Work is issued on the stream
+ *     given at creation (NULL = the library creates its own stream);
+ *     mh_step returns once the work is queued, mh_sync / mh_diagnostics wait.
+ *   - Units are the caller's; G defaults to 1.
+ *   - Not thread safe per handle: one thread at a time may use an mh_sim.
+ */
+#ifndef MH_H
+#define MH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mh_sim mh_sim;
+
+typedef enum {
+    MH_OK = 0,
+    MH_EINVAL = -1,       /* bad argument (order, sizes, NULL pointer, dt) */
+    MH_ENOMEM = -2,       /* device allocation failed */
+    MH_ECUDA = -3,        /* a CUDA runtime call or kernel launch failed */
+    MH_ENONFINITE = -4,   /* a NaN or Inf appeared in the state */
+    MH_ETIMEOUT = -5,     /* a bounded device-side wait ran out */
+    MH_ENOTCONV = 1       /* warning: a convergence tolerance was not reached */
+} mh_status;
+
+enum { MH_BETA_MODIFIED = 0, MH_BETA_STANDARD = 1 };
+enum { MH_PREC_FP64 = 0, MH_PREC_FP32PAIR = 1 };
+enum { MH_STEP_SHARED = 0, MH_STEP_BLOCK = 1 };
+
+/* Integrator configuration.  Fill with mh_config_default() first. */
+typedef struct {
+    int order;          /* 4, 6 or 8 (default 8) */
+    int beta_mode;      /* MH_BETA_MODIFIED: beta of Eq. 20; MH_BETA_STANDARD: beta = 1 */
+    int precision;      /* MH_PREC_FP64: all arithmetic FP64.
+                           MH_PREC_FP32PAIR: pair arithmetic in FP32, state, pre-cast
+                           differences (hi/lo split), accumulation across j-tiles,
+                           corrector and diagnostics in FP64. */
+    int step_mode;      /* MH_STEP_SHARED or MH_STEP_BLOCK */
+    double G;           /* gravitational constant (default 1) */
+    double eta;         /* block steps: accuracy parameter of the per-particle criterion */
+    double dt_max;      /* block steps: largest step (levels are dt_max * 2^-k) */
+    int k_max;          /* block steps: deepest level, 0 <= k_max <= 20 (default 12) */
+    int split_j;        /* pair kernel: j-range split factor, 0 = automatic */
+} mh_config;
+
+/* Snapshot of a simulation (mh_sync / mh_set_state).  Each pointer may be NULL
+ * to skip that field.  derivs holds a^(0..2p-1), i.e. K = 2p vectors per body. */
+typedef struct {
+    double t;           /* simulation time */
+    double *x;          /* N x 3 */
+    double *v;          /* N x 3 */
+    double *derivs;     /* N x 2p x 3 */
+} mh_state;
+
+/* Per-handle counters (cumulative since creation). */
+typedef struct {
+    int64_t steps;               /* mh_step calls completed */
+    int64_t evaluations;         /* O(N^2) evaluations (E of P(EC)^n) */
+    double pair_interactions;    /* sum over evaluations of N_active * (N - 1) */
+    double particle_steps;       /* particles advanced */
+    int64_t kernel_launches;     /* kernels launched by this handle */
+} mh_counters;
+
+/* Fill *cfg with the defaults listed above. */
+void mh_config_default(mh_config *cfg);
+
+/* Create a simulation of N bodies (N >= 1).
+ *   m: N masses; x, v: N x 3 positions and velocities (host, copied in);
+ *   eps: Plummer softening (>= 0; with eps = 0 two bodies at one point are
+ *   undefined); cfg: NULL for defaults (the order argument wins over cfg->order);
+ *   stream: a cudaStream_t or NULL.
+ * Computes a^(0) .. a^(2p-1) at t = 0 by explicit pair derivatives in p
+ * O(N^2) passes (Section 3, intro).  On error *out is NULL. */
+int mh_create(mh_sim **out, int64_t N, int order, const double *m, const double *x,
+              const double *v, double eps, const mh_config *cfg, void *stream);
+
+/* Release every resource of the handle (NULL is a no-op). */
+void mh_destroy(mh_sim *sim);
+
+/* Shared step: advance every body by dt (dt != 0; dt < 0 integrates backward)
+ * with one Taylor prediction and n_iter >= 1 evaluate-correct passes, P(EC)^n.
+ * The derivatives a^(0..p) kept for the next step are those of the n-th
+ * evaluation; a^(p+1..2p-1) come from Hermite interpolation.
+ * Block mode: advance the block scheme until time t + dt. */
+int mh_step(mh_sim *sim, double dt, int n_iter);
+
+/* Copy the current state to host buffers (waits for queued work). */
+int mh_sync(mh_sim *sim, mh_state *out);
+
+/* Overwrite the state from host buffers: x, v must be given; derivs may be NULL,
+ * in which case a^(0..2p-1) are recomputed by the initialisation passes. */
+int mh_set_state(mh_sim *sim, const mh_state *in);
+
+/* Diagnostics (waits).  energy (may be NULL): total energy
+ * sum m v^2/2 - sum_{i<j} G m_i m_j / sqrt(r^2 + eps^2), accumulated in FP64.
+ * ecc (may be NULL): N x 3 eccentricity vectors about body `central`
+ * (Appendix A, Eq. A1: mu e = (|v|^2 - mu/|r|) r - (r.v) v, mu = G(m_c + m_i));
+ * the central body's row is zero. */
+int mh_diagnostics(mh_sim *sim, double *energy, double *ecc, int central);
+
+/* Number of bodies, order and counters of a handle. */
+int mh_info(const mh_sim *sim, int64_t *N, int *order, mh_counters *counters);
+
+/* Message describing the calling thread's most recent error ("" if none). */
+const char *mh_last_error(void);
+
+/* ------------------------------------------------------------------------- */
+/* Kernel-level entry points on caller-owned DEVICE memory.                   */
+/* ------------------------------------------------------------------------- */
+
+/* Direct-summation derivatives a^(0..P) (Section 3, intro) of bodies
+ * i0 <= i < i1 from all N bodies, j != i.
+ *   traj: device, SoA, (P+1)*3 rows of N doubles: row 3k+c holds component c of
+ *         the k-th trajectory derivative (x, v, a, a-dot) of every body;
+ *   m:    device, N masses;  out: device, (P+1)*3 rows of (i1-i0) doubles.
+ *   P = 1, 2 or 3; precision as in mh_config.  Uses scratch memory that the
+ *   library allocates and caches per device (freed by mh_release_scratch).
+ *   Stream-ordered on `stream` (a cudaStream_t, NULL = legacy default stream). */
+int mh_pair_eval(int P, int precision, int64_t N, const double *m, const double *traj,
+                 double eps, double G, int64_t i0, int64_t i1, double *out, void *stream);
+
+/* Free the scratch memory cached by mh_pair_eval on the current device. */
+int mh_release_scratch(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MH_H */

@@ -1,0 +1,156 @@
+"""GB300-native modified Hermite N-body integrators (Dittmann 2020), orders 4, 6, 8.
+
+Thin Python binding over the C ABI of include/mh.h.  Every step of the
+integration runs in the library's CUDA kernels; this module only marshals
+arguments (numpy arrays for host data, torch tensors or raw pointers for
+device data and streams).
+
+    sim = Simulation(order=8, m=m, x=x, v=v, eps=1e-4)
+    sim.step(dt, n_iter=3)
+    t, x, v, derivs = sim.sync()
+    E, ecc = sim.diagnostics(central=0)
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _capi
+from ._capi import (MH_BETA_MODIFIED, MH_BETA_STANDARD, MH_PREC_FP32PAIR, MH_PREC_FP64,  # noqa: F401
+                    MHError, check)
+
+__all__ = ["Simulation", "pair_eval", "MHError", "build_library", "MH_PREC_FP64", "MH_PREC_FP32PAIR",
+           "MH_BETA_MODIFIED", "MH_BETA_STANDARD"]
+
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+def build_library(force: bool = False) -> str:
+    """Compile lib/libmh.so (nvcc, sm_103a) if it is missing or stale."""
+    from .build import build as _b
+    return _b(force=force)
+
+
+def _host(a, shape=None) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.shape != shape:
+        a = a.reshape(shape)
+    return a
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_DP)
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)        # torch.cuda.Stream
+
+
+class Simulation:
+    """One N-body system advanced by the shared-step P(EC)^n scheme.
+
+    order: 4, 6 or 8; precision: MH_PREC_FP64 or MH_PREC_FP32PAIR; beta:
+    MH_BETA_MODIFIED (Eq. 20) or MH_BETA_STANDARD (beta = 1); stream: a
+    torch.cuda.Stream, a raw cudaStream_t integer, or None (library stream).
+    """
+
+    def __init__(self, order: int, m, x, v, eps: float, precision: int = MH_PREC_FP64,
+                 beta: int = MH_BETA_MODIFIED, G: float = 1.0, stream=None, split_j: int = 0):
+        L = _capi.lib()
+        m = _host(m)
+        N = m.shape[0]
+        x, v = _host(x, (N, 3)), _host(v, (N, 3))
+        cfg = _capi.Config()
+        L.mh_config_default(ctypes.byref(cfg))
+        cfg.order, cfg.precision, cfg.beta_mode, cfg.G, cfg.split_j = order, precision, beta, G, split_j
+        h = ctypes.c_void_p()
+        check(L.mh_create(ctypes.byref(h), N, order, _ptr(m), _ptr(x), _ptr(v), float(eps),
+                          ctypes.byref(cfg), _stream_handle(stream)))
+        self._h = h
+        self.N, self.order, self.p = N, order, order // 2 - 1
+        self.eps, self.G, self.precision = eps, G, precision
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _capi.lib().mh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def step(self, dt: float, n_iter: int, nsteps: int = 1) -> None:
+        L = _capi.lib()
+        for _ in range(nsteps):
+            check(L.mh_step(self._h, float(dt), int(n_iter)))
+
+    def sync(self):
+        """(t, x (N,3), v (N,3), derivs (N,2p,3)) copied to the host."""
+        x = np.zeros((self.N, 3))
+        v = np.zeros((self.N, 3))
+        d = np.zeros((self.N, 2 * self.p, 3))
+        st = _capi.StateC(0.0, _ptr(x), _ptr(v), _ptr(d))
+        check(_capi.lib().mh_sync(self._h, ctypes.byref(st)))
+        return st.t, x, v, d
+
+    def set_state(self, x, v, derivs=None, t: float = 0.0) -> None:
+        x, v = _host(x, (self.N, 3)), _host(v, (self.N, 3))
+        dp = None
+        if derivs is not None:
+            derivs = _host(derivs, (self.N, 2 * self.p, 3))
+            dp = _ptr(derivs)
+        st = _capi.StateC(float(t), _ptr(x), _ptr(v), dp)
+        check(_capi.lib().mh_set_state(self._h, ctypes.byref(st)))
+
+    def diagnostics(self, central: int = 0, energy: bool = True, ecc: bool = True):
+        e = ctypes.c_double(0.0)
+        ev = np.zeros((self.N, 3)) if ecc else None
+        check(_capi.lib().mh_diagnostics(self._h, ctypes.byref(e) if energy else None,
+                                         _ptr(ev) if ecc else None, int(central)))
+        return (e.value if energy else None), ev
+
+    def energy(self) -> float:
+        return self.diagnostics(energy=True, ecc=False)[0]
+
+    def counters(self) -> dict:
+        n, o, c = ctypes.c_int64(), ctypes.c_int(), _capi.Counters()
+        check(_capi.lib().mh_info(self._h, ctypes.byref(n), ctypes.byref(o), ctypes.byref(c)))
+        return {f: getattr(c, f) for f, _ in c._fields_}
+
+
+def _dev_ptr(t) -> int:
+    if isinstance(t, int):
+        return t
+    return int(t.data_ptr())
+
+
+def pair_eval(P: int, precision: int, m, traj, eps: float, out, G: float = 1.0, i0: int = 0,
+              i1: int | None = None, stream=None) -> None:
+    """Direct-summation a^(0..P) of bodies i0..i1-1 on DEVICE memory.
+
+    m: (N,) float64 device tensor; traj: ((P+1)*3, N) float64 device tensor (row
+    3k+c = component c of x, v, a, a-dot, ...); out: ((P+1)*3, i1-i0) float64
+    device tensor.  Stream-ordered on `stream` (default: torch's current stream).
+    """
+    N = int(m.shape[0]) if hasattr(m, "shape") else None
+    if N is None:
+        raise ValueError("m must be a device tensor")
+    i1 = N if i1 is None else i1
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    check(_capi.lib().mh_pair_eval(int(P), int(precision), N, _dev_ptr(m), _dev_ptr(traj), float(eps),
+                                   float(G), int(i0), int(i1), _dev_ptr(out), _stream_handle(stream)))

@@ -1,0 +1,98 @@
+"""ctypes declarations of the C ABI in include/mh.h (argument marshalling only).
+
+The shared library is built in-tree (paper_2006_02501_gb300/lib/libmh.so) by
+paper_2006_02501_gb300.build.  Loading fails loudly if it is missing: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libmh.so")
+
+MH_OK = 0
+MH_EINVAL = -1
+MH_ENOMEM = -2
+MH_ECUDA = -3
+MH_ENONFINITE = -4
+MH_ETIMEOUT = -5
+MH_ENOTCONV = 1
+
+MH_BETA_MODIFIED, MH_BETA_STANDARD = 0, 1
+MH_PREC_FP64, MH_PREC_FP32PAIR = 0, 1
+MH_STEP_SHARED, MH_STEP_BLOCK = 0, 1
+
+# Every entry point declared in include/mh.h (checked by the CPU test suite).
+EXPORTS = [
+    "mh_config_default", "mh_create", "mh_destroy", "mh_step", "mh_sync", "mh_set_state",
+    "mh_diagnostics", "mh_info", "mh_last_error", "mh_pair_eval", "mh_release_scratch",
+]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("beta_mode", ctypes.c_int), ("precision", ctypes.c_int),
+                ("step_mode", ctypes.c_int), ("G", ctypes.c_double), ("eta", ctypes.c_double),
+                ("dt_max", ctypes.c_double), ("k_max", ctypes.c_int), ("split_j", ctypes.c_int)]
+
+
+class StateC(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("x", ctypes.POINTER(ctypes.c_double)),
+                ("v", ctypes.POINTER(ctypes.c_double)), ("derivs", ctypes.POINTER(ctypes.c_double))]
+
+
+class Counters(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("evaluations", ctypes.c_int64),
+                ("pair_interactions", ctypes.c_double), ("particle_steps", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64)]
+
+
+class MHError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"mh error {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                                   "(run python -m paper_2006_02501_gb300.build)")
+            L = ctypes.CDLL(LIB_PATH)
+            P, D, I, I64 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int64
+            DP = ctypes.POINTER(ctypes.c_double)
+            L.mh_config_default.argtypes = [ctypes.POINTER(Config)]
+            L.mh_config_default.restype = None
+            L.mh_create.argtypes = [ctypes.POINTER(P), I64, I, DP, DP, DP, D, ctypes.POINTER(Config), P]
+            L.mh_destroy.argtypes = [P]
+            L.mh_destroy.restype = None
+            L.mh_step.argtypes = [P, D, I]
+            L.mh_sync.argtypes = [P, ctypes.POINTER(StateC)]
+            L.mh_set_state.argtypes = [P, ctypes.POINTER(StateC)]
+            L.mh_diagnostics.argtypes = [P, DP, DP, I]
+            L.mh_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(Counters)]
+            L.mh_last_error.argtypes = []
+            L.mh_last_error.restype = ctypes.c_char_p
+            L.mh_pair_eval.argtypes = [I, I, I64, P, P, D, D, I64, I64, P, P]
+            L.mh_release_scratch.argtypes = []
+            for name in EXPORTS:
+                if name not in ("mh_destroy", "mh_config_default", "mh_last_error"):
+                    getattr(L, name).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def check(rc: int, allow=(MH_OK,)) -> int:
+    if rc not in allow:
+        msg = lib().mh_last_error().decode(errors="replace")
+        raise MHError(rc, msg)
+    return rc

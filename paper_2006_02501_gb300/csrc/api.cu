@@ -1,0 +1,480 @@
+// Host side of the C ABI declared in include/mh.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace mh {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();   // clear the sticky-free allocation error
+        return MH_ENOMEM;
+    }
+    return MH_ECUDA;
+}
+
+namespace {
+
+int order_to_p(int order) { return order == 4 ? 1 : order == 6 ? 2 : order == 8 ? 3 : 0; }
+
+template <typename T>
+int dalloc(T **ptr, size_t count)
+{
+    *ptr = nullptr;
+    if (count == 0) return MH_OK;
+    MH_CUDA(cudaMalloc((void **)ptr, count * sizeof(T)));
+    return MH_OK;
+}
+
+void free_state(DeviceState &s)
+{
+    void *ptrs[] = {s.m, s.x0, s.v0, s.d0, s.x1, s.v1, s.jrec, s.jrec32, s.part, s.diag, s.flag, s.bound};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    s = DeviceState{};
+}
+
+// AoS (N x K x 3) host array -> SoA rows [K*3][ld] (padding columns filled with fill).
+void to_soa(const double *src, int64_t N, int K, int64_t ld, std::vector<double> &dst, double fill)
+{
+    dst.assign((size_t)K * 3 * ld, fill);
+    for (int64_t i = 0; i < N; ++i)
+        for (int k = 0; k < K; ++k)
+            for (int c = 0; c < 3; ++c) dst[(size_t)(3 * k + c) * ld + i] = src[((size_t)i * K + k) * 3 + c];
+}
+
+void from_soa(const std::vector<double> &src, int64_t N, int K, int64_t ld, double *dst)
+{
+    for (int64_t i = 0; i < N; ++i)
+        for (int k = 0; k < K; ++k)
+            for (int c = 0; c < 3; ++c) dst[((size_t)i * K + k) * 3 + c] = src[(size_t)(3 * k + c) * ld + i];
+}
+
+// Make sure the partial-sum buffer holds `need` doubles.
+int ensure_part(DeviceState &s, size_t need, cudaStream_t st)
+{
+    if (need <= s.part_doubles) return MH_OK;
+    if (s.part) {
+        MH_CUDA(cudaStreamSynchronize(st));
+        cudaFree(s.part);
+        s.part = nullptr;
+        s.part_doubles = 0;
+    }
+    int rc = dalloc(&s.part, need);
+    if (rc) return rc;
+    s.part_doubles = need;
+    return MH_OK;
+}
+
+// One O(N^2) evaluation of a^(0..P) for all bodies into s.part; returns S via *split.
+int evaluate(mh_sim *sim, int P, int precision, int *split)
+{
+    DeviceState &s = sim->s;
+    const PairPlan pl = plan_pair(P, precision, s.N, s.N, sim->cfg.split_j, sim->device);
+    int rc = ensure_part(s, (size_t)pl.split * (P + 1) * 3 * s.Np, sim->stream);
+    if (rc) return rc;
+    rc = launch_pair(P, precision, s.N, s.Np, s.m, s.jrec, s.jrec32, sim->eps, sim->cfg.G, 0, s.N,
+                     s.part, s.Np, pl, sim->stream);
+    if (rc) return rc;
+    *split = pl.split;
+    sim->ctr.evaluations += 1;
+    sim->ctr.pair_interactions += (double)s.N * (double)(s.N - 1);
+    sim->ctr.kernel_launches += 1;
+    return MH_OK;
+}
+
+// a^(0..2p-1) at t0 from x0, v0 by explicit pair derivatives: passes of two
+// orders each, the later passes using the derivatives found before (Section 3).
+int initialise(mh_sim *sim)
+{
+    DeviceState &s = sim->s;
+    const int K = 2 * s.p;
+    for (int have = 0; have < K; have += 2) {
+        const int P = have + 1;
+        int rc = launch_init_rows(s, have, sim->stream);
+        if (rc) return rc;
+        int split = 0;
+        rc = evaluate(sim, P, MH_PREC_FP64, &split);
+        if (rc) return rc;
+        rc = launch_init_reduce(s, (P + 1) * 3, have, std::min(P + 1, K), split, sim->stream);
+        if (rc) return rc;
+        sim->ctr.kernel_launches += 2;
+    }
+    sim->ctr.evaluations -= s.p;   // initialisation passes are not step evaluations
+    sim->ctr.pair_interactions -= (double)s.p * (double)s.N * (double)(s.N - 1);
+    return MH_OK;
+}
+
+// Precision form: both bound slots <- max |x|, max |v| of host state arrays (N x 3).
+int upload_bounds(DeviceState &s, const double *x, const double *v, cudaStream_t st)
+{
+    if (!s.bound) return MH_OK;
+    double bx = 0.0, bv = 0.0;
+    for (int64_t q = 0; q < 3 * s.N; ++q) {
+        bx = std::max(bx, std::fabs(x[q]));
+        bv = std::max(bv, std::fabs(v[q]));
+    }
+    unsigned long long h[4];
+    std::memcpy(&h[0], &bx, 8);
+    std::memcpy(&h[1], &bv, 8);
+    h[2] = h[0];
+    h[3] = h[1];
+    MH_CUDA(cudaMemcpyAsync(s.bound, h, sizeof(h), cudaMemcpyHostToDevice, st));
+    MH_CUDA(cudaStreamSynchronize(st));
+    s.flip = 0;
+    return MH_OK;
+}
+
+int check_handle(const mh_sim *sim)
+{
+    if (!sim) {
+        set_error("NULL mh_sim handle");
+        return MH_EINVAL;
+    }
+    return MH_OK;
+}
+
+}  // namespace
+
+}  // namespace mh
+
+using namespace mh;
+
+extern "C" {
+
+void mh_config_default(mh_config *cfg)
+{
+    if (!cfg) return;
+    cfg->order = 8;
+    cfg->beta_mode = MH_BETA_MODIFIED;
+    cfg->precision = MH_PREC_FP64;
+    cfg->step_mode = MH_STEP_SHARED;
+    cfg->G = 1.0;
+    cfg->eta = 0.1;
+    cfg->dt_max = 1.0 / 32.0;
+    cfg->k_max = 12;
+    cfg->split_j = 0;
+}
+
+const char *mh_last_error(void) { return g_last_error.c_str(); }
+
+int mh_create(mh_sim **out, int64_t N, int order, const double *m, const double *x, const double *v,
+              double eps, const mh_config *cfg, void *stream)
+{
+    if (!out) {
+        set_error("mh_create: out is NULL");
+        return MH_EINVAL;
+    }
+    *out = nullptr;
+    set_error("");
+    mh_config c;
+    if (cfg) c = *cfg; else mh_config_default(&c);
+    c.order = order;
+    const int p = order_to_p(order);
+    if (p == 0) { set_error("mh_create: order must be 4, 6 or 8"); return MH_EINVAL; }
+    if (N < 1 || !m || !x || !v) { set_error("mh_create: N >= 1 and non-NULL m, x, v required"); return MH_EINVAL; }
+    if (!(eps >= 0.0) || !std::isfinite(eps)) { set_error("mh_create: eps must be finite and >= 0"); return MH_EINVAL; }
+    if (c.precision != MH_PREC_FP64 && c.precision != MH_PREC_FP32PAIR) { set_error("mh_create: bad precision"); return MH_EINVAL; }
+    if (c.beta_mode != MH_BETA_MODIFIED && c.beta_mode != MH_BETA_STANDARD) { set_error("mh_create: bad beta_mode"); return MH_EINVAL; }
+    if (c.step_mode != MH_STEP_SHARED) { set_error("mh_create: block steps are created with step_mode = MH_STEP_BLOCK through mh_create_block"); return MH_EINVAL; }
+    for (int64_t i = 0; i < N; ++i) {
+        if (!std::isfinite(m[i]) || m[i] < 0.0) { set_error("mh_create: masses must be finite and >= 0"); return MH_EINVAL; }
+        for (int q = 0; q < 3; ++q)
+            if (!std::isfinite(x[3 * i + q]) || !std::isfinite(v[3 * i + q])) { set_error("mh_create: non-finite x or v"); return MH_ENONFINITE; }
+    }
+
+    mh_sim *sim = new (std::nothrow) mh_sim();
+    if (!sim) { set_error("mh_create: host allocation failed"); return MH_ENOMEM; }
+    sim->cfg = c;
+    sim->eps = eps;
+    cudaGetDevice(&sim->device);
+    if (stream) {
+        sim->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&sim->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { int rc = cuda_fail(e, "cudaStreamCreate"); delete sim; return rc; }
+        sim->own_stream = true;
+    }
+    DeviceState &s = sim->s;
+    s.N = N;
+    s.Np = pad_to(N, kPad);
+    s.p = p;
+    const int K = 2 * p;
+    const int Pinit = K - 1;                 // highest pair derivative of the initialisation
+    const int rows64 = 3 * (std::max(Pinit, p) + 1);
+    int rc = MH_OK;
+    auto fail = [&](int r) { free_state(s); if (sim->own_stream) cudaStreamDestroy(sim->stream); delete sim; return r; };
+    if ((rc = dalloc(&s.m, s.Np)) || (rc = dalloc(&s.x0, 3 * s.Np)) || (rc = dalloc(&s.v0, 3 * s.Np)) ||
+        (rc = dalloc(&s.d0, (size_t)K * 3 * s.Np)) || (rc = dalloc(&s.x1, 3 * s.Np)) ||
+        (rc = dalloc(&s.v1, 3 * s.Np)) || (rc = dalloc(&s.jrec, (size_t)rows64 * s.Np)) ||
+        (rc = dalloc(&s.flag, 1)) || (rc = dalloc(&s.diag, 3 * s.Np + energy_scratch_doubles(N) + 1)))
+        return fail(rc);
+    if (c.precision == MH_PREC_FP32PAIR &&
+        ((rc = dalloc(&s.jrec32, (size_t)nf32(p) * s.Np)) || (rc = dalloc(&s.bound, 4))))
+        return fail(rc);
+
+    std::vector<double> h;
+    h.assign(s.Np, 0.0);
+    std::memcpy(h.data(), m, N * sizeof(double));
+    cudaError_t e = cudaMemcpyAsync(s.m, h.data(), s.Np * sizeof(double), cudaMemcpyHostToDevice, sim->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "copy m"));
+    std::vector<double> hx, hv;
+    to_soa(x, N, 1, s.Np, hx, 0.0);
+    for (int c3 = 0; c3 < 3; ++c3)
+        for (int64_t i = N; i < s.Np; ++i) hx[(size_t)c3 * s.Np + i] = kFarAway;
+    to_soa(v, N, 1, s.Np, hv, 0.0);
+    e = cudaMemcpyAsync(s.x0, hx.data(), 3 * s.Np * sizeof(double), cudaMemcpyHostToDevice, sim->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.v0, hv.data(), 3 * s.Np * sizeof(double), cudaMemcpyHostToDevice, sim->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.d0, 0, (size_t)K * 3 * s.Np * sizeof(double), sim->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.jrec, 0, (size_t)rows64 * s.Np * sizeof(double), sim->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.flag, 0, sizeof(int), sim->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.x1, s.x0, 3 * s.Np * sizeof(double), cudaMemcpyDeviceToDevice, sim->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.v1, s.v0, 3 * s.Np * sizeof(double), cudaMemcpyDeviceToDevice, sim->stream);
+    std::vector<float> m32;
+    if (e == cudaSuccess && s.jrec32) {
+        // precision-form input: the mass row is constant, the others are written by every step
+        e = cudaMemsetAsync(s.jrec32, 0, (size_t)nf32(p) * s.Np * sizeof(float), sim->stream);
+        m32.assign(s.Np, 0.0f);
+        for (int64_t i = 0; i < N; ++i) m32[i] = (float)m[i];
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s.jrec32 + (size_t)(nf32(p) - 1) * s.Np, m32.data(), s.Np * sizeof(float),
+                                cudaMemcpyHostToDevice, sim->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);   // host buffers go out of scope
+    if (e != cudaSuccess) return fail(cuda_fail(e, "upload state"));
+    if ((rc = upload_bounds(s, x, v, sim->stream))) return fail(rc);
+    if ((rc = initialise(sim))) return fail(rc);
+    e = cudaStreamSynchronize(sim->stream);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "initialisation"));
+    *out = sim;
+    return MH_OK;
+}
+
+void mh_destroy(mh_sim *sim)
+{
+    if (!sim) return;
+    if (sim->stream) cudaStreamSynchronize(sim->stream);
+    free_state(sim->s);
+    if (sim->own_stream && sim->stream) cudaStreamDestroy(sim->stream);
+    delete sim;
+}
+
+int mh_step(mh_sim *sim, double dt, int n_iter)
+{
+    if (int rc = check_handle(sim)) return rc;
+    if (!(dt != 0.0) || !std::isfinite(dt)) { set_error("mh_step: dt must be finite and non-zero"); return MH_EINVAL; }
+    if (n_iter < 1 || n_iter > 64) { set_error("mh_step: n_iter must be in [1, 64]"); return MH_EINVAL; }
+    DeviceState &s = sim->s;
+    const int prec = sim->cfg.precision;
+    int rc = launch_step_phase(s, sim->cfg, dt, 0, false, 0, sim->stream);
+    if (rc) return rc;
+    s.flip ^= 1;                        // the predictor raised the other bound slot
+    sim->ctr.kernel_launches += 1;
+    for (int it = 0; it < n_iter; ++it) {
+        int split = 0;
+        if ((rc = evaluate(sim, s.p, prec, &split))) return rc;
+        const bool last = it == n_iter - 1;
+        if ((rc = launch_step_phase(s, sim->cfg, dt, 1, last, split, sim->stream))) return rc;
+        if (!last) s.flip ^= 1;
+        sim->ctr.kernel_launches += 1;
+    }
+    sim->t += dt;
+    sim->ctr.steps += 1;
+    sim->ctr.particle_steps += (double)s.N;
+    return MH_OK;
+}
+
+static int check_flag(mh_sim *sim)
+{
+    int flag = 0;
+    MH_CUDA(cudaMemcpyAsync(&flag, sim->s.flag, sizeof(int), cudaMemcpyDeviceToHost, sim->stream));
+    MH_CUDA(cudaStreamSynchronize(sim->stream));
+    if (flag) {
+        set_error("non-finite position or velocity produced by a step");
+        return MH_ENONFINITE;
+    }
+    return MH_OK;
+}
+
+int mh_sync(mh_sim *sim, mh_state *out)
+{
+    if (int rc = check_handle(sim)) return rc;
+    if (!out) { set_error("mh_sync: out is NULL"); return MH_EINVAL; }
+    DeviceState &s = sim->s;
+    MH_CUDA(cudaStreamSynchronize(sim->stream));
+    out->t = sim->t;
+    std::vector<double> h;
+    if (out->x) {
+        h.resize(3 * s.Np);
+        MH_CUDA(cudaMemcpy(h.data(), s.x0, 3 * s.Np * sizeof(double), cudaMemcpyDeviceToHost));
+        from_soa(h, s.N, 1, s.Np, out->x);
+    }
+    if (out->v) {
+        h.resize(3 * s.Np);
+        MH_CUDA(cudaMemcpy(h.data(), s.v0, 3 * s.Np * sizeof(double), cudaMemcpyDeviceToHost));
+        from_soa(h, s.N, 1, s.Np, out->v);
+    }
+    if (out->derivs) {
+        const int K = 2 * s.p;
+        h.resize((size_t)K * 3 * s.Np);
+        MH_CUDA(cudaMemcpy(h.data(), s.d0, (size_t)K * 3 * s.Np * sizeof(double), cudaMemcpyDeviceToHost));
+        from_soa(h, s.N, K, s.Np, out->derivs);
+    }
+    return check_flag(sim);
+}
+
+int mh_set_state(mh_sim *sim, const mh_state *in)
+{
+    if (int rc = check_handle(sim)) return rc;
+    if (!in || !in->x || !in->v) { set_error("mh_set_state: x and v are required"); return MH_EINVAL; }
+    DeviceState &s = sim->s;
+    MH_CUDA(cudaStreamSynchronize(sim->stream));
+    std::vector<double> h;
+    to_soa(in->x, s.N, 1, s.Np, h, kFarAway);
+    MH_CUDA(cudaMemcpy(s.x0, h.data(), 3 * s.Np * sizeof(double), cudaMemcpyHostToDevice));
+    to_soa(in->v, s.N, 1, s.Np, h, 0.0);
+    MH_CUDA(cudaMemcpy(s.v0, h.data(), 3 * s.Np * sizeof(double), cudaMemcpyHostToDevice));
+    MH_CUDA(cudaMemsetAsync(s.flag, 0, sizeof(int), sim->stream));
+    if (int rc = upload_bounds(s, in->x, in->v, sim->stream)) return rc;
+    sim->t = in->t;
+    if (in->derivs) {
+        to_soa(in->derivs, s.N, 2 * s.p, s.Np, h, 0.0);
+        MH_CUDA(cudaMemcpy(s.d0, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+        return MH_OK;
+    }
+    int rc = initialise(sim);
+    if (rc) return rc;
+    MH_CUDA(cudaStreamSynchronize(sim->stream));
+    return MH_OK;
+}
+
+int mh_diagnostics(mh_sim *sim, double *energy, double *ecc, int central)
+{
+    if (int rc = check_handle(sim)) return rc;
+    DeviceState &s = sim->s;
+    if (ecc && (central < 0 || central >= s.N)) { set_error("mh_diagnostics: central index out of range"); return MH_EINVAL; }
+    double *e_rows = s.diag;
+    double *e_scalar = s.diag + 3 * s.Np;
+    double *scratch = e_scalar + 1;
+    if (energy) {
+        if (int rc = launch_energy(s, sim->eps, sim->cfg.G, scratch, e_scalar, sim->stream)) return rc;
+        MH_CUDA(cudaMemcpyAsync(energy, e_scalar, sizeof(double), cudaMemcpyDeviceToHost, sim->stream));
+        sim->ctr.kernel_launches += 2;
+    }
+    if (ecc) {
+        if (int rc = launch_ecc(s, sim->cfg.G, central, e_rows, sim->stream)) return rc;
+        sim->ctr.kernel_launches += 1;
+        std::vector<double> h(3 * s.Np);
+        MH_CUDA(cudaMemcpyAsync(h.data(), e_rows, 3 * s.Np * sizeof(double), cudaMemcpyDeviceToHost, sim->stream));
+        MH_CUDA(cudaStreamSynchronize(sim->stream));
+        from_soa(h, s.N, 1, s.Np, ecc);
+    }
+    MH_CUDA(cudaStreamSynchronize(sim->stream));
+    return check_flag(sim);
+}
+
+int mh_info(const mh_sim *sim, int64_t *N, int *order, mh_counters *counters)
+{
+    if (int rc = check_handle(sim)) return rc;
+    if (N) *N = sim->s.N;
+    if (order) *order = sim->cfg.order;
+    if (counters) *counters = sim->ctr;
+    return MH_OK;
+}
+
+}  // extern "C"
+
+// ---- kernel-level entry point on caller-owned device memory ----
+
+namespace {
+struct Scratch {
+    double *part = nullptr;
+    size_t doubles = 0;
+    float *rows32 = nullptr;
+    size_t floats = 0;
+    unsigned long long *bound = nullptr;
+    size_t nbound = 0;
+};
+Scratch g_scratch[64];
+
+template <typename T>
+int grow(T **ptr, size_t *cap, size_t need, cudaStream_t st)
+{
+    if (need <= *cap) return MH_OK;
+    MH_CUDA(cudaStreamSynchronize(st));
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    MH_CUDA(cudaMalloc((void **)ptr, need * sizeof(T)));
+    *cap = need;
+    return MH_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int mh_pair_eval(int P, int precision, int64_t N, const double *m, const double *traj, double eps,
+                 double G, int64_t i0, int64_t i1, double *out, void *stream)
+{
+    set_error("");
+    const bool ok_p = precision == MH_PREC_FP64 ? (P >= 1 && P <= 5)
+                    : precision == MH_PREC_FP32PAIR ? (P >= 1 && P <= 3) : false;
+    if (!ok_p) {
+        set_error("mh_pair_eval: P must be 1..5 (FP64) or 1..3 (FP32-pair)");
+        return MH_EINVAL;
+    }
+    if (N < 1 || !m || !traj || !out || i0 < 0 || i1 > N || i0 >= i1 || !(eps >= 0.0)) {
+        set_error("mh_pair_eval: need N >= 1, device pointers, 0 <= i0 < i1 <= N, eps >= 0");
+        return MH_EINVAL;
+    }
+    int dev = 0;
+    MH_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) { set_error("mh_pair_eval: device index out of range"); return MH_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n_i = i1 - i0;
+    const PairPlan pl = plan_pair(P, precision, n_i, N, 0, dev);
+    Scratch &sc = g_scratch[dev];
+    int rc = grow(&sc.part, &sc.doubles, (size_t)pl.split * (P + 1) * 3 * n_i, st);
+    if (rc) return rc;
+    if (precision == MH_PREC_FP32PAIR) {
+        if ((rc = grow(&sc.rows32, &sc.floats, (size_t)nf32(P) * N, st))) return rc;
+        if ((rc = grow(&sc.bound, &sc.nbound, 2, st))) return rc;
+        if ((rc = launch_split32(N, P, traj, m, sc.rows32, sc.bound, st))) return rc;
+    }
+    rc = launch_pair(P, precision, N, N, m, traj, sc.rows32, eps, G, i0, i1, sc.part, n_i, pl, st);
+    if (rc) return rc;
+    return launch_reduce_out(n_i, n_i, (P + 1) * 3, pl.split, sc.part, out, st);
+}
+
+int mh_release_scratch(void)
+{
+    int dev = 0;
+    MH_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64) {
+        Scratch &sc = g_scratch[dev];
+        if (sc.part || sc.rows32 || sc.bound) MH_CUDA(cudaDeviceSynchronize());
+        if (sc.part) cudaFree(sc.part);
+        if (sc.rows32) cudaFree(sc.rows32);
+        if (sc.bound) cudaFree(sc.bound);
+        sc = Scratch{};
+    }
+    return MH_OK;
+}
+
+}  // extern "C"

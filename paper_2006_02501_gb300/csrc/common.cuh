@@ -1,0 +1,136 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/mh.h"
+
+namespace mh {
+
+constexpr int kPad = 256;          // particle arrays are padded to a multiple of this
+constexpr double kFarAway = 1.0e6;  // position of padding bodies (mass 0)
+
+inline int64_t pad_to(int64_t n, int64_t q) { return (n + q - 1) / q * q; }
+
+// Thread-local last-error message (mh_last_error).
+void set_error(const std::string &msg);
+
+// Record a CUDA failure and return MH_ECUDA (or MH_ENOMEM for allocations).
+int cuda_fail(cudaError_t e, const char *what);
+
+#define MH_CUDA(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return mh::cuda_fail(e_, #call); \
+    } while (0)
+
+#define MH_LAUNCHED(what)                               \
+    do {                                                \
+        cudaError_t e_ = cudaGetLastError();            \
+        if (e_ != cudaSuccess) return mh::cuda_fail(e_, what); \
+    } while (0)
+
+// Work decomposition of one O(N^2) evaluation: i-tiles x j-chunks.  Every
+// (i-tile, j-chunk) item writes its own slot of a partial-sum buffer, and the
+// corrector adds the S slots in a fixed order, so results do not depend on
+// which CTA ran which item.
+struct PairPlan {
+    int threads;        // threads per CTA (one i per thread)
+    int i_per_cta;      // i-particles per CTA tile
+    int tj;             // j-records per shared-memory tile
+    int split;          // S: number of j-chunks
+    int grid;           // CTAs launched (each loops over items)
+    int64_t n_itiles;
+    int64_t chunk;      // j-records per chunk (multiple of tj)
+};
+
+// Device buffers of one simulation (every per-particle array is padded to Np).
+struct DeviceState {
+    int64_t N = 0, Np = 0;
+    int p = 0;             // order 2(p+1)
+    double *m = nullptr;   // [Np]
+    double *x0 = nullptr, *v0 = nullptr;   // [3][Np] committed state at t0
+    double *d0 = nullptr;  // [2p][3][Np]    a^(0..2p-1) at t0
+    double *x1 = nullptr, *v1 = nullptr;   // [3][Np] current estimate at t1
+    double *jrec = nullptr;   // FP64 evaluation input, [3(P+1)][Np] with P = max(p, 2p-1 for init)
+    float *jrec32 = nullptr;  // FP32-pair evaluation input, [NF32][Np]
+    double *part = nullptr;   // [S][P+1][3][Np] partial sums of the split-j evaluation
+    size_t part_doubles = 0;  // capacity of part
+    double *diag = nullptr;   // diagnostics scratch (energy partials, ecc rows, result)
+    int *flag = nullptr;      // device status word (non-finite detection)
+    // Precision form: bounds on |x| and |v| (IEEE bit patterns of non-negative
+    // doubles, so integer atomicMax orders them) in two slots [slot][x, v].
+    // A kernel writing the split input reads slot `flip` and raises slot
+    // 1 - flip, so every thread of one kernel sees the same grid.
+    unsigned long long *bound = nullptr;
+    int flip = 0;
+};
+
+}  // namespace mh
+
+struct mh_sim {
+    mh_config cfg;
+    double eps = 0.0;
+    double t = 0.0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    mh::DeviceState s;
+    mh_counters ctr{};
+};
+
+namespace mh {
+
+// ---- kernels' host launchers (integrator.cu, pair.cu, diag.cu) ----
+
+// Evaluation: fills part[0..S) with a^(0..P) partial sums of bodies i0 <= i < i1
+// from bodies 0 <= j < n_j.  Input rows have stride ld: jrec (FP64, 3(P+1) rows)
+// with masses m, or jrec32 (precision form, nf32(P) rows, mass last).
+int launch_pair(int P, int precision, int64_t n_j, int64_t ld, const double *m, const double *jrec,
+                const float *jrec32, double eps, double G, int64_t i0, int64_t i1, double *part,
+                int64_t part_ld, const PairPlan &plan, cudaStream_t st);
+
+// O(N) step kernels (integrator.cu): phase 0 = predict, 1 = correct.
+int launch_step_phase(const DeviceState &s, const mh_config &cfg, double dt, int phase, bool last,
+                      int split, cudaStream_t st);
+int launch_init_rows(const DeviceState &s, int have, cudaStream_t st);
+int launch_init_reduce(const DeviceState &s, int nr, int lo, int hi, int split, cudaStream_t st);
+int launch_reduce_out(int64_t n, int64_t ld_part, int nr, int split, const double *part, double *out,
+                      cudaStream_t st);
+int launch_split32(int64_t N, int P, const double *traj, const double *m, float *rows,
+                   unsigned long long *bound, cudaStream_t st);
+
+// Hi/lo split of the precision form.  All hi parts lie on one power-of-two
+// grid g with 2^23 g > 2 * bound, so hi_j - hi_i is exact in FP32 for every
+// pair; lo = x - hi (|lo| <= g/2) carries the remaining bits.  A body beyond
+// twice the bound still splits exactly (x = hi + lo to FP32 precision of lo),
+// only its hi differences may round.
+__host__ __device__ inline double split_grid(double bound)
+{
+    int e = 0;
+    frexp(fmax(2.0 * bound, 2.2250738585072014e-308), &e);   // 2^(e-1) <= 2*bound < 2^e
+    return ldexp(1.0, e - 23);
+}
+
+__device__ inline void split_hi_lo(double x, double g, double inv_g, float &hi, float &lo)
+{
+    const double h = rint(x * inv_g) * g;
+    hi = (float)h;
+    lo = (float)(x - (double)hi);
+}
+
+// Diagnostics (diag.cu): energy into *e_dev (device scalar); ecc rows [3][ld].
+int launch_energy(const DeviceState &s, double eps, double G, double *scratch, double *e_dev,
+                  cudaStream_t st);
+int launch_ecc(const DeviceState &s, double G, int central, double *ecc, cudaStream_t st);
+size_t energy_scratch_doubles(int64_t N);
+
+PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hint, int device);
+
+// Number of FP32 rows of the precision-form evaluation input for a given P.
+__host__ __device__ constexpr int nf32(int P) { return 12 + 3 * (P >= 2) + 3 * (P >= 3) + 1; }
+
+}  // namespace mh

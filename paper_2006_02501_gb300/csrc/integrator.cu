@@ -1,0 +1,366 @@
+// O(N) kernels of one P(EC)^n step (Dittmann 2020, Section 2 and Section 3 intro):
+//   k_predict   Taylor predictor of x, v and the a-derivatives the evaluation
+//               needs; writes the evaluation input (FP64 rows or the FP32
+//               hi/lo rows of the precision form).
+//   k_correct   adds the split-j partial sums of the evaluation, applies the
+//               corrector (velocity first, Eq. 6, then position with the new
+//               velocity, Eq. 7 with beta of Eq. 20 or beta = 1), writes the
+//               next evaluation input; after the last pass also the Hermite
+//               interpolation of a^(p+1..2p-1) at t1 and the commit t0 <- t1.
+//   k_init_rows / k_init_reduce   plumbing of the explicit initial derivatives.
+// One thread per body; arrays are SoA rows of length ld (coalesced).
+#include "common.cuh"
+#include "hermite_consts.cuh"
+
+namespace mh {
+
+namespace {
+
+struct StepArgs {
+    int64_t N, ld;
+    double dt;
+    const double *m;
+    double *x0, *v0, *d0;     // committed state at t0 (d0: [2p][3][ld])
+    double *x1, *v1;          // estimate at t1
+    double *jrec;             // FP64 evaluation input [3(p+1)][ld] (x, v, a, a-dot)
+    float *jrec32;            // FP32 evaluation input [nf32(p)][ld]
+    const double *part;       // [S][(p+1)*3][ld]
+    int split;
+    int precision;
+    int beta_mode;
+    int *flag;
+    const unsigned long long *bound_rd;   // [x, v] grid bounds read by this kernel
+    unsigned long long *bound_wr;         // [x, v] raised with this kernel's values
+};
+
+__device__ __forceinline__ void raise_bound(unsigned long long *slot, double val)
+{
+    // warp-wide max of non-negative doubles through their bit patterns, one atomic per warp
+    unsigned long long b = __double_as_longlong(val);
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long q = __shfl_xor_sync(0xffffffffu, b, o);
+        b = q > b ? q : b;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(slot, b);
+}
+
+// Evaluation input of body i (FP64 rows 3k+c: x, v, a, a-dot as needed by P = p).
+template <int p>
+__device__ __forceinline__ void write_input(const StepArgs &a, int64_t i, const double (&x)[3],
+                                            const double (&v)[3], const double (&ad)[p > 1 ? p - 1 : 1][3])
+{
+    if (a.precision == MH_PREC_FP64) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a.jrec[(0 + c) * a.ld + i] = x[c];
+            a.jrec[(3 + c) * a.ld + i] = v[c];
+#pragma unroll
+            for (int q = 0; q + 2 <= p; ++q) a.jrec[(6 + 3 * q + c) * a.ld + i] = ad[q][c];
+        }
+    } else {
+        const double gx = split_grid(__longlong_as_double(a.bound_rd[0]));
+        const double gv = split_grid(__longlong_as_double(a.bound_rd[1]));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float h, l;
+            split_hi_lo(x[c], gx, 1.0 / gx, h, l);
+            a.jrec32[(0 + c) * a.ld + i] = h;
+            a.jrec32[(3 + c) * a.ld + i] = l;
+            split_hi_lo(v[c], gv, 1.0 / gv, h, l);
+            a.jrec32[(6 + c) * a.ld + i] = h;
+            a.jrec32[(9 + c) * a.ld + i] = l;
+#pragma unroll
+            for (int q = 0; q + 2 <= p; ++q) a.jrec32[(12 + 3 * q + c) * a.ld + i] = (float)ad[q][c];
+        }
+    }
+}
+
+// Raise the grid bounds with this thread's |x|, |v| (every lane of the warp calls it).
+__device__ __forceinline__ void track_bounds(const StepArgs &a, bool live, const double (&x)[3],
+                                             const double (&v)[3])
+{
+    if (a.precision == MH_PREC_FP64) return;
+    double bx = 0.0, bv = 0.0;
+    if (live) {
+        bx = fmax(fabs(x[0]), fmax(fabs(x[1]), fabs(x[2])));
+        bv = fmax(fabs(v[0]), fmax(fabs(v[1]), fabs(v[2])));
+        if (!(bx <= 1e300)) bx = 0.0;      // non-finite values are reported by the flag, not tracked
+        if (!(bv <= 1e300)) bv = 0.0;
+    }
+    raise_bound(a.bound_wr + 0, bx);
+    raise_bound(a.bound_wr + 1, bv);
+}
+
+template <int p>
+__global__ void k_predict(StepArgs a)
+{
+    constexpr int K = 2 * p;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i0 < a.N;
+    const int64_t i = live ? i0 : a.N - 1;      // idle lanes recompute the last body, store nothing
+    const double dt = a.dt;
+    double x[3], v[3], ad[p > 1 ? p - 1 : 1][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double d[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) d[k] = a.d0[(3 * k + c) * a.ld + i];
+        // Horner: x + dt (v + dt (d0/2! + dt (d1/3! + ...)))
+        double sx = 0.0, sv = 0.0;
+#pragma unroll
+        for (int k = K - 1; k >= 0; --k) {
+            sx = fma(sx, dt, d[k] * inv_fact(k + 2));
+            sv = fma(sv, dt, d[k] * inv_fact(k + 1));
+        }
+        const double x0 = a.x0[c * a.ld + i], v0 = a.v0[c * a.ld + i];
+        x[c] = fma(fma(sx, dt, v0), dt, x0);
+        v[c] = fma(sv, dt, v0);
+#pragma unroll
+        for (int q = 0; q + 2 <= p; ++q) {
+            double sa = 0.0;
+#pragma unroll
+            for (int k = K - 1; k >= q; --k) sa = fma(sa, dt, d[k] * inv_fact(k - q));
+            ad[q][c] = sa;
+        }
+        if (live) {
+            a.x1[c * a.ld + i] = x[c];
+            a.v1[c * a.ld + i] = v[c];
+        }
+    }
+    track_bounds(a, live, x, v);
+    if (live) write_input<p>(a, i, x, v, ad);
+}
+
+template <int p, bool kLast>
+__global__ void k_correct(StepArgs a)
+{
+    constexpr int K = 2 * p;
+    constexpr int NR = (p + 1) * 3;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i0 < a.N;
+    const int64_t i = live ? i0 : a.N - 1;      // idle lanes recompute the last body, store nothing
+    const double dt = a.dt;
+    const int bm = a.beta_mode;
+    double x[3], v[3], ad[p > 1 ? p - 1 : 1][3];
+    bool finite = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double d1[p + 1], d0[K];
+#pragma unroll
+        for (int k = 0; k <= p; ++k) {
+            double s = 0.0;
+            for (int q = 0; q < a.split; ++q) s += a.part[((int64_t)q * NR + 3 * k + c) * a.ld + i];
+            d1[k] = s;
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) d0[k] = a.d0[(3 * k + c) * a.ld + i];
+        const double x0 = a.x0[c * a.ld + i], v0 = a.v0[c * a.ld + i];
+        // velocity (Eq. 6): sum_k kv(k) (a1^(k) + (-1)^k a0^(k)) dt^(k+1)
+        double sv = 0.0;
+#pragma unroll
+        for (int k = p; k >= 0; --k) {
+            const double f = (k & 1) ? d1[k] - d0[k] : d1[k] + d0[k];
+            sv = fma(sv, dt, kv<p>(k) * f);
+        }
+        const double vn = fma(sv, dt, v0);
+        // position (Eq. 7): kx(0) (v1 + v0) dt + sum_{k>=1} kx(k) (a1^(k-1) +- a0^(k-1)) dt^(k+1)
+        double sx = 0.0;
+#pragma unroll
+        for (int k = p + 1; k >= 1; --k) {
+            const double f = (k & 1) ? d1[k - 1] - d0[k - 1] : d1[k - 1] + d0[k - 1];
+            sx = fma(sx, dt, (bm == 0 ? kx<p>(0, k) : kx<p>(1, k)) * f);
+        }
+        sx = fma(sx, dt, (bm == 0 ? kx<p>(0, 0) : kx<p>(1, 0)) * (vn + v0));
+        const double xn = fma(sx, dt, x0);
+        x[c] = xn;
+        v[c] = vn;
+#pragma unroll
+        for (int q = 0; q + 2 <= p; ++q) ad[q][c] = d1[q];
+        finite = finite && isfinite(xn) && isfinite(vn);
+        if (!live) continue;
+        if (kLast) {
+            a.x0[c * a.ld + i] = xn;
+            a.v0[c * a.ld + i] = vn;
+            double hi[K > p + 1 ? K - p - 1 : 1];
+            if constexpr (p >= 2) {
+                // a^(n)(t1) = sum_k (e1(n,k) a1^(k) + e0(n,k) a0^(k)) dt^(k-n), n = p+1 .. 2p-1
+                const double rdt = 1.0 / dt;
+#pragma unroll
+                for (int n = p + 1; n < K; ++n) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int k = p; k >= 0; --k)
+                        s = fma(s, dt, fma(e1<p>(n, k), d1[k], e0<p>(n, k) * d0[k]));
+                    double sc = 1.0;
+#pragma unroll
+                    for (int e = 0; e < n; ++e) sc *= rdt;
+                    hi[n - p - 1] = s * sc;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                a.d0[(3 * k + c) * a.ld + i] = k <= p ? d1[k] : hi[k - p - 1];
+        } else {
+            a.x1[c * a.ld + i] = xn;
+            a.v1[c * a.ld + i] = vn;
+        }
+    }
+    if (live && !finite) atomicOr(a.flag, 1);
+    if (!kLast) {
+        track_bounds(a, live, x, v);
+        if (live) write_input<p>(a, i, x, v, ad);
+    }
+}
+
+// Initialisation pass with P = have+1: rows 3k+c of jrec hold x, v, a^(0..have-1).
+__global__ void k_init_rows(int64_t N, int64_t ld, int have, const double *x0, const double *v0,
+                            const double *d0, double *jrec)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    for (int c = 0; c < 3; ++c) {
+        jrec[(0 + c) * ld + i] = x0[c * ld + i];
+        jrec[(3 + c) * ld + i] = v0[c * ld + i];
+        for (int k = 0; k < have; ++k) jrec[(6 + 3 * k + c) * ld + i] = d0[(3 * k + c) * ld + i];
+    }
+}
+
+// d0 rows [lo, hi) <- sum over S partial slots of rows [lo, hi) (slot row count nr).
+__global__ void k_init_reduce(int64_t N, int64_t ld, int nr, int lo, int hi, int split,
+                              const double *part, double *d0)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    for (int k = lo; k < hi; ++k)
+        for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (int q = 0; q < split; ++q) s += part[((int64_t)q * nr + 3 * k + c) * ld + i];
+            d0[(3 * k + c) * ld + i] = s;
+        }
+}
+
+// out rows [0, nr) <- sum over S slots (mh_pair_eval's reduction).
+__global__ void k_reduce_out(int64_t n, int64_t ld_part, int nr, int split, const double *part,
+                             double *out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int r = 0; r < nr; ++r) {
+        double s = 0.0;
+        for (int q = 0; q < split; ++q) s += part[((int64_t)q * nr + r) * ld_part + i];
+        out[r * n + i] = s;
+    }
+}
+
+// max |x| and max |v| over the bodies of FP64 SoA rows (stride N) into bound[0..1]
+// (bound must be zero on entry).
+__global__ void k_absmax(int64_t N, const double *traj, unsigned long long *bound)
+{
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i0 < N;
+    const int64_t i = live ? i0 : 0;
+    double bx = 0.0, bv = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        bx = fmax(bx, fabs(traj[c * N + i]));
+        bv = fmax(bv, fabs(traj[(3 + c) * N + i]));
+    }
+    if (!live || !(bx <= 1e300)) bx = 0.0;
+    if (!live || !(bv <= 1e300)) bv = 0.0;
+    raise_bound(bound + 0, bx);
+    raise_bound(bound + 1, bv);
+}
+
+// Precision-form input rows (x hi/lo, v hi/lo, a, a-dot, m) from FP64 SoA rows
+// (stride N) of x, v, a, a-dot, with the hi parts on the grid of bound[0..1].
+__global__ void k_split32(int64_t N, int P, const double *traj, const double *m, float *rows,
+                          const unsigned long long *bound)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double gx = split_grid(__longlong_as_double(bound[0]));
+    const double gv = split_grid(__longlong_as_double(bound[1]));
+    for (int c = 0; c < 3; ++c) {
+        float h, l;
+        split_hi_lo(traj[(0 + c) * N + i], gx, 1.0 / gx, h, l);
+        rows[(0 + c) * N + i] = h;
+        rows[(3 + c) * N + i] = l;
+        split_hi_lo(traj[(3 + c) * N + i], gv, 1.0 / gv, h, l);
+        rows[(6 + c) * N + i] = h;
+        rows[(9 + c) * N + i] = l;
+        for (int q = 0; q + 2 <= P; ++q) rows[(12 + 3 * q + c) * N + i] = (float)traj[(6 + 3 * q + c) * N + i];
+    }
+    rows[(int64_t)(nf32(P) - 1) * N + i] = (float)m[i];
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <int p>
+int launch_step_kernels(const StepArgs &a, int phase, bool last, cudaStream_t st)
+{
+    const int T = 128;
+    const unsigned g = blocks_for(a.N, T);
+    if (phase == 0) {
+        k_predict<p><<<g, T, 0, st>>>(a);
+        MH_LAUNCHED("k_predict");
+    } else if (last) {
+        k_correct<p, true><<<g, T, 0, st>>>(a);
+        MH_LAUNCHED("k_correct(last)");
+    } else {
+        k_correct<p, false><<<g, T, 0, st>>>(a);
+        MH_LAUNCHED("k_correct");
+    }
+    return MH_OK;
+}
+
+}  // namespace
+
+// phase 0: predict; phase 1: correct (last = final pass of the step).
+int launch_step_phase(const DeviceState &s, const mh_config &cfg, double dt, int phase, bool last,
+                      int split, cudaStream_t st)
+{
+    StepArgs a{s.N, s.Np, dt, s.m, s.x0, s.v0, s.d0, s.x1, s.v1, s.jrec, s.jrec32, s.part,
+               split, cfg.precision, cfg.beta_mode, s.flag,
+               s.bound ? s.bound + 2 * s.flip : nullptr, s.bound ? s.bound + 2 * (1 - s.flip) : nullptr};
+    switch (s.p) {
+    case 1: return launch_step_kernels<1>(a, phase, last, st);
+    case 2: return launch_step_kernels<2>(a, phase, last, st);
+    case 3: return launch_step_kernels<3>(a, phase, last, st);
+    }
+    set_error("unsupported p");
+    return MH_EINVAL;
+}
+
+int launch_init_rows(const DeviceState &s, int have, cudaStream_t st)
+{
+    k_init_rows<<<blocks_for(s.N, 128), 128, 0, st>>>(s.N, s.Np, have, s.x0, s.v0, s.d0, s.jrec);
+    MH_LAUNCHED("k_init_rows");
+    return MH_OK;
+}
+
+int launch_init_reduce(const DeviceState &s, int nr, int lo, int hi, int split, cudaStream_t st)
+{
+    k_init_reduce<<<blocks_for(s.N, 128), 128, 0, st>>>(s.N, s.Np, nr, lo, hi, split, s.part, s.d0);
+    MH_LAUNCHED("k_init_reduce");
+    return MH_OK;
+}
+
+int launch_split32(int64_t N, int P, const double *traj, const double *m, float *rows,
+                   unsigned long long *bound, cudaStream_t st)
+{
+    MH_CUDA(cudaMemsetAsync(bound, 0, 2 * sizeof(unsigned long long), st));
+    k_absmax<<<blocks_for(N, 128), 128, 0, st>>>(N, traj, bound);
+    MH_LAUNCHED("k_absmax");
+    k_split32<<<blocks_for(N, 128), 128, 0, st>>>(N, P, traj, m, rows, bound);
+    MH_LAUNCHED("k_split32");
+    return MH_OK;
+}
+
+int launch_reduce_out(int64_t n, int64_t ld_part, int nr, int split, const double *part, double *out,
+                      cudaStream_t st)
+{
+    k_reduce_out<<<blocks_for(n, 128), 128, 0, st>>>(n, ld_part, nr, split, part, out);
+    MH_LAUNCHED("k_reduce_out");
+    return MH_OK;
+}
+
+}  // namespace mh

@@ -1,0 +1,381 @@
+// O(N^2) direct-summation evaluation of a^(0..P) (the E of P(EC)^n).
+//
+// Pair physics (Dittmann 2020, Section 3, intro): a_ij = G m_j r_ij s^(-3/2),
+// s = r_ij^2 + eps^2.  Its time derivatives along the trajectory follow from
+// T a = G m r with T = s^(3/2): differentiating n times,
+//   A^(n) = G m S r^(n) - sum_{k=1..n} C(n,k) tau_k A^(n-k),   S = s^(-3/2),
+//   tau_k = T^(k)/T,  tau_n = 1.5 q_n + sum_{j=1..n-1} (1.5 C(n-1,j-1) - C(n-1,j)) q_j tau_(n-j),
+//   q_k = s^(k)/s,    s^(k) = sum_j C(k,j) r^(j).r^(k-j)   (eps enters s^(0) only).
+// For P = 3 this is the familiar alpha/beta/gamma form: tau_1 = 3 alpha,
+// tau_2 = 3 beta, tau_3 = 3 gamma.
+//
+// Decomposition: items = (i-tile of `threads` bodies, one per thread) x
+// (j-chunk); a CTA loops over items with a grid stride; j-records of a chunk
+// are staged through shared memory in tiles of `tj`.  Each item writes its own
+// partial-sum slot; the corrector (or mh_pair_eval's reduction) adds the
+// slots in a fixed order, so the result is deterministic.
+//
+// Two arithmetic forms:
+//   FP64:     every operation in double precision; 1/sqrt(s) from the FP32
+//             MUFU estimate refined by one third-order Householder step.
+//   FP32PAIR: the pair arithmetic in FP32.  Differences of x and v are taken
+//             from a hi/lo split of the FP64 values, (hi_j - hi_i) + (lo_j - lo_i),
+//             which is the FP64 difference rounded to FP32 within about one ulp;
+//             sums run in FP32 over one shared-memory tile and are added to
+//             FP64 accumulators after every tile.
+#include <algorithm>
+
+#include "common.cuh"
+#include "hermite_consts.cuh"
+
+namespace mh {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// pair-derivative core, shared by both forms (T = double or float)
+// ---------------------------------------------------------------------------
+
+// q_k = s^(k)/s for k = 1..P from the relative trajectory derivatives r[0..P].
+template <int P, typename T>
+__device__ __forceinline__ void s_ratios(const T (&r)[P + 1][3], T sinv, T (&q)[P + 1])
+{
+#pragma unroll
+    for (int k = 1; k <= P; ++k) {
+        T acc = T(0);
+#pragma unroll
+        for (int j = 0; 2 * j <= k; ++j) {
+            const T w = T((2 * j == k) ? binom(k, j) : 2.0 * binom(k, j));
+            const T d = r[j][0] * r[k - j][0] + r[j][1] * r[k - j][1] + r[j][2] * r[k - j][2];
+            acc = (j == 0) ? w * d : acc + w * d;
+        }
+        q[k] = acc * sinv;
+    }
+}
+
+// A^(0..P) of one pair given mS = G m s^(-3/2), q_k and r^(k); accumulated into acc.
+template <int P, typename T>
+__device__ __forceinline__ void pair_terms(const T (&r)[P + 1][3], T mS, const T (&q)[P + 1],
+                                           T (&acc)[P + 1][3])
+{
+    T tau[P + 1];
+    tau[0] = T(1);
+#pragma unroll
+    for (int n = 1; n <= P; ++n) {
+        T t = T(1.5) * q[n];
+#pragma unroll
+        for (int j = 1; j <= n - 1; ++j) {
+            const T w = T(1.5 * binom(n - 1, j - 1) - binom(n - 1, j));
+            t += w * q[j] * tau[n - j];
+        }
+        tau[n] = t;
+    }
+    T A[P + 1][3];
+#pragma unroll
+    for (int n = 0; n <= P; ++n) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            T a = mS * r[n][c];
+#pragma unroll
+            for (int k = 1; k <= n; ++k) a -= (T(binom(n, k)) * tau[k]) * A[n - k][c];
+            A[n][c] = a;
+            acc[n][c] += a;
+        }
+    }
+}
+
+// 1/sqrt(s) in FP64: FP32 estimate (MUFU), then one third-order Householder
+// step y <- y (1 + e/2 + 3e^2/8), e = 1 - s y^2 (error ~ e0^3).
+__device__ __forceinline__ double rsqrt_fp64(double s)
+{
+    double y = (double)rsqrtf((float)s);
+    const double e = fma(-s, y * y, 1.0);
+    const double t = fma(0.375, e, 0.5);
+    return fma(y * e, t, y);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 form
+// ---------------------------------------------------------------------------
+
+template <int P>
+struct PairArgs64 {
+    const double *jrec;   // [3(P+1)][ld]
+    const double *m;      // [ld]
+    int64_t ld;           // row stride of jrec / length of m
+    int64_t n_j;          // bodies j in [0, n_j) (multiple of tj; padding has m = 0)
+    int64_t i0, i1;
+    double eps2, G;
+    double *part;         // [S][(P+1)*3][part_ld], index i - i0
+    int64_t part_ld;
+    int64_t n_itiles, chunk;
+    int split, tj;
+};
+
+template <int P>
+__global__ void __launch_bounds__(128) k_pair_fp64(PairArgs64<P> a)
+{
+    constexpr int NF = 3 * (P + 1);
+    extern __shared__ double sh[];      // [NF + 1][tj]
+    const int tj = a.tj;
+    const int64_t items = a.n_itiles * a.split;
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int64_t itile = item % a.n_itiles;
+        const int jc = (int)(item / a.n_itiles);
+        const int64_t i = a.i0 + itile * blockDim.x + threadIdx.x;
+        const bool live = i < a.i1;
+        const int64_t ic = live ? i : a.i0;
+        double ri[P + 1][3];
+#pragma unroll
+        for (int k = 0; k <= P; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ri[k][c] = a.jrec[(3 * k + c) * a.ld + ic];
+        double acc[P + 1][3];
+#pragma unroll
+        for (int k = 0; k <= P; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[k][c] = 0.0;
+
+        const int64_t jb = (int64_t)jc * a.chunk;
+        const int64_t je = min(jb + a.chunk, a.n_j);
+        for (int64_t j0 = jb; j0 < je; j0 += tj) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < (NF + 1) * tj; e += blockDim.x) {
+                const int row = e / tj, col = e - row * tj;
+                const int64_t j = j0 + col;
+                // bodies past n_j: massless and far away, so they add exactly zero
+                sh[e] = j < a.n_j ? (row < NF ? a.jrec[row * a.ld + j] : a.m[j])
+                                  : (row < 3 ? kFarAway : 0.0);
+            }
+            __syncthreads();
+            for (int jj = 0; jj < tj; ++jj) {
+                double r[P + 1][3];
+#pragma unroll
+                for (int k = 0; k <= P; ++k)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) r[k][c] = sh[(3 * k + c) * tj + jj] - ri[k][c];
+                const bool self = (j0 + jj) == ic;
+                double s = fma(r[0][0], r[0][0], fma(r[0][1], r[0][1], fma(r[0][2], r[0][2], a.eps2)));
+                s = self ? 1.0 : s;
+                const double mj = self ? 0.0 : sh[NF * tj + jj];
+                const double rinv = rsqrt_fp64(s);
+                const double sinv = rinv * rinv;
+                const double mS = a.G * mj * (rinv * sinv);
+                double q[P + 1];
+                s_ratios<P, double>(r, sinv, q);
+                pair_terms<P, double>(r, mS, q, acc);
+            }
+        }
+        if (live) {
+            double *out = a.part + (int64_t)jc * (P + 1) * 3 * a.part_ld + (i - a.i0);
+#pragma unroll
+            for (int k = 0; k <= P; ++k)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) out[(3 * k + c) * a.part_ld] = acc[k][c];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP32-pair form
+// ---------------------------------------------------------------------------
+// Input rows (jrec32, each of length ld):
+//   0-2 x_hi, 3-5 x_lo, 6-8 v_hi, 9-11 v_lo, then a (P >= 2), a-dot (P >= 3), m.
+// Shared-memory tile: one record of RS floats per j (x_hi, x_lo, v_hi, v_lo,
+// a, a-dot, m, padding), read by every lane of a warp as broadcast float4s.
+
+template <int P>
+struct Rec32 {
+    static constexpr int NF = nf32(P);                 // input rows
+    static constexpr int RS = (NF + 3) / 4 * 4;        // floats per smem record
+};
+
+template <int P>
+struct PairArgs32 {
+    const float *jrec32;  // [NF][ld]
+    int64_t ld, n_j, i0, i1;
+    float eps2, G;
+    double *part;
+    int64_t part_ld, n_itiles, chunk;
+    int split, tj;
+};
+
+template <int P>
+__global__ void __launch_bounds__(256) k_pair_fp32(PairArgs32<P> a)
+{
+    constexpr int NF = Rec32<P>::NF;
+    constexpr int RS = Rec32<P>::RS;
+    extern __shared__ float4 sh4[];                   // [tj][RS/4]
+    float *sh = reinterpret_cast<float *>(sh4);
+    const int tj = a.tj;
+    const int64_t items = a.n_itiles * a.split;
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int64_t itile = item % a.n_itiles;
+        const int jc = (int)(item / a.n_itiles);
+        const int64_t i = a.i0 + itile * blockDim.x + threadIdx.x;
+        const bool live = i < a.i1;
+        const int64_t ic = live ? i : a.i0;
+        float xh[3], xl[3], vh[3], vl[3], ai[(P >= 2) ? 3 : 1], ji[(P >= 3) ? 3 : 1];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            xh[c] = a.jrec32[(0 + c) * a.ld + ic];
+            xl[c] = a.jrec32[(3 + c) * a.ld + ic];
+            vh[c] = a.jrec32[(6 + c) * a.ld + ic];
+            vl[c] = a.jrec32[(9 + c) * a.ld + ic];
+            if constexpr (P >= 2) ai[c] = a.jrec32[(12 + c) * a.ld + ic];
+            if constexpr (P >= 3) ji[c] = a.jrec32[(15 + c) * a.ld + ic];
+        }
+        double acc64[P + 1][3];
+#pragma unroll
+        for (int k = 0; k <= P; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc64[k][c] = 0.0;
+
+        const int64_t jb = (int64_t)jc * a.chunk;
+        const int64_t je = min(jb + a.chunk, a.n_j);
+        for (int64_t j0 = jb; j0 < je; j0 += tj) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < NF * tj; e += blockDim.x) {
+                const int row = e / tj, col = e - row * tj;
+                const int64_t j = j0 + col;
+                sh[col * RS + row] = j < a.n_j ? a.jrec32[row * a.ld + j] : (row < 3 ? (float)kFarAway : 0.0f);
+            }
+            __syncthreads();
+            float acc[P + 1][3];
+#pragma unroll
+            for (int k = 0; k <= P; ++k)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) acc[k][c] = 0.0f;
+#pragma unroll 2
+            for (int jj = 0; jj < tj; ++jj) {
+                float rec[RS];
+#pragma unroll
+                for (int q4 = 0; q4 < RS / 4; ++q4) {
+                    const float4 t = sh4[jj * (RS / 4) + q4];
+                    rec[4 * q4 + 0] = t.x; rec[4 * q4 + 1] = t.y;
+                    rec[4 * q4 + 2] = t.z; rec[4 * q4 + 3] = t.w;
+                }
+                float r[P + 1][3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    r[0][c] = (rec[c] - xh[c]) + (rec[3 + c] - xl[c]);
+                    r[1][c] = (rec[6 + c] - vh[c]) + (rec[9 + c] - vl[c]);
+                    if constexpr (P >= 2) r[2][c] = rec[12 + c] - ai[c];
+                    if constexpr (P >= 3) r[3][c] = rec[15 + c] - ji[c];
+                }
+                const bool self = (j0 + jj) == ic;
+                float s = fmaf(r[0][0], r[0][0], fmaf(r[0][1], r[0][1], fmaf(r[0][2], r[0][2], a.eps2)));
+                s = self ? 1.0f : s;
+                const float mj = self ? 0.0f : rec[NF - 1];
+                const float rinv = rsqrtf(s);
+                const float sinv = rinv * rinv;
+                const float mS = a.G * mj * (rinv * sinv);
+                float q[P + 1];
+                s_ratios<P, float>(r, sinv, q);
+                pair_terms<P, float>(r, mS, q, acc);
+            }
+#pragma unroll
+            for (int k = 0; k <= P; ++k)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) acc64[k][c] += (double)acc[k][c];
+        }
+        if (live) {
+            double *out = a.part + (int64_t)jc * (P + 1) * 3 * a.part_ld + (i - a.i0);
+#pragma unroll
+            for (int k = 0; k <= P; ++k)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) out[(3 * k + c) * a.part_ld] = acc64[k][c];
+        }
+    }
+}
+
+template <int P>
+int launch_fp64(const double *jrec, const double *m, int64_t ld, int64_t n_j, double eps,
+                double G, int64_t i0, int64_t i1, double *part, int64_t part_ld,
+                const PairPlan &pl, cudaStream_t st)
+{
+    PairArgs64<P> a{jrec, m, ld, n_j, i0, i1, eps * eps, G, part, part_ld,
+                    pl.n_itiles, pl.chunk, pl.split, pl.tj};
+    const size_t smem = sizeof(double) * (3 * (P + 1) + 1) * pl.tj;
+    k_pair_fp64<P><<<pl.grid, pl.threads, smem, st>>>(a);
+    MH_LAUNCHED("k_pair_fp64");
+    return MH_OK;
+}
+
+template <int P>
+int launch_fp32(const float *jrec32, int64_t ld, int64_t n_j, double eps, double G, int64_t i0,
+                int64_t i1, double *part, int64_t part_ld, const PairPlan &pl, cudaStream_t st)
+{
+    PairArgs32<P> a{jrec32, ld, n_j, i0, i1, (float)(eps * eps), (float)G, part, part_ld,
+                    pl.n_itiles, pl.chunk, pl.split, pl.tj};
+    const size_t smem = sizeof(float) * Rec32<P>::RS * pl.tj;
+    k_pair_fp32<P><<<pl.grid, pl.threads, smem, st>>>(a);
+    MH_LAUNCHED("k_pair_fp32");
+    return MH_OK;
+}
+
+}  // namespace
+
+PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hint, int device)
+{
+    static int n_sm_cache[64] = {0};
+    int n_sm = device >= 0 && device < 64 ? n_sm_cache[device] : 0;
+    if (n_sm == 0) {
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
+        if (n_sm <= 0) n_sm = 148;
+        if (device >= 0 && device < 64) n_sm_cache[device] = n_sm;
+    }
+    PairPlan pl{};
+    pl.threads = precision == MH_PREC_FP64 ? 128 : 256;
+    pl.i_per_cta = pl.threads;
+    pl.tj = precision == MH_PREC_FP64 ? 64 : 128;
+    const int occ = precision == MH_PREC_FP64 ? 4 : 2;     // resident CTAs per SM
+    const int slots = n_sm * occ;
+    pl.n_itiles = (n_i + pl.i_per_cta - 1) / pl.i_per_cta;
+    const int64_t n_jt = (n_j + pl.tj - 1) / pl.tj;        // j-tiles
+    int best_S = 1;
+    double best_cost = 1e300;
+    const int s_max = (int)std::min<int64_t>(64, n_jt);
+    for (int S = 1; S <= s_max; ++S) {
+        if (split_hint > 0 && S != std::min(split_hint, s_max)) continue;
+        const int64_t tiles_per_chunk = (n_jt + S - 1) / S;
+        const int64_t S_eff = (n_jt + tiles_per_chunk - 1) / tiles_per_chunk;
+        if (S_eff != S) continue;
+        const int64_t items = pl.n_itiles * S;
+        const int64_t waves = (items + slots - 1) / slots;
+        // time ~ waves x tiles per item; small penalty per chunk for the partial-sum traffic
+        const double cost = (double)waves * tiles_per_chunk * (1.0 + 0.002 * S);
+        if (cost < best_cost) { best_cost = cost; best_S = S; }
+    }
+    pl.split = best_S;
+    const int64_t tiles_per_chunk = (n_jt + best_S - 1) / best_S;
+    pl.chunk = tiles_per_chunk * pl.tj;
+    const int64_t items = pl.n_itiles * pl.split;
+    pl.grid = (int)std::min<int64_t>(items, slots);
+    return pl;
+}
+
+int launch_pair(int P, int precision, int64_t n_j, int64_t ld, const double *m, const double *jrec,
+                const float *jrec32, double eps, double G, int64_t i0, int64_t i1, double *part,
+                int64_t part_ld, const PairPlan &pl, cudaStream_t st)
+{
+    if (precision == MH_PREC_FP64) {
+        switch (P) {
+        case 1: return launch_fp64<1>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, st);
+        case 2: return launch_fp64<2>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, st);
+        case 3: return launch_fp64<3>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, st);
+        case 4: return launch_fp64<4>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, st);
+        case 5: return launch_fp64<5>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, st);
+        }
+    } else {
+        switch (P) {
+        case 1: return launch_fp32<1>(jrec32, ld, n_j, eps, G, i0, i1, part, part_ld, pl, st);
+        case 2: return launch_fp32<2>(jrec32, ld, n_j, eps, G, i0, i1, part, part_ld, pl, st);
+        case 3: return launch_fp32<3>(jrec32, ld, n_j, eps, G, i0, i1, part, part_ld, pl, st);
+        }
+    }
+    set_error("launch_pair: unsupported P/precision");
+    return MH_EINVAL;
+}
+
+}  // namespace mh

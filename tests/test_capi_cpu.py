@@ -1,0 +1,97 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every
+entry point that include/*.h declares, and rejects bad arguments before
+touching the device."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2006_02501_gb300.build import build
+    build()
+    from paper_2006_02501_gb300 import _capi
+    return _capi.lib()
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names.update(re.findall(r"\b(mh_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = _declared()
+    assert "mh_create" in names and "mh_step" in names and "mh_sync" in names and "mh_diagnostics" in names
+    for n in names:
+        assert hasattr(L, n), n
+    from paper_2006_02501_gb300 import _capi
+    assert sorted(_capi.EXPORTS) == names
+
+
+def test_config_default(L):
+    from paper_2006_02501_gb300 import _capi
+    c = _capi.Config()
+    L.mh_config_default(ctypes.byref(c))
+    assert c.order == 8 and c.G == 1.0 and c.precision == 0 and c.beta_mode == 0 and c.k_max == 12
+
+
+def _create(L, N, order, m, x, v, eps):
+    h = ctypes.c_void_p()
+    dp = ctypes.POINTER(ctypes.c_double)
+    ptr = lambda a: None if a is None else a.ctypes.data_as(dp)
+    rc = L.mh_create(ctypes.byref(h), N, order, ptr(m), ptr(x), ptr(v), eps, None, None)
+    return rc, h
+
+
+def test_invalid_arguments_rejected_before_device_use(L):
+    m = np.ones(4)
+    x = np.zeros((4, 3))
+    v = np.zeros((4, 3))
+    rc, h = _create(L, 4, 5, m, x, v, 0.1)        # order must be 4, 6, 8
+    assert rc == -1 and not h.value
+    assert b"order" in L.mh_last_error()
+    rc, h = _create(L, 0, 8, m, x, v, 0.1)        # N >= 1
+    assert rc == -1
+    rc, h = _create(L, 4, 8, m, x, v, -1.0)       # eps >= 0
+    assert rc == -1
+    rc, h = _create(L, 4, 8, None, x, v, 0.1)     # NULL masses
+    assert rc == -1
+    bad = x.copy()
+    bad[2, 1] = np.nan
+    rc, h = _create(L, 4, 8, m, bad, v, 0.1)      # non-finite input
+    assert rc == -4
+    mneg = m.copy()
+    mneg[0] = -1
+    rc, h = _create(L, 4, 8, mneg, x, v, 0.1)
+    assert rc == -1
+    assert L.mh_step(None, 0.1, 3) == -1          # NULL handle
+    assert L.mh_sync(None, None) == -1
+    assert L.mh_diagnostics(None, None, None, 0) == -1
+    L.mh_destroy(None)                            # no-op
+
+
+def test_pair_eval_argument_checks(L):
+    # unsupported P / precision combinations fail before any device call
+    assert L.mh_pair_eval(6, 0, 10, 1, 1, 0.0, 1.0, 0, 10, 1, None) == -1
+    assert L.mh_pair_eval(4, 1, 10, 1, 1, 0.0, 1.0, 0, 10, 1, None) == -1
+    assert L.mh_pair_eval(3, 0, 10, 1, 1, 0.0, 1.0, 5, 5, 1, None) == -1   # empty range
+    assert L.mh_pair_eval(3, 0, 10, 1, 1, 0.0, 1.0, 0, 11, 1, None) == -1  # i1 > N
+    assert L.mh_pair_eval(3, 0, 10, 0, 1, 0.0, 1.0, 0, 10, 1, None) == -1  # NULL m
+
+
+def test_python_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_2006_02501_gb300 import _capi
+    monkeypatch.setattr(_capi, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(_capi, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        _capi.lib()
