@@ -68,6 +68,11 @@ typedef struct {
     double dt_max;      /* block steps: largest step (levels are dt_max * 2^-k) */
     int k_max;          /* block steps: deepest level, 0 <= k_max <= 20 (default 12) */
     int split_j;        /* pair kernel: j-range split factor, 0 = automatic */
+    double heavy_frac;  /* precision form only: pairs whose source body j has
+                           m_j >= heavy_frac * (total mass) are evaluated in FP64
+                           (at most 32 such bodies; 0 disables; default 1e-3).  In
+                           a disc around a central mass this keeps the dominant
+                           central force at FP64 accuracy for O(N) extra work. */
 } mh_config;
 
 /* Snapshot of a simulation (mh_sync / mh_set_state).  Each pointer may be NULL

@@ -56,11 +56,14 @@ class Simulation:
 
     order: 4, 6 or 8; precision: MH_PREC_FP64 or MH_PREC_FP32PAIR; beta:
     MH_BETA_MODIFIED (Eq. 20) or MH_BETA_STANDARD (beta = 1); stream: a
-    torch.cuda.Stream, a raw cudaStream_t integer, or None (library stream).
+    torch.cuda.Stream, a raw cudaStream_t integer, or None (library stream);
+    heavy_frac: precision form, mass fraction above which a source body's
+    pairs run in FP64 (None = library default 1e-3, 0 = all pairs FP32).
     """
 
     def __init__(self, order: int, m, x, v, eps: float, precision: int = MH_PREC_FP64,
-                 beta: int = MH_BETA_MODIFIED, G: float = 1.0, stream=None, split_j: int = 0):
+                 beta: int = MH_BETA_MODIFIED, G: float = 1.0, stream=None, split_j: int = 0,
+                 heavy_frac: float | None = None):
         L = _capi.lib()
         m = _host(m)
         N = m.shape[0]
@@ -68,6 +71,8 @@ class Simulation:
         cfg = _capi.Config()
         L.mh_config_default(ctypes.byref(cfg))
         cfg.order, cfg.precision, cfg.beta_mode, cfg.G, cfg.split_j = order, precision, beta, G, split_j
+        if heavy_frac is not None:
+            cfg.heavy_frac = heavy_frac
         h = ctypes.c_void_p()
         check(L.mh_create(ctypes.byref(h), N, order, _ptr(m), _ptr(x), _ptr(v), float(eps),
                           ctypes.byref(cfg), _stream_handle(stream)))

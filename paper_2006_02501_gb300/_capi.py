@@ -35,7 +35,8 @@ EXPORTS = [
 class Config(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("beta_mode", ctypes.c_int), ("precision", ctypes.c_int),
                 ("step_mode", ctypes.c_int), ("G", ctypes.c_double), ("eta", ctypes.c_double),
-                ("dt_max", ctypes.c_double), ("k_max", ctypes.c_int), ("split_j", ctypes.c_int)]
+                ("dt_max", ctypes.c_double), ("k_max", ctypes.c_int), ("split_j", ctypes.c_int),
+                ("heavy_frac", ctypes.c_double)]
 
 
 class StateC(ctypes.Structure):

@@ -43,7 +43,8 @@ int dalloc(T **ptr, size_t count)
 
 void free_state(DeviceState &s)
 {
-    void *ptrs[] = {s.m, s.x0, s.v0, s.d0, s.x1, s.v1, s.jrec, s.jrec32, s.part, s.diag, s.flag, s.bound};
+    void *ptrs[] = {s.m, s.x0, s.v0, s.d0, s.x1, s.v1, s.jrec, s.jrec32, s.part, s.diag, s.flag, s.bound,
+                    s.heavy};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     s = DeviceState{};
@@ -86,12 +87,20 @@ int evaluate(mh_sim *sim, int P, int precision, int *split)
 {
     DeviceState &s = sim->s;
     const PairPlan pl = plan_pair(P, precision, s.N, s.N, sim->cfg.split_j, sim->device);
-    int rc = ensure_part(s, (size_t)pl.split * (P + 1) * 3 * s.Np, sim->stream);
+    const bool heavy = precision == MH_PREC_FP32PAIR && s.n_heavy > 0;
+    const int slots = pl.split + (heavy ? 1 : 0);
+    int rc = ensure_part(s, (size_t)slots * (P + 1) * 3 * s.Np, sim->stream);
     if (rc) return rc;
     rc = launch_pair(P, precision, s.N, s.Np, s.m, s.jrec, s.jrec32, sim->eps, sim->cfg.G, 0, s.N,
                      s.part, s.Np, pl, sim->stream);
     if (rc) return rc;
-    *split = pl.split;
+    if (heavy) {
+        rc = launch_pair_heavy(P, s.N, s.Np, s.m, s.jrec, s.heavy, s.n_heavy, sim->eps, sim->cfg.G,
+                               s.part, pl.split, sim->stream);
+        if (rc) return rc;
+        sim->ctr.kernel_launches += 1;
+    }
+    *split = slots;
     sim->ctr.evaluations += 1;
     sim->ctr.pair_interactions += (double)s.N * (double)(s.N - 1);
     sim->ctr.kernel_launches += 1;
@@ -169,6 +178,7 @@ void mh_config_default(mh_config *cfg)
     cfg->dt_max = 1.0 / 32.0;
     cfg->k_max = 12;
     cfg->split_j = 0;
+    cfg->heavy_frac = 1e-3;
 }
 
 const char *mh_last_error(void) { return g_last_error.c_str(); }
@@ -247,11 +257,27 @@ int mh_create(mh_sim **out, int64_t N, int order, const double *m, const double 
     if (e == cudaSuccess) e = cudaMemcpyAsync(s.x1, s.x0, 3 * s.Np * sizeof(double), cudaMemcpyDeviceToDevice, sim->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s.v1, s.v0, 3 * s.Np * sizeof(double), cudaMemcpyDeviceToDevice, sim->stream);
     std::vector<float> m32;
+    std::vector<int> heavy;
     if (e == cudaSuccess && s.jrec32) {
+        // heavy source bodies: their pairs run in FP64, so their FP32 mass is 0
+        double mtot = 0.0;
+        for (int64_t i = 0; i < N; ++i) mtot += m[i];
+        if (c.heavy_frac > 0.0)
+            for (int64_t i = 0; i < N; ++i)
+                if (m[i] > 0.0 && m[i] >= c.heavy_frac * mtot && (int)heavy.size() < kMaxHeavy)
+                    heavy.push_back((int)i);
         // precision-form input: the mass row is constant, the others are written by every step
         e = cudaMemsetAsync(s.jrec32, 0, (size_t)nf32(p) * s.Np * sizeof(float), sim->stream);
         m32.assign(s.Np, 0.0f);
         for (int64_t i = 0; i < N; ++i) m32[i] = (float)m[i];
+        for (int h : heavy) m32[h] = 0.0f;
+        if (e == cudaSuccess && !heavy.empty()) {
+            e = cudaMalloc((void **)&s.heavy, heavy.size() * sizeof(int));
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(s.heavy, heavy.data(), heavy.size() * sizeof(int),
+                                    cudaMemcpyHostToDevice, sim->stream);
+            s.n_heavy = (int)heavy.size();
+        }
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(s.jrec32 + (size_t)(nf32(p) - 1) * s.Np, m32.data(), s.Np * sizeof(float),
                                 cudaMemcpyHostToDevice, sim->stream);

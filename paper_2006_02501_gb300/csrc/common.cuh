@@ -67,7 +67,12 @@ struct DeviceState {
     // 1 - flip, so every thread of one kernel sees the same grid.
     unsigned long long *bound = nullptr;
     int flip = 0;
+    // Precision form: source bodies whose pairs are evaluated in FP64.
+    int n_heavy = 0;
+    int *heavy = nullptr;     // [n_heavy] body indices (device)
 };
+
+constexpr int kMaxHeavy = 32;
 
 }  // namespace mh
 
@@ -129,6 +134,12 @@ int launch_ecc(const DeviceState &s, double G, int central, double *ecc, cudaStr
 size_t energy_scratch_doubles(int64_t N);
 
 PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hint, int device);
+
+// FP64 contributions of the heavy source bodies to every body i < N, written
+// to partial slot `slot` (rows (P+1)*3 of stride ld) of part.
+int launch_pair_heavy(int P, int64_t N, int64_t ld, const double *m, const double *jrec,
+                      const int *heavy, int n_heavy, double eps, double G, double *part, int slot,
+                      cudaStream_t st);
 
 // Number of FP32 rows of the precision-form evaluation input for a given P.
 __host__ __device__ constexpr int nf32(int P) { return 12 + 3 * (P >= 2) + 3 * (P >= 3) + 1; }

@@ -49,15 +49,15 @@ template <int p>
 __device__ __forceinline__ void write_input(const StepArgs &a, int64_t i, const double (&x)[3],
                                             const double (&v)[3], const double (&ad)[p > 1 ? p - 1 : 1][3])
 {
-    if (a.precision == MH_PREC_FP64) {
+    // FP64 rows: the input of the FP64 form, and of the heavy-body pairs of the precision form
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            a.jrec[(0 + c) * a.ld + i] = x[c];
-            a.jrec[(3 + c) * a.ld + i] = v[c];
+    for (int c = 0; c < 3; ++c) {
+        a.jrec[(0 + c) * a.ld + i] = x[c];
+        a.jrec[(3 + c) * a.ld + i] = v[c];
 #pragma unroll
-            for (int q = 0; q + 2 <= p; ++q) a.jrec[(6 + 3 * q + c) * a.ld + i] = ad[q][c];
-        }
-    } else {
+        for (int q = 0; q + 2 <= p; ++q) a.jrec[(6 + 3 * q + c) * a.ld + i] = ad[q][c];
+    }
+    if (a.precision != MH_PREC_FP64) {
         const double gx = split_grid(__longlong_as_double(a.bound_rd[0]));
         const double gv = split_grid(__longlong_as_double(a.bound_rd[1]));
 #pragma unroll

@@ -289,6 +289,45 @@ __global__ void __launch_bounds__(256) k_pair_fp32(PairArgs32<P> a)
     }
 }
 
+// FP64 contributions of a short list of heavy source bodies (precision form):
+// one thread per body i, the heavy records read through the read-only cache.
+template <int P>
+__global__ void k_pair_heavy(int64_t N, int64_t ld, const double *__restrict__ m,
+                             const double *__restrict__ jrec, const int *__restrict__ heavy,
+                             int n_heavy, double eps2, double G, double *__restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double ri[P + 1][3], acc[P + 1][3];
+#pragma unroll
+    for (int k = 0; k <= P; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ri[k][c] = jrec[(3 * k + c) * ld + i];
+            acc[k][c] = 0.0;
+        }
+    for (int h = 0; h < n_heavy; ++h) {
+        const int j = __ldg(heavy + h);
+        if (j == i) continue;
+        double r[P + 1][3];
+#pragma unroll
+        for (int k = 0; k <= P; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) r[k][c] = __ldg(jrec + (3 * k + c) * ld + j) - ri[k][c];
+        const double s = fma(r[0][0], r[0][0], fma(r[0][1], r[0][1], fma(r[0][2], r[0][2], eps2)));
+        const double rinv = rsqrt_fp64(s);
+        const double sinv = rinv * rinv;
+        const double mS = G * __ldg(m + j) * (rinv * sinv);
+        double q[P + 1];
+        s_ratios<P, double>(r, sinv, q);
+        pair_terms<P, double>(r, mS, q, acc);
+    }
+#pragma unroll
+    for (int k = 0; k <= P; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) out[(3 * k + c) * ld + i] = acc[k][c];
+}
+
 template <int P>
 int launch_fp64(const double *jrec, const double *m, int64_t ld, int64_t n_j, double eps,
                 double G, int64_t i0, int64_t i1, double *part, int64_t part_ld,
@@ -315,6 +354,22 @@ int launch_fp32(const float *jrec32, int64_t ld, int64_t n_j, double eps, double
 }
 
 }  // namespace
+
+int launch_pair_heavy(int P, int64_t N, int64_t ld, const double *m, const double *jrec,
+                      const int *heavy, int n_heavy, double eps, double G, double *part, int slot,
+                      cudaStream_t st)
+{
+    double *out = part + (int64_t)slot * (P + 1) * 3 * ld;
+    const unsigned g = (unsigned)((N + 127) / 128);
+    switch (P) {
+    case 1: k_pair_heavy<1><<<g, 128, 0, st>>>(N, ld, m, jrec, heavy, n_heavy, eps * eps, G, out); break;
+    case 2: k_pair_heavy<2><<<g, 128, 0, st>>>(N, ld, m, jrec, heavy, n_heavy, eps * eps, G, out); break;
+    case 3: k_pair_heavy<3><<<g, 128, 0, st>>>(N, ld, m, jrec, heavy, n_heavy, eps * eps, G, out); break;
+    default: set_error("launch_pair_heavy: P must be 1..3"); return MH_EINVAL;
+    }
+    MH_LAUNCHED("k_pair_heavy");
+    return MH_OK;
+}
 
 PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hint, int device)
 {
