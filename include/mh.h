@@ -91,6 +91,9 @@ typedef struct {
     double pair_interactions;    /* sum over evaluations of N_active * (N - 1) */
     double particle_steps;       /* particles advanced */
     int64_t kernel_launches;     /* kernels launched by this handle */
+    double pair_kernel_ms;       /* with timing on: summed device time of the O(N^2)
+                                    evaluation kernels (CUDA events around each launch) */
+    int64_t pair_kernel_timed;   /* number of evaluation launches in pair_kernel_ms */
 } mh_counters;
 
 /* Fill *cfg with the defaults listed above. */
@@ -131,7 +134,13 @@ int mh_set_state(mh_sim *sim, const mh_state *in);
 int mh_diagnostics(mh_sim *sim, double *energy, double *ecc, int central);
 
 /* Number of bodies, order and counters of a handle. */
-int mh_info(const mh_sim *sim, int64_t *N, int *order, mh_counters *counters);
+int mh_info(mh_sim *sim, int64_t *N, int *order, mh_counters *counters);
+
+/* Turn per-launch timing of the O(N^2) evaluation kernels on (1) or off (0).
+ * While on, CUDA events bracket every evaluation launch on the handle's stream;
+ * their durations are added to the counters at the next mh_sync, mh_diagnostics
+ * or mh_info call (which then waits for the stream). */
+int mh_set_timing(mh_sim *sim, int on);
 
 /* Message describing the calling thread's most recent error ("" if none). */
 const char *mh_last_error(void);

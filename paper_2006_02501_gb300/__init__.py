@@ -130,6 +130,10 @@ class Simulation:
     def energy(self) -> float:
         return self.diagnostics(energy=True, ecc=False)[0]
 
+    def set_timing(self, on: bool) -> None:
+        """Bracket every O(N^2) evaluation launch with CUDA events (see counters())."""
+        check(_capi.lib().mh_set_timing(self._h, 1 if on else 0))
+
     def counters(self) -> dict:
         n, o, c = ctypes.c_int64(), ctypes.c_int(), _capi.Counters()
         check(_capi.lib().mh_info(self._h, ctypes.byref(n), ctypes.byref(o), ctypes.byref(c)))

@@ -29,6 +29,7 @@ MH_STEP_SHARED, MH_STEP_BLOCK = 0, 1
 EXPORTS = [
     "mh_config_default", "mh_create", "mh_destroy", "mh_step", "mh_sync", "mh_set_state",
     "mh_diagnostics", "mh_info", "mh_last_error", "mh_pair_eval", "mh_release_scratch",
+    "mh_set_timing",
 ]
 
 
@@ -47,7 +48,8 @@ class StateC(ctypes.Structure):
 class Counters(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("evaluations", ctypes.c_int64),
                 ("pair_interactions", ctypes.c_double), ("particle_steps", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("pair_kernel_ms", ctypes.c_double),
+                ("pair_kernel_timed", ctypes.c_int64)]
 
 
 class MHError(RuntimeError):
@@ -85,6 +87,7 @@ def lib() -> ctypes.CDLL:
             L.mh_last_error.restype = ctypes.c_char_p
             L.mh_pair_eval.argtypes = [I, I, I64, P, P, D, D, I64, I64, P, P]
             L.mh_release_scratch.argtypes = []
+            L.mh_set_timing.argtypes = [P, I]
             for name in EXPORTS:
                 if name not in ("mh_destroy", "mh_config_default", "mh_last_error"):
                     getattr(L, name).restype = ctypes.c_int

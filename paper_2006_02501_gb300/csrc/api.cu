@@ -82,10 +82,43 @@ int ensure_part(DeviceState &s, size_t need, cudaStream_t st)
     return MH_OK;
 }
 
+// Resolve the timing events of finished evaluation launches (waits for the stream).
+int collect_timing(mh_sim *sim)
+{
+    if (sim->ev_pending.empty()) return MH_OK;
+    MH_CUDA(cudaStreamSynchronize(sim->stream));
+    for (auto &pr : sim->ev_pending) {
+        float ms = 0.0f;
+        MH_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+        sim->ctr.pair_kernel_ms += ms;
+        sim->ctr.pair_kernel_timed += 1;
+        sim->ev_free.push_back(pr);
+    }
+    sim->ev_pending.clear();
+    return MH_OK;
+}
+
+int timed_event_pair(mh_sim *sim, std::pair<cudaEvent_t, cudaEvent_t> *out)
+{
+    if (!sim->ev_free.empty()) {
+        *out = sim->ev_free.back();
+        sim->ev_free.pop_back();
+        return MH_OK;
+    }
+    MH_CUDA(cudaEventCreate(&out->first));
+    MH_CUDA(cudaEventCreate(&out->second));
+    return MH_OK;
+}
+
 // One O(N^2) evaluation of a^(0..P) for all bodies into s.part; returns S via *split.
 int evaluate(mh_sim *sim, int P, int precision, int *split)
 {
     DeviceState &s = sim->s;
+    std::pair<cudaEvent_t, cudaEvent_t> ev{};
+    if (sim->timing) {
+        if (int rc = timed_event_pair(sim, &ev)) return rc;
+        MH_CUDA(cudaEventRecord(ev.first, sim->stream));
+    }
     const PairPlan pl = plan_pair(P, precision, s.N, s.N, sim->cfg.split_j, sim->device);
     const bool heavy = precision == MH_PREC_FP32PAIR && s.n_heavy > 0;
     const int slots = pl.split + (heavy ? 1 : 0);
@@ -94,6 +127,10 @@ int evaluate(mh_sim *sim, int P, int precision, int *split)
     rc = launch_pair(P, precision, s.N, s.Np, s.m, s.jrec, s.jrec32, sim->eps, sim->cfg.G, 0, s.N,
                      s.part, s.Np, pl, sim->stream);
     if (rc) return rc;
+    if (sim->timing) {
+        MH_CUDA(cudaEventRecord(ev.second, sim->stream));
+        sim->ev_pending.push_back(ev);
+    }
     if (heavy) {
         rc = launch_pair_heavy(P, s.N, s.Np, s.m, s.jrec, s.heavy, s.n_heavy, sim->eps, sim->cfg.G,
                                s.part, pl.split, sim->stream);
@@ -296,6 +333,11 @@ void mh_destroy(mh_sim *sim)
 {
     if (!sim) return;
     if (sim->stream) cudaStreamSynchronize(sim->stream);
+    for (auto &pr : sim->ev_pending) sim->ev_free.push_back(pr);
+    for (auto &pr : sim->ev_free) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
     free_state(sim->s);
     if (sim->own_stream && sim->stream) cudaStreamDestroy(sim->stream);
     delete sim;
@@ -344,6 +386,7 @@ int mh_sync(mh_sim *sim, mh_state *out)
     if (!out) { set_error("mh_sync: out is NULL"); return MH_EINVAL; }
     DeviceState &s = sim->s;
     MH_CUDA(cudaStreamSynchronize(sim->stream));
+    if (int rc = collect_timing(sim)) return rc;
     out->t = sim->t;
     std::vector<double> h;
     if (out->x) {
@@ -415,9 +458,17 @@ int mh_diagnostics(mh_sim *sim, double *energy, double *ecc, int central)
     return check_flag(sim);
 }
 
-int mh_info(const mh_sim *sim, int64_t *N, int *order, mh_counters *counters)
+int mh_set_timing(mh_sim *sim, int on)
 {
     if (int rc = check_handle(sim)) return rc;
+    sim->timing = on != 0;
+    return MH_OK;
+}
+
+int mh_info(mh_sim *sim, int64_t *N, int *order, mh_counters *counters)
+{
+    if (int rc = check_handle(sim)) return rc;
+    if (int rc = collect_timing(sim)) return rc;
     if (N) *N = sim->s.N;
     if (order) *order = sim->cfg.order;
     if (counters) *counters = sim->ctr;

@@ -5,6 +5,8 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/mh.h"
 
@@ -78,6 +80,8 @@ constexpr int kMaxHeavy = 32;
 
 struct mh_sim {
     mh_config cfg;
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_free;
     double eps = 0.0;
     double t = 0.0;
     cudaStream_t stream = nullptr;

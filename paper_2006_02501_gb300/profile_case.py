@@ -1,0 +1,39 @@
+"""Run one small disc case through the library, for profilers.
+
+    python -m paper_2006_02501_gb300.profile_case --N 16384 --precision fp64 --order 8 --steps 1
+
+Creates an SMBH disc of N stars (same recipe as the benchmark workload, seed 2),
+runs the initialisation and `steps` shared P(EC)^3 steps, then exits.  The
+initialisation launches one evaluation per pass (p passes), so a profiler that
+wants the first step's evaluation skips those.
+"""
+import argparse
+import os
+import sys
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--N", type=int, default=16384)
+    ap.add_argument("--precision", choices=["fp64", "fp32pair"], default="fp64")
+    ap.add_argument("--order", type=int, default=8)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--n-iter", type=int, default=3)
+    a = ap.parse_args()
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import paper_2006_02501_gb300 as mh
+    from paper_2006_02501_gb300 import inputs
+    mh.build_library()
+    m, x, v = inputs.smbh_disc(seed=2, N=a.N)
+    prec = mh.MH_PREC_FP64 if a.precision == "fp64" else mh.MH_PREC_FP32PAIR
+    with mh.Simulation(a.order, m, x, v, 1e-4, precision=prec) as sim:
+        sim.step(2 * np.pi * 1e-3, a.n_iter, nsteps=a.steps)
+        t, xs, vs, ds = sim.sync()
+    print(f"ok N={len(m)} {a.precision} order {a.order} steps {a.steps} t={t:.6f} "
+          f"finite={bool(np.isfinite(xs).all())}")
+
+
+if __name__ == "__main__":
+    main()
