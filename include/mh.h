@@ -163,6 +163,27 @@ int mh_pair_eval(int P, int precision, int64_t N, const double *m, const double 
 /* Free the scratch memory cached by mh_pair_eval on the current device. */
 int mh_release_scratch(void);
 
+/* mh_pair_eval without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that must not call cudaMalloc, such as a
+ * solver embedded in a host application that owns and budgets all device
+ * memory, or a latency-critical loop that cannot afford the implicit
+ * synchronisation an allocation may cause.  Same arguments, semantics and
+ * results (within rounding of the partial-sum grouping) as mh_pair_eval.
+ *   Scratch: a fixed 32 MiB array compiled into the library; every GPU that
+ *   loads the library holds it until the process exits.  A problem whose
+ *   scratch does not fit (the split-j partial sums of (P+1)*3*(i1-i0) doubles,
+ *   plus nf32(P)*N floats in the precision form) is rejected with MH_EINVAL and
+ *   a message naming the bytes it needed; nothing is launched then.
+ *   The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   All calls on a device share the one array and it keeps the previous call's
+ *   contents; the entry point clears what must start at zero.  Calls whose
+ *   work overlaps on the GPU (different streams, or several host threads) race
+ *   on the array: order them on one stream or synchronise between them. */
+int mh_pair_eval_noalloc(int P, int precision, int64_t N, const double *m, const double *traj,
+                         double eps, double G, int64_t i0, int64_t i1, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

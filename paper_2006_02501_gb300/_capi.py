@@ -29,7 +29,7 @@ MH_STEP_SHARED, MH_STEP_BLOCK = 0, 1
 EXPORTS = [
     "mh_config_default", "mh_create", "mh_destroy", "mh_step", "mh_sync", "mh_set_state",
     "mh_diagnostics", "mh_info", "mh_last_error", "mh_pair_eval", "mh_release_scratch",
-    "mh_set_timing",
+    "mh_set_timing", "mh_pair_eval_noalloc",
 ]
 
 
@@ -88,6 +88,7 @@ def lib() -> ctypes.CDLL:
             L.mh_pair_eval.argtypes = [I, I, I64, P, P, D, D, I64, I64, P, P]
             L.mh_release_scratch.argtypes = []
             L.mh_set_timing.argtypes = [P, I]
+            L.mh_pair_eval_noalloc.argtypes = [I, I, I64, P, P, D, D, I64, I64, P, P]
             for name in EXPORTS:
                 if name not in ("mh_destroy", "mh_config_default", "mh_last_error"):
                     getattr(L, name).restype = ctypes.c_int
