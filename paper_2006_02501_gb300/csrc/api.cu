@@ -306,7 +306,7 @@ int mh_create(mh_sim **out, int64_t N, int order, const double *m, const double 
         // precision-form input: the mass row is constant, the others are written by every step
         e = cudaMemsetAsync(s.jrec32, 0, (size_t)nf32(p) * s.Np * sizeof(float), sim->stream);
         m32.assign(s.Np, 0.0f);
-        for (int64_t i = 0; i < N; ++i) m32[i] = (float)m[i];
+        for (int64_t i = 0; i < N; ++i) m32[i] = (float)(c.G * m[i]);
         for (int h : heavy) m32[h] = 0.0f;
         if (e == cudaSuccess && !heavy.empty()) {
             e = cudaMalloc((void **)&s.heavy, heavy.size() * sizeof(int));
@@ -532,7 +532,7 @@ int mh_pair_eval(int P, int precision, int64_t N, const double *m, const double 
     if (precision == MH_PREC_FP32PAIR) {
         if ((rc = grow(&sc.rows32, &sc.floats, (size_t)nf32(P) * N, st))) return rc;
         if ((rc = grow(&sc.bound, &sc.nbound, 2, st))) return rc;
-        if ((rc = launch_split32(N, P, traj, m, sc.rows32, sc.bound, st))) return rc;
+        if ((rc = launch_split32(N, P, traj, m, G, sc.rows32, sc.bound, st))) return rc;
     }
     rc = launch_pair(P, precision, N, N, m, traj, sc.rows32, eps, G, i0, i1, sc.part, n_i, pl, st);
     if (rc) return rc;

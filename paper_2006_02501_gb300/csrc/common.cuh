@@ -109,7 +109,7 @@ int launch_init_rows(const DeviceState &s, int have, cudaStream_t st);
 int launch_init_reduce(const DeviceState &s, int nr, int lo, int hi, int split, cudaStream_t st);
 int launch_reduce_out(int64_t n, int64_t ld_part, int nr, int split, const double *part, double *out,
                       cudaStream_t st);
-int launch_split32(int64_t N, int P, const double *traj, const double *m, float *rows,
+int launch_split32(int64_t N, int P, const double *traj, const double *m, double G, float *rows,
                    unsigned long long *bound, cudaStream_t st);
 
 // Hi/lo split of the precision form.  All hi parts lie on one power-of-two

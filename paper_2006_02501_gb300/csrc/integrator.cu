@@ -270,9 +270,9 @@ __global__ void k_absmax(int64_t N, const double *traj, unsigned long long *boun
     raise_bound(bound + 1, bv);
 }
 
-// Precision-form input rows (x hi/lo, v hi/lo, a, a-dot, m) from FP64 SoA rows
+// Precision-form input rows (x hi/lo, v hi/lo, a, a-dot, G m) from FP64 SoA rows
 // (stride N) of x, v, a, a-dot, with the hi parts on the grid of bound[0..1].
-__global__ void k_split32(int64_t N, int P, const double *traj, const double *m, float *rows,
+__global__ void k_split32(int64_t N, int P, const double *traj, const double *m, double G, float *rows,
                           const unsigned long long *bound)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -289,7 +289,7 @@ __global__ void k_split32(int64_t N, int P, const double *traj, const double *m,
         rows[(9 + c) * N + i] = l;
         for (int q = 0; q + 2 <= P; ++q) rows[(12 + 3 * q + c) * N + i] = (float)traj[(6 + 3 * q + c) * N + i];
     }
-    rows[(int64_t)(nf32(P) - 1) * N + i] = (float)m[i];
+    rows[(int64_t)(nf32(P) - 1) * N + i] = (float)(G * m[i]);
 }
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -344,13 +344,13 @@ int launch_init_reduce(const DeviceState &s, int nr, int lo, int hi, int split, 
     return MH_OK;
 }
 
-int launch_split32(int64_t N, int P, const double *traj, const double *m, float *rows,
+int launch_split32(int64_t N, int P, const double *traj, const double *m, double G, float *rows,
                    unsigned long long *bound, cudaStream_t st)
 {
     MH_CUDA(cudaMemsetAsync(bound, 0, 2 * sizeof(unsigned long long), st));
     k_absmax<<<blocks_for(N, 128), 128, 0, st>>>(N, traj, bound);
     MH_LAUNCHED("k_absmax");
-    k_split32<<<blocks_for(N, 128), 128, 0, st>>>(N, P, traj, m, rows, bound);
+    k_split32<<<blocks_for(N, 128), 128, 0, st>>>(N, P, traj, m, G, rows, bound);
     MH_LAUNCHED("k_split32");
     return MH_OK;
 }

@@ -89,7 +89,7 @@ extern "C" int mh_pair_eval_noalloc(int P, int precision, int64_t N, const doubl
         bound = reinterpret_cast<unsigned long long *>(b + part_bytes + rows_bytes);
         // the previous call's contents stay in the array: launch_split32 zeroes
         // the two bounds before raising them
-        if (int rc = launch_split32(N, P, traj, m, rows32, bound, st)) return rc;
+        if (int rc = launch_split32(N, P, traj, m, G, rows32, bound, st)) return rc;
     }
     // every partial-sum entry the reduction reads is written by the evaluation
     if (int rc = launch_pair(P, precision, N, N, m, traj, rows32, eps, G, i0, i1, part, n_i, pl, st))

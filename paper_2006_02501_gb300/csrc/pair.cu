@@ -84,6 +84,79 @@ __device__ __forceinline__ void pair_terms(const T (&r)[P + 1][3], T mS, const T
     }
 }
 
+// The same derivatives for P <= 3 written out with alpha = tau_1/3,
+// beta = tau_2/3, gamma = tau_3/3, the highest term folded into its
+// accumulator (it is not needed by any other term):
+//   alpha = (r.v)/s,  beta = (v.v + r.a)/s + alpha^2,
+//   gamma = (3 v.a + r.adot)/s + alpha (3 beta - 4 alpha^2),
+//   A0 = mS r, A1 = mS v - 3 alpha A0, A2 = mS a - 6 alpha A1 - 3 beta A0,
+//   A3 = mS adot - 9 alpha A2 - 9 beta A1 - 3 gamma A0.
+template <int P, typename T>
+__device__ __forceinline__ void pair_abg(const T (&r)[P + 1][3], T mS, T sinv, T (&acc)[P + 1][3])
+{
+    static_assert(P >= 1 && P <= 3, "pair_abg handles P = 1, 2, 3");
+    const T rv = r[0][0] * r[1][0] + r[0][1] * r[1][1] + r[0][2] * r[1][2];
+    const T al = rv * sinv;
+    T A0[3], A1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) A0[c] = mS * r[0][c];
+    const T a3 = T(3) * al;
+    if constexpr (P == 1) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            acc[0][c] += A0[c];
+            acc[1][c] += mS * r[1][c] - a3 * A0[c];
+        }
+        return;
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A1[c] = mS * r[1][c] - a3 * A0[c];
+        const T al2 = al * al;
+        const T w2 = r[1][0] * r[1][0] + r[1][1] * r[1][1] + r[1][2] * r[1][2]
+                   + r[0][0] * r[2][0] + r[0][1] * r[2][1] + r[0][2] * r[2][2];
+        const T be = w2 * sinv + al2;
+        const T a6 = T(6) * al, b3 = T(3) * be;
+        if constexpr (P == 2) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                acc[0][c] += A0[c];
+                acc[1][c] += A1[c];
+                acc[2][c] += mS * r[2][c] - a6 * A1[c] - b3 * A0[c];
+            }
+            return;
+        } else {
+            T A2[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) A2[c] = mS * r[2][c] - a6 * A1[c] - b3 * A0[c];
+            const T va = r[1][0] * r[2][0] + r[1][1] * r[2][1] + r[1][2] * r[2][2];
+            const T w3 = T(3) * va + r[0][0] * r[3][0] + r[0][1] * r[3][1] + r[0][2] * r[3][2];
+            const T ga = w3 * sinv + al * (b3 - T(4) * al2);
+            const T a9 = T(9) * al, b9 = T(9) * be, g3 = T(3) * ga;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                acc[0][c] += A0[c];
+                acc[1][c] += A1[c];
+                acc[2][c] += A2[c];
+                acc[3][c] += mS * r[3][c] - a9 * A2[c] - b9 * A1[c] - g3 * A0[c];
+            }
+        }
+    }
+}
+
+// Pair derivatives for any supported P: the alpha/beta/gamma form up to P = 3,
+// the general recursion above it.
+template <int P, typename T>
+__device__ __forceinline__ void pair_derivs(const T (&r)[P + 1][3], T mS, T sinv, T (&acc)[P + 1][3])
+{
+    if constexpr (P <= 3) {
+        pair_abg<P, T>(r, mS, sinv, acc);
+    } else {
+        T q[P + 1];
+        s_ratios<P, T>(r, sinv, q);
+        pair_terms<P, T>(r, mS, q, acc);
+    }
+}
+
 // 1/sqrt(s) in FP64: FP32 estimate (MUFU), then one third-order Householder
 // step y <- y (1 + e/2 + 3e^2/8), e = 1 - s y^2 (error ~ e0^3).
 __device__ __forceinline__ double rsqrt_fp64(double s)
@@ -111,6 +184,29 @@ struct PairArgs64 {
     int64_t n_itiles, chunk;
     int split, tj;
 };
+
+template <int P, bool kGuard>
+__device__ __forceinline__ void interact64(const double *sh, int tj, int jj, bool self,
+                                           const double (&ri)[P + 1][3], const PairArgs64<P> &a,
+                                           double (&acc)[P + 1][3])
+{
+    constexpr int NF = 3 * (P + 1);
+    double r[P + 1][3];
+#pragma unroll
+    for (int k = 0; k <= P; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r[k][c] = sh[(3 * k + c) * tj + jj] - ri[k][c];
+    double s = fma(r[0][0], r[0][0], fma(r[0][1], r[0][1], fma(r[0][2], r[0][2], a.eps2)));
+    double mj = sh[NF * tj + jj];
+    if (kGuard) {
+        s = self ? 1.0 : s;
+        mj = self ? 0.0 : mj;
+    }
+    const double rinv = rsqrt_fp64(s);
+    const double sinv = rinv * rinv;
+    const double mS = a.G * mj * (rinv * sinv);
+    pair_derivs<P, double>(r, mS, sinv, acc);
+}
 
 template <int P>
 __global__ void __launch_bounds__(128) k_pair_fp64(PairArgs64<P> a)
@@ -148,22 +244,12 @@ __global__ void __launch_bounds__(128) k_pair_fp64(PairArgs64<P> a)
                                   : (row < 3 ? kFarAway : 0.0);
             }
             __syncthreads();
-            for (int jj = 0; jj < tj; ++jj) {
-                double r[P + 1][3];
-#pragma unroll
-                for (int k = 0; k <= P; ++k)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) r[k][c] = sh[(3 * k + c) * tj + jj] - ri[k][c];
-                const bool self = (j0 + jj) == ic;
-                double s = fma(r[0][0], r[0][0], fma(r[0][1], r[0][1], fma(r[0][2], r[0][2], a.eps2)));
-                s = self ? 1.0 : s;
-                const double mj = self ? 0.0 : sh[NF * tj + jj];
-                const double rinv = rsqrt_fp64(s);
-                const double sinv = rinv * rinv;
-                const double mS = a.G * mj * (rinv * sinv);
-                double q[P + 1];
-                s_ratios<P, double>(r, sinv, q);
-                pair_terms<P, double>(r, mS, q, acc);
+            // the i == j pair can only occur when this tile overlaps the CTA's i-range
+            const int64_t ib = a.i0 + itile * blockDim.x;
+            if (j0 < ib + (int64_t)blockDim.x && ib < j0 + tj) {
+                for (int jj = 0; jj < tj; ++jj) interact64<P, true>(sh, tj, jj, j0 + jj == ic, ri, a, acc);
+            } else {
+                for (int jj = 0; jj < tj; ++jj) interact64<P, false>(sh, tj, jj, false, ri, a, acc);
             }
         }
         if (live) {
@@ -192,50 +278,87 @@ struct Rec32 {
 
 template <int P>
 struct PairArgs32 {
-    const float *jrec32;  // [NF][ld]
+    const float *jrec32;  // [NF][ld], the mass row holding G m
     int64_t ld, n_j, i0, i1;
-    float eps2, G;
+    float eps2;
     double *part;
     int64_t part_ld, n_itiles, chunk;
     int split, tj;
 };
 
-template <int P>
-__global__ void __launch_bounds__(256) k_pair_fp32(PairArgs32<P> a)
+constexpr int kThreads32 = 256;
+
+template <int P, bool kGuard>
+__device__ __forceinline__ void interact32(const float4 *sh4, int jj, bool self, const float (&xh)[3],
+                                           const float (&xl)[3], const float (&vh)[3], const float (&vl)[3],
+                                           const float (&ai)[3], const float (&ji)[3], float eps2,
+                                           float (&acc)[P + 1][3])
 {
     constexpr int NF = Rec32<P>::NF;
     constexpr int RS = Rec32<P>::RS;
-    extern __shared__ float4 sh4[];                   // [tj][RS/4]
+    float rec[RS];
+#pragma unroll
+    for (int q4 = 0; q4 < RS / 4; ++q4) {
+        const float4 t = sh4[jj * (RS / 4) + q4];
+        rec[4 * q4 + 0] = t.x; rec[4 * q4 + 1] = t.y;
+        rec[4 * q4 + 2] = t.z; rec[4 * q4 + 3] = t.w;
+    }
+    float r[P + 1][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        r[0][c] = (rec[c] - xh[c]) + (rec[3 + c] - xl[c]);
+        r[1][c] = (rec[6 + c] - vh[c]) + (rec[9 + c] - vl[c]);
+        if constexpr (P >= 2) r[2][c] = rec[12 + c] - ai[c];
+        if constexpr (P >= 3) r[3][c] = rec[15 + c] - ji[c];
+    }
+    float s = fmaf(r[0][0], r[0][0], fmaf(r[0][1], r[0][1], fmaf(r[0][2], r[0][2], eps2)));
+    float gm = rec[NF - 1];
+    if (kGuard) {
+        s = self ? 1.0f : s;
+        gm = self ? 0.0f : gm;
+    }
+    const float rinv = rsqrtf(s);
+    const float sinv = rinv * rinv;
+    const float mS = gm * rinv * sinv;
+    pair_abg<P, float>(r, mS, sinv, acc);
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads32, 2) k_pair_fp32(PairArgs32<P> a)
+{
+    constexpr int NF = Rec32<P>::NF;
+    constexpr int RS = Rec32<P>::RS;
+    extern __shared__ float4 sh4[];                   // [tj][RS/4] records, then FP64 accumulators
     float *sh = reinterpret_cast<float *>(sh4);
     const int tj = a.tj;
+    // per-thread FP64 accumulators across tiles: [(P+1)*3][kThreads32]
+    double *acc64 = reinterpret_cast<double *>(sh + (size_t)tj * RS);
     const int64_t items = a.n_itiles * a.split;
     for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
         const int64_t itile = item % a.n_itiles;
         const int jc = (int)(item / a.n_itiles);
-        const int64_t i = a.i0 + itile * blockDim.x + threadIdx.x;
+        const int64_t ib = a.i0 + itile * kThreads32;
+        const int64_t i = ib + threadIdx.x;
         const bool live = i < a.i1;
         const int64_t ic = live ? i : a.i0;
-        float xh[3], xl[3], vh[3], vl[3], ai[(P >= 2) ? 3 : 1], ji[(P >= 3) ? 3 : 1];
+        float xh[3], xl[3], vh[3], vl[3], ai[3], ji[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             xh[c] = a.jrec32[(0 + c) * a.ld + ic];
             xl[c] = a.jrec32[(3 + c) * a.ld + ic];
             vh[c] = a.jrec32[(6 + c) * a.ld + ic];
             vl[c] = a.jrec32[(9 + c) * a.ld + ic];
-            if constexpr (P >= 2) ai[c] = a.jrec32[(12 + c) * a.ld + ic];
-            if constexpr (P >= 3) ji[c] = a.jrec32[(15 + c) * a.ld + ic];
+            ai[c] = P >= 2 ? a.jrec32[(12 + c) * a.ld + ic] : 0.0f;
+            ji[c] = P >= 3 ? a.jrec32[(15 + c) * a.ld + ic] : 0.0f;
         }
-        double acc64[P + 1][3];
 #pragma unroll
-        for (int k = 0; k <= P; ++k)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) acc64[k][c] = 0.0;
+        for (int q = 0; q < (P + 1) * 3; ++q) acc64[q * kThreads32 + threadIdx.x] = 0.0;
 
         const int64_t jb = (int64_t)jc * a.chunk;
         const int64_t je = min(jb + a.chunk, a.n_j);
         for (int64_t j0 = jb; j0 < je; j0 += tj) {
             __syncthreads();
-            for (int e = threadIdx.x; e < NF * tj; e += blockDim.x) {
+            for (int e = threadIdx.x; e < NF * tj; e += kThreads32) {
                 const int row = e / tj, col = e - row * tj;
                 const int64_t j = j0 + col;
                 sh[col * RS + row] = j < a.n_j ? a.jrec32[row * a.ld + j] : (row < 3 ? (float)kFarAway : 0.0f);
@@ -246,45 +369,25 @@ __global__ void __launch_bounds__(256) k_pair_fp32(PairArgs32<P> a)
             for (int k = 0; k <= P; ++k)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) acc[k][c] = 0.0f;
+            if (j0 < ib + kThreads32 && ib < j0 + tj) {
+                // the tile overlaps this CTA's i-range: guard the i == j pair
 #pragma unroll 2
-            for (int jj = 0; jj < tj; ++jj) {
-                float rec[RS];
-#pragma unroll
-                for (int q4 = 0; q4 < RS / 4; ++q4) {
-                    const float4 t = sh4[jj * (RS / 4) + q4];
-                    rec[4 * q4 + 0] = t.x; rec[4 * q4 + 1] = t.y;
-                    rec[4 * q4 + 2] = t.z; rec[4 * q4 + 3] = t.w;
-                }
-                float r[P + 1][3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    r[0][c] = (rec[c] - xh[c]) + (rec[3 + c] - xl[c]);
-                    r[1][c] = (rec[6 + c] - vh[c]) + (rec[9 + c] - vl[c]);
-                    if constexpr (P >= 2) r[2][c] = rec[12 + c] - ai[c];
-                    if constexpr (P >= 3) r[3][c] = rec[15 + c] - ji[c];
-                }
-                const bool self = (j0 + jj) == ic;
-                float s = fmaf(r[0][0], r[0][0], fmaf(r[0][1], r[0][1], fmaf(r[0][2], r[0][2], a.eps2)));
-                s = self ? 1.0f : s;
-                const float mj = self ? 0.0f : rec[NF - 1];
-                const float rinv = rsqrtf(s);
-                const float sinv = rinv * rinv;
-                const float mS = a.G * mj * (rinv * sinv);
-                float q[P + 1];
-                s_ratios<P, float>(r, sinv, q);
-                pair_terms<P, float>(r, mS, q, acc);
+                for (int jj = 0; jj < tj; ++jj)
+                    interact32<P, true>(sh4, jj, j0 + jj == ic, xh, xl, vh, vl, ai, ji, a.eps2, acc);
+            } else {
+#pragma unroll 2
+                for (int jj = 0; jj < tj; ++jj)
+                    interact32<P, false>(sh4, jj, false, xh, xl, vh, vl, ai, ji, a.eps2, acc);
             }
 #pragma unroll
             for (int k = 0; k <= P; ++k)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) acc64[k][c] += (double)acc[k][c];
+                for (int c = 0; c < 3; ++c) acc64[(3 * k + c) * kThreads32 + threadIdx.x] += (double)acc[k][c];
         }
         if (live) {
             double *out = a.part + (int64_t)jc * (P + 1) * 3 * a.part_ld + (i - a.i0);
 #pragma unroll
-            for (int k = 0; k <= P; ++k)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) out[(3 * k + c) * a.part_ld] = acc64[k][c];
+            for (int q = 0; q < (P + 1) * 3; ++q) out[q * a.part_ld] = acc64[q * kThreads32 + threadIdx.x];
         }
     }
 }
@@ -318,9 +421,7 @@ __global__ void k_pair_heavy(int64_t N, int64_t ld, const double *__restrict__ m
         const double rinv = rsqrt_fp64(s);
         const double sinv = rinv * rinv;
         const double mS = G * __ldg(m + j) * (rinv * sinv);
-        double q[P + 1];
-        s_ratios<P, double>(r, sinv, q);
-        pair_terms<P, double>(r, mS, q, acc);
+        pair_derivs<P, double>(r, mS, sinv, acc);
     }
 #pragma unroll
     for (int k = 0; k <= P; ++k)
@@ -342,12 +443,12 @@ int launch_fp64(const double *jrec, const double *m, int64_t ld, int64_t n_j, do
 }
 
 template <int P>
-int launch_fp32(const float *jrec32, int64_t ld, int64_t n_j, double eps, double G, int64_t i0,
+int launch_fp32(const float *jrec32, int64_t ld, int64_t n_j, double eps, int64_t i0,
                 int64_t i1, double *part, int64_t part_ld, const PairPlan &pl, cudaStream_t st)
 {
-    PairArgs32<P> a{jrec32, ld, n_j, i0, i1, (float)(eps * eps), (float)G, part, part_ld,
+    PairArgs32<P> a{jrec32, ld, n_j, i0, i1, (float)(eps * eps), part, part_ld,
                     pl.n_itiles, pl.chunk, pl.split, pl.tj};
-    const size_t smem = sizeof(float) * Rec32<P>::RS * pl.tj;
+    const size_t smem = sizeof(float) * Rec32<P>::RS * pl.tj + sizeof(double) * (P + 1) * 3 * kThreads32;
     k_pair_fp32<P><<<pl.grid, pl.threads, smem, st>>>(a);
     MH_LAUNCHED("k_pair_fp32");
     return MH_OK;
@@ -381,7 +482,7 @@ PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hin
         if (device >= 0 && device < 64) n_sm_cache[device] = n_sm;
     }
     PairPlan pl{};
-    pl.threads = precision == MH_PREC_FP64 ? 128 : 256;
+    pl.threads = precision == MH_PREC_FP64 ? 128 : kThreads32;
     pl.i_per_cta = pl.threads;
     pl.tj = precision == MH_PREC_FP64 ? 64 : 128;
     const int occ = precision == MH_PREC_FP64 ? 4 : 2;     // resident CTAs per SM
@@ -424,9 +525,10 @@ int launch_pair(int P, int precision, int64_t n_j, int64_t ld, const double *m, 
         }
     } else {
         switch (P) {
-        case 1: return launch_fp32<1>(jrec32, ld, n_j, eps, G, i0, i1, part, part_ld, pl, st);
-        case 2: return launch_fp32<2>(jrec32, ld, n_j, eps, G, i0, i1, part, part_ld, pl, st);
-        case 3: return launch_fp32<3>(jrec32, ld, n_j, eps, G, i0, i1, part, part_ld, pl, st);
+        // the FP32 input rows carry G m: G is applied when they are written
+        case 1: return launch_fp32<1>(jrec32, ld, n_j, eps, i0, i1, part, part_ld, pl, st);
+        case 2: return launch_fp32<2>(jrec32, ld, n_j, eps, i0, i1, part, part_ld, pl, st);
+        case 3: return launch_fp32<3>(jrec32, ld, n_j, eps, i0, i1, part, part_ld, pl, st);
         }
     }
     set_error("launch_pair: unsupported P/precision");
