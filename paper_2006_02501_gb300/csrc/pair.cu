@@ -85,60 +85,46 @@ __device__ __forceinline__ void pair_terms(const T (&r)[P + 1][3], T mS, const T
 }
 
 // The same derivatives for P <= 3 written out with alpha = tau_1/3,
-// beta = tau_2/3, gamma = tau_3/3, the highest term folded into its
-// accumulator (it is not needed by any other term):
+// beta = tau_2/3, gamma = tau_3/3 and scaled terms B_k = A^(k) / (G m S):
 //   alpha = (r.v)/s,  beta = (v.v + r.a)/s + alpha^2,
 //   gamma = (3 v.a + r.adot)/s + alpha (3 beta - 4 alpha^2),
-//   A0 = mS r, A1 = mS v - 3 alpha A0, A2 = mS a - 6 alpha A1 - 3 beta A0,
-//   A3 = mS adot - 9 alpha A2 - 9 beta A1 - 3 gamma A0.
+//   B0 = r, B1 = v - 3 alpha B0, B2 = a - 6 alpha B1 - 3 beta B0,
+//   B3 = adot - 9 alpha B2 - 9 beta B1 - 3 gamma B0,
+// so every term is accumulated by one multiply-add, acc_k += (G m S) B_k.
 template <int P, typename T>
 __device__ __forceinline__ void pair_abg(const T (&r)[P + 1][3], T mS, T sinv, T (&acc)[P + 1][3])
 {
     static_assert(P >= 1 && P <= 3, "pair_abg handles P = 1, 2, 3");
     const T rv = r[0][0] * r[1][0] + r[0][1] * r[1][1] + r[0][2] * r[1][2];
     const T al = rv * sinv;
-    T A0[3], A1[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) A0[c] = mS * r[0][c];
     const T a3 = T(3) * al;
-    if constexpr (P == 1) {
+    T B1[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            acc[0][c] += A0[c];
-            acc[1][c] += mS * r[1][c] - a3 * A0[c];
-        }
-        return;
-    } else {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) A1[c] = mS * r[1][c] - a3 * A0[c];
+    for (int c = 0; c < 3; ++c) {
+        B1[c] = r[1][c] - a3 * r[0][c];
+        acc[0][c] += mS * r[0][c];
+        acc[1][c] += mS * B1[c];
+    }
+    if constexpr (P >= 2) {
         const T al2 = al * al;
         const T w2 = r[1][0] * r[1][0] + r[1][1] * r[1][1] + r[1][2] * r[1][2]
                    + r[0][0] * r[2][0] + r[0][1] * r[2][1] + r[0][2] * r[2][2];
         const T be = w2 * sinv + al2;
         const T a6 = T(6) * al, b3 = T(3) * be;
-        if constexpr (P == 2) {
+        T B2[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                acc[0][c] += A0[c];
-                acc[1][c] += A1[c];
-                acc[2][c] += mS * r[2][c] - a6 * A1[c] - b3 * A0[c];
-            }
-            return;
-        } else {
-            T A2[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) A2[c] = mS * r[2][c] - a6 * A1[c] - b3 * A0[c];
+        for (int c = 0; c < 3; ++c) {
+            B2[c] = r[2][c] - a6 * B1[c] - b3 * r[0][c];
+            acc[2][c] += mS * B2[c];
+        }
+        if constexpr (P >= 3) {
             const T va = r[1][0] * r[2][0] + r[1][1] * r[2][1] + r[1][2] * r[2][2];
             const T w3 = T(3) * va + r[0][0] * r[3][0] + r[0][1] * r[3][1] + r[0][2] * r[3][2];
             const T ga = w3 * sinv + al * (b3 - T(4) * al2);
             const T a9 = T(9) * al, b9 = T(9) * be, g3 = T(3) * ga;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                acc[0][c] += A0[c];
-                acc[1][c] += A1[c];
-                acc[2][c] += A2[c];
-                acc[3][c] += mS * r[3][c] - a9 * A2[c] - b9 * A1[c] - g3 * A0[c];
-            }
+            for (int c = 0; c < 3; ++c)
+                acc[3][c] += mS * (r[3][c] - a9 * B2[c] - b9 * B1[c] - g3 * r[0][c]);
         }
     }
 }
