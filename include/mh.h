@@ -65,8 +65,8 @@ typedef struct {
     int step_mode;      /* MH_STEP_SHARED or MH_STEP_BLOCK */
     double G;           /* gravitational constant (default 1) */
     double eta;         /* block steps: accuracy parameter of the per-particle criterion */
-    double dt_max;      /* block steps: largest step (levels are dt_max * 2^-k) */
-    int k_max;          /* block steps: deepest level, 0 <= k_max <= 20 (default 12) */
+    double dt_max;      /* block steps: largest step (levels are dt_max * 2^-k, default 1/32) */
+    int k_max;          /* block steps: deepest level, 0 <= k_max <= 30 (default 12) */
     int split_j;        /* pair kernel: j-range split factor, 0 = automatic */
     double heavy_frac;  /* precision form only: pairs whose source body j has
                            m_j >= heavy_frac * (total mass) are evaluated in FP64
@@ -82,6 +82,7 @@ typedef struct {
     double *x;          /* N x 3 */
     double *v;          /* N x 3 */
     double *derivs;     /* N x 2p x 3 */
+    int32_t *level;     /* block steps: N levels (step dt_max 2^-level); ignored otherwise */
 } mh_state;
 
 /* Per-handle counters (cumulative since creation). */
@@ -116,7 +117,16 @@ void mh_destroy(mh_sim *sim);
  * with one Taylor prediction and n_iter >= 1 evaluate-correct passes, P(EC)^n.
  * The derivatives a^(0..p) kept for the next step are those of the n-th
  * evaluation; a^(p+1..2p-1) come from Hermite interpolation.
- * Block mode: advance the block scheme until time t + dt. */
+ * Block mode (step_mode = MH_STEP_BLOCK, order 6 or 8; Section 4 names block
+ * steps as an option): dt must be a positive multiple of cfg.dt_max.  Every body
+ * has its own level k (step dt_max 2^-k, 0 <= k <= k_max) and time; each block
+ * step predicts all bodies to the earliest next time, runs n_iter
+ * evaluate-correct passes on the bodies due then (the active list), and gives
+ * them a new level from dt = eta sqrt((|a||a2| + |a1|^2) / (|a1||a3| + |a2|^2)):
+ * a step may halve freely and double only when the body's time is a multiple of
+ * the doubled step.  All bodies meet again at every multiple of dt_max, so on
+ * return the whole system is at t + dt.  One 16-byte device-to-host read per
+ * block step sizes the evaluation of the active list. */
 int mh_step(mh_sim *sim, double dt, int n_iter);
 
 /* Copy the current state to host buffers (waits for queued work). */

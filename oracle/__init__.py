@@ -65,6 +65,13 @@ def _lib_handle():
             lib.orc_ecc.argtypes = [i, _D, _D, _D, d, i, _D]
             lib.orc_timestep_H.argtypes = [i, _D, _D, d, d]
             lib.orc_timestep_H.restype = d
+            LL = ctypes.POINTER(ctypes.c_longlong)
+            IP = ctypes.POINTER(ctypes.c_int)
+            lib.orc_aarseth_dt.argtypes = [_D, d]
+            lib.orc_aarseth_dt.restype = d
+            lib.orc_block_level.argtypes = [d, d, i, i, ctypes.c_longlong]
+            lib.orc_block_init_levels.argtypes = [i, i, _D, d, d, i, IP]
+            lib.orc_block_step.argtypes = [i, i, i, i, d, i, d, _D, d, d, _D, _D, _D, LL, IP, LL]
             _lib = lib
     return _lib
 
@@ -220,3 +227,59 @@ def ecc(m, x, v, G: float = 1.0, central: int = 0) -> np.ndarray:
 def timestep_H(m, x, eps: float, eta: float) -> float:
     m, x = _f64(m), _f64(x)
     return _lib_handle().orc_timestep_H(m.shape[0], _p(m), _p(x), eps, eta)
+
+
+# --------------------------------------------------------------------------- #
+# block time steps (Section 4 option; scheme of reading R12)
+# --------------------------------------------------------------------------- #
+
+def aarseth_dt(d, eta: float) -> float:
+    d = _f64(d).reshape(-1, 3)
+    return _lib_handle().orc_aarseth_dt(_p(d), eta)
+
+
+def block_level(dt_c: float, dt_max: float, k_max: int, k_old: int = -1, T: int = 0) -> int:
+    return _lib_handle().orc_block_level(dt_c, dt_max, k_max, k_old, T)
+
+
+class BlockState(State):
+    """Oracle state advanced by block time steps: every body has its own tick
+    T (units of dt_max 2^-k_max) and level (step dt_max 2^-level)."""
+
+    def __init__(self, order: int, m, x, v, eps: float, dt_max: float, k_max: int, eta: float,
+                 G: float = 1.0, modified: bool = True, derivs=None, level=None):
+        super().__init__(order, m, x, v, eps, G=G, derivs=derivs, modified=modified)
+        if self.p < 2:
+            raise ValueError("block steps need order 6 or 8")
+        self.dt_max, self.k_max, self.eta = float(dt_max), int(k_max), float(eta)
+        self.T = np.zeros(self.N, dtype=np.int64)
+        if level is None:
+            self.level = np.zeros(self.N, dtype=np.int32)
+            _lib_handle().orc_block_init_levels(self.N, self.p, _p(self.derivs), self.eta, self.dt_max,
+                                                self.k_max, self.level.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        else:
+            self.level = np.ascontiguousarray(level, dtype=np.int32).copy()
+        self.block_steps = 0
+        self.active_total = 0
+
+    @property
+    def tick(self) -> float:
+        return self.dt_max * 2.0 ** -self.k_max
+
+    def block_step(self, n_iter: int) -> int:
+        Tn = ctypes.c_longlong(0)
+        n_act = _lib_handle().orc_block_step(
+            self.N, self.p, 0 if self.modified else 1, n_iter, self.dt_max, self.k_max, self.eta,
+            _p(self.m), self.eps, self.G, _p(self.x), _p(self.v), _p(self.derivs),
+            self.T.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+            self.level.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.byref(Tn))
+        self.block_steps += 1
+        self.active_total += n_act
+        self.t = Tn.value * self.tick
+        return n_act
+
+    def advance(self, dt: float, n_iter: int) -> None:
+        """Block steps until every body reaches the current time + dt (a multiple of dt_max)."""
+        target = int(round((self.T.max() * self.tick + dt) / self.tick))
+        while self.T.min() < target:
+            self.block_step(n_iter)

@@ -40,6 +40,7 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#include <limits.h>
 
 #define ORC_MAXP 5           /* highest acceleration derivative supported in a pair */
 #define ORC_MAXSYS 8         /* largest Pascal sub-system (p+2 for p <= 6) */
@@ -487,4 +488,129 @@ double orc_timestep_H(int N, const double *m, const double *x, double eps, doubl
             if (q < best) best = q;
         }
     return eta * best;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Block time steps (Section 4 names the option; the scheme below is the     */
+/* reading recorded in the design notes, R12)                                 */
+/* ------------------------------------------------------------------------- */
+
+/* Aarseth-type step estimate from a, a-dot, a^(2), a^(3) of one body:
+ *   dt = eta sqrt((|a||a2| + |a1|^2) / (|a1||a3| + |a2|^2)).                 */
+double orc_aarseth_dt(const double *d, double eta)
+{
+    const double a0 = sqrt(dot3(d, d)), a1 = sqrt(dot3(d + 3, d + 3));
+    const double a2 = sqrt(dot3(d + 6, d + 6)), a3 = sqrt(dot3(d + 9, d + 9));
+    return eta * sqrt((a0 * a2 + a1 * a1) / (a1 * a3 + a2 * a2));
+}
+
+/* Level for a body with estimate dt_c: the smallest k in [0, k_max] with
+ * dt_max 2^-k <= dt_c (k_max if none).  From level k_old at tick T (ticks of
+ * dt_max 2^-k_max) the step may shrink freely but grows by at most one level,
+ * and only when T is a multiple of the grown step.  k_old < 0: no constraint. */
+int orc_block_level(double dt_c, double dt_max, int k_max, int k_old, long long T)
+{
+    int k = 0;
+    while (k < k_max && dt_max * ldexp(1.0, -k) > dt_c) ++k;
+    if (k_old < 0 || k >= k_old) return k;
+    const int kg = k_old - 1;                      /* grow by one level at most */
+    const long long span = 1LL << (k_max - kg);
+    return (T % span == 0) ? kg : k_old;
+}
+
+/* Initial levels at T = 0 from the initial derivatives (N x K x 3, K = 2p >= 4). */
+void orc_block_init_levels(int N, int p, const double *derivs, double eta, double dt_max,
+                           int k_max, int *level)
+{
+    const int K = 2 * p;
+    for (int i = 0; i < N; ++i)
+        level[i] = orc_block_level(orc_aarseth_dt(derivs + (size_t)i * K * 3, eta), dt_max, k_max, -1, 0);
+}
+
+/* One block step (p >= 2).  Every body i lives at its own tick T[i] with level
+ * level[i] (step dt_max 2^-level).  The next block time is
+ * T_next = min_i (T[i] + 2^(k_max - level[i])); the bodies reaching it are
+ * active.  All bodies are predicted to T_next by their Taylor series; the
+ * active ones then take n_iter evaluate-correct passes with their own step
+ * (inactive sources keep their predicted values, active sources their latest
+ * corrected x, v and, from the second pass on, the a, a-dot of the previous
+ * evaluation), followed by the interpolation of their higher derivatives, the
+ * commit T[i] = T_next and a new level.  Returns the number of active bodies;
+ * *T_out receives T_next.                                                    */
+int orc_block_step(int N, int p, int beta_mode, int n_iter, double dt_max, int k_max,
+                   double eta, const double *m, double eps, double G, double *x, double *v,
+                   double *derivs, long long *T, int *level, long long *T_out)
+{
+    const int K = 2 * p;
+    const int P = p;
+    const int na = p - 1;
+    const double tick = dt_max * ldexp(1.0, -k_max);
+    double cv[ORC_MAXSYS], cx[ORC_MAXSYS];
+    orc_corrector_weights(p, beta_mode, cv, cx);
+
+    long long Tn = LLONG_MAX;
+    for (int i = 0; i < N; ++i) {
+        const long long t = T[i] + (1LL << (k_max - level[i]));
+        if (t < Tn) Tn = t;
+    }
+    int *act = (int *)malloc((size_t)N * sizeof(int));
+    int n_act = 0;
+    for (int i = 0; i < N; ++i)
+        if (T[i] + (1LL << (k_max - level[i])) == Tn) act[n_act++] = i;
+
+    /* prediction of every body to T_next */
+    double *tr = (double *)malloc((size_t)N * (P + 1) * 3 * sizeof(double));
+    double *ap = (double *)malloc((size_t)(na > 0 ? na : 1) * 3 * sizeof(double));
+    for (int i = 0; i < N; ++i) {
+        double *t = tr + (size_t)i * (P + 1) * 3;
+        predict_one(p, (double)(Tn - T[i]) * tick, x + 3 * i, v + 3 * i, derivs + (size_t)i * K * 3,
+                    t, t + 3, ap);
+        for (int q = 0; q < na; ++q)
+            for (int c = 0; c < 3; ++c) t[(q + 2) * 3 + c] = ap[q * 3 + c];
+    }
+    double *d1 = (double *)malloc((size_t)n_act * (P + 1) * 3 * sizeof(double));
+    double *one = (double *)malloc((size_t)(P + 1) * 3 * sizeof(double));
+    double *x1 = (double *)malloc((size_t)n_act * 3 * sizeof(double));
+    double *v1 = (double *)malloc((size_t)n_act * 3 * sizeof(double));
+    for (int it = 0; it < n_iter; ++it) {
+        for (int q = 0; q < n_act; ++q) {
+            orc_evaluate(N, P, m, tr, eps, G, act[q], act[q] + 1, one);
+            memcpy(d1 + (size_t)q * (P + 1) * 3, one, (size_t)(P + 1) * 3 * sizeof(double));
+        }
+        for (int q = 0; q < n_act; ++q) {
+            const int i = act[q];
+            const double dt = (double)(Tn - T[i]) * tick;
+            double d0[(ORC_MAXP + 1) * 3];
+            for (int k = 0; k <= P; ++k)
+                for (int c = 0; c < 3; ++c) d0[k * 3 + c] = derivs[((size_t)i * K + k) * 3 + c];
+            correct_one(p, dt, cv, cx, x + 3 * i, v + 3 * i, d0, d1 + (size_t)q * (P + 1) * 3,
+                        x1 + 3 * q, v1 + 3 * q);
+        }
+        /* the active bodies' new estimates become the evaluation inputs (R2) */
+        for (int q = 0; q < n_act; ++q) {
+            double *t = tr + (size_t)act[q] * (P + 1) * 3;
+            for (int c = 0; c < 3; ++c) { t[c] = x1[q * 3 + c]; t[3 + c] = v1[q * 3 + c]; }
+            for (int k = 0; k + 2 <= P; ++k)
+                for (int c = 0; c < 3; ++c) t[(k + 2) * 3 + c] = d1[((size_t)q * (P + 1) + k) * 3 + c];
+        }
+    }
+    for (int q = 0; q < n_act; ++q) {
+        const int i = act[q];
+        const double dt = (double)(Tn - T[i]) * tick;
+        double d0[(ORC_MAXP + 1) * 3], hi[2 * ORC_MAXSYS * 3];
+        const double *e1 = d1 + (size_t)q * (P + 1) * 3;
+        for (int k = 0; k <= P; ++k)
+            for (int c = 0; c < 3; ++c) d0[k * 3 + c] = derivs[((size_t)i * K + k) * 3 + c];
+        orc_hermite_interp(p, dt, d0, e1, K, hi);
+        for (int k = 0; k < K; ++k)
+            for (int c = 0; c < 3; ++c)
+                derivs[((size_t)i * K + k) * 3 + c] = (k <= P) ? e1[k * 3 + c] : hi[k * 3 + c];
+        for (int c = 0; c < 3; ++c) { x[3 * i + c] = x1[q * 3 + c]; v[3 * i + c] = v1[q * 3 + c]; }
+        T[i] = Tn;
+        level[i] = orc_block_level(orc_aarseth_dt(derivs + (size_t)i * K * 3, eta), dt_max, k_max,
+                                   level[i], Tn);
+    }
+    free(act); free(tr); free(ap); free(d1); free(one); free(x1); free(v1);
+    *T_out = Tn;
+    return n_act;
 }

@@ -58,12 +58,14 @@ class Simulation:
     MH_BETA_MODIFIED (Eq. 20) or MH_BETA_STANDARD (beta = 1); stream: a
     torch.cuda.Stream, a raw cudaStream_t integer, or None (library stream);
     heavy_frac: precision form, mass fraction above which a source body's
-    pairs run in FP64 (None = library default 1e-3, 0 = all pairs FP32).
+    pairs run in FP64 (None = library default 1e-3, 0 = all pairs FP32);
+    block: None for shared steps, or {"dt_max", "k_max", "eta"} for block time
+    steps (order 6 or 8; step() then needs a multiple of dt_max).
     """
 
     def __init__(self, order: int, m, x, v, eps: float, precision: int = MH_PREC_FP64,
                  beta: int = MH_BETA_MODIFIED, G: float = 1.0, stream=None, split_j: int = 0,
-                 heavy_frac: float | None = None):
+                 heavy_frac: float | None = None, block: dict | None = None):
         L = _capi.lib()
         m = _host(m)
         N = m.shape[0]
@@ -73,12 +75,18 @@ class Simulation:
         cfg.order, cfg.precision, cfg.beta_mode, cfg.G, cfg.split_j = order, precision, beta, G, split_j
         if heavy_frac is not None:
             cfg.heavy_frac = heavy_frac
+        if block is not None:
+            cfg.step_mode = _capi.MH_STEP_BLOCK
+            cfg.dt_max = float(block.get("dt_max", cfg.dt_max))
+            cfg.k_max = int(block.get("k_max", cfg.k_max))
+            cfg.eta = float(block.get("eta", cfg.eta))
         h = ctypes.c_void_p()
         check(L.mh_create(ctypes.byref(h), N, order, _ptr(m), _ptr(x), _ptr(v), float(eps),
                           ctypes.byref(cfg), _stream_handle(stream)))
         self._h = h
         self.N, self.order, self.p = N, order, order // 2 - 1
         self.eps, self.G, self.precision = eps, G, precision
+        self.block = block is not None
 
     def close(self) -> None:
         if getattr(self, "_h", None):
@@ -107,17 +115,27 @@ class Simulation:
         x = np.zeros((self.N, 3))
         v = np.zeros((self.N, 3))
         d = np.zeros((self.N, 2 * self.p, 3))
-        st = _capi.StateC(0.0, _ptr(x), _ptr(v), _ptr(d))
+        st = _capi.StateC(0.0, _ptr(x), _ptr(v), _ptr(d), None)
         check(_capi.lib().mh_sync(self._h, ctypes.byref(st)))
         return st.t, x, v, d
 
-    def set_state(self, x, v, derivs=None, t: float = 0.0) -> None:
+    def levels(self) -> np.ndarray:
+        """Block steps: the level of every body (step dt_max 2^-level)."""
+        lv = np.zeros(self.N, dtype=np.int32)
+        st = _capi.StateC(0.0, None, None, None, lv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        check(_capi.lib().mh_sync(self._h, ctypes.byref(st)))
+        return lv
+
+    def set_state(self, x, v, derivs=None, t: float = 0.0, level=None) -> None:
         x, v = _host(x, (self.N, 3)), _host(v, (self.N, 3))
-        dp = None
+        dp = lp = None
         if derivs is not None:
             derivs = _host(derivs, (self.N, 2 * self.p, 3))
             dp = _ptr(derivs)
-        st = _capi.StateC(float(t), _ptr(x), _ptr(v), dp)
+        if level is not None:
+            level = np.ascontiguousarray(level, dtype=np.int32)
+            lp = level.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        st = _capi.StateC(float(t), _ptr(x), _ptr(v), dp, lp)
         check(_capi.lib().mh_set_state(self._h, ctypes.byref(st)))
 
     def diagnostics(self, central: int = 0, energy: bool = True, ecc: bool = True):

@@ -42,7 +42,8 @@ class Config(ctypes.Structure):
 
 class StateC(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("x", ctypes.POINTER(ctypes.c_double)),
-                ("v", ctypes.POINTER(ctypes.c_double)), ("derivs", ctypes.POINTER(ctypes.c_double))]
+                ("v", ctypes.POINTER(ctypes.c_double)), ("derivs", ctypes.POINTER(ctypes.c_double)),
+                ("level", ctypes.POINTER(ctypes.c_int32))]
 
 
 class Counters(ctypes.Structure):

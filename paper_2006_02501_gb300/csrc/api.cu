@@ -44,9 +44,10 @@ int dalloc(T **ptr, size_t count)
 void free_state(DeviceState &s)
 {
     void *ptrs[] = {s.m, s.x0, s.v0, s.d0, s.x1, s.v1, s.jrec, s.jrec32, s.part, s.diag, s.flag, s.bound,
-                    s.heavy};
+                    s.heavy, s.T, s.level, s.act, s.blk};
     for (void *q : ptrs)
         if (q) cudaFree(q);
+    if (s.blk_host) cudaFreeHost(s.blk_host);
     s = DeviceState{};
 }
 
@@ -238,7 +239,14 @@ int mh_create(mh_sim **out, int64_t N, int order, const double *m, const double 
     if (!(eps >= 0.0) || !std::isfinite(eps)) { set_error("mh_create: eps must be finite and >= 0"); return MH_EINVAL; }
     if (c.precision != MH_PREC_FP64 && c.precision != MH_PREC_FP32PAIR) { set_error("mh_create: bad precision"); return MH_EINVAL; }
     if (c.beta_mode != MH_BETA_MODIFIED && c.beta_mode != MH_BETA_STANDARD) { set_error("mh_create: bad beta_mode"); return MH_EINVAL; }
-    if (c.step_mode != MH_STEP_SHARED) { set_error("mh_create: block steps are created with step_mode = MH_STEP_BLOCK through mh_create_block"); return MH_EINVAL; }
+    if (c.step_mode != MH_STEP_SHARED && c.step_mode != MH_STEP_BLOCK) { set_error("mh_create: bad step_mode"); return MH_EINVAL; }
+    if (c.step_mode == MH_STEP_BLOCK) {
+        if (p < 2) { set_error("mh_create: block steps need order 6 or 8"); return MH_EINVAL; }
+        if (!(c.dt_max > 0.0) || !std::isfinite(c.dt_max) || c.k_max < 0 || c.k_max > 30 || !(c.eta > 0.0)) {
+            set_error("mh_create: block steps need dt_max > 0, 0 <= k_max <= 30, eta > 0");
+            return MH_EINVAL;
+        }
+    }
     for (int64_t i = 0; i < N; ++i) {
         if (!std::isfinite(m[i]) || m[i] < 0.0) { set_error("mh_create: masses must be finite and >= 0"); return MH_EINVAL; }
         for (int q = 0; q < 3; ++q)
@@ -274,6 +282,13 @@ int mh_create(mh_sim **out, int64_t N, int order, const double *m, const double 
     if (c.precision == MH_PREC_FP32PAIR &&
         ((rc = dalloc(&s.jrec32, (size_t)nf32(p) * s.Np)) || (rc = dalloc(&s.bound, 4))))
         return fail(rc);
+    if (c.step_mode == MH_STEP_BLOCK) {
+        if ((rc = dalloc(&s.T, s.Np)) || (rc = dalloc(&s.level, s.Np)) || (rc = dalloc(&s.act, s.Np)) ||
+            (rc = dalloc(&s.blk, 2)))
+            return fail(rc);
+        cudaError_t eh = cudaMallocHost((void **)&s.blk_host, 2 * sizeof(unsigned long long));
+        if (eh != cudaSuccess) return fail(cuda_fail(eh, "cudaMallocHost"));
+    }
 
     std::vector<double> h;
     h.assign(s.Np, 0.0);
@@ -323,6 +338,7 @@ int mh_create(mh_sim **out, int64_t N, int order, const double *m, const double 
     if (e != cudaSuccess) return fail(cuda_fail(e, "upload state"));
     if ((rc = upload_bounds(s, x, v, sim->stream))) return fail(rc);
     if ((rc = initialise(sim))) return fail(rc);
+    if (c.step_mode == MH_STEP_BLOCK && (rc = launch_block_init(s, c, sim->stream))) return fail(rc);
     e = cudaStreamSynchronize(sim->stream);
     if (e != cudaSuccess) return fail(cuda_fail(e, "initialisation"));
     *out = sim;
@@ -343,11 +359,79 @@ void mh_destroy(mh_sim *sim)
     delete sim;
 }
 
+static int block_advance(mh_sim *sim, double dt, int n_iter)
+{
+    DeviceState &s = sim->s;
+    const mh_config &c = sim->cfg;
+    const double q = dt / c.dt_max;
+    const long long nq = std::llround(q);
+    if (!(dt > 0.0) || nq < 1 || std::fabs(q - (double)nq) > 1e-9 * std::max(1.0, q)) {
+        set_error("mh_step: in block mode dt must be a positive multiple of dt_max");
+        return MH_EINVAL;
+    }
+    const long long span0 = 1LL << c.k_max;
+    const long long target = s.T_now + nq * span0;
+    const int prec = c.precision;
+    for (;;) {
+        if (int rc = launch_block_schedule(s, c, sim->stream)) return rc;
+        MH_CUDA(cudaMemcpyAsync(s.blk_host, s.blk, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                sim->stream));
+        MH_CUDA(cudaStreamSynchronize(sim->stream));
+        const long long T_next = (long long)s.blk_host[0];
+        const int64_t n_act = (int64_t)s.blk_host[1];
+        sim->ctr.kernel_launches += 3;
+        if (n_act < 1 || T_next > target) {
+            set_error("mh_step: block schedule out of order (levels corrupted?)");
+            return MH_EINVAL;
+        }
+        if (int rc = launch_block_phase(s, c, T_next, n_act, 0, false, 0, sim->stream)) return rc;
+        s.flip ^= 1;
+        sim->ctr.kernel_launches += 1;
+        for (int it = 0; it < n_iter; ++it) {
+            const PairPlan pl = plan_pair(s.p, prec, n_act, s.N, c.split_j, sim->device);
+            const bool heavy = prec == MH_PREC_FP32PAIR && s.n_heavy > 0;
+            const int slots = pl.split + (heavy ? 1 : 0);
+            if (int rc = ensure_part(s, (size_t)slots * (s.p + 1) * 3 * s.Np, sim->stream)) return rc;
+            std::pair<cudaEvent_t, cudaEvent_t> ev{};
+            if (sim->timing) {
+                if (int rc = timed_event_pair(sim, &ev)) return rc;
+                MH_CUDA(cudaEventRecord(ev.first, sim->stream));
+            }
+            if (int rc = launch_pair(s.p, prec, s.N, s.Np, s.m, s.jrec, s.jrec32, sim->eps, c.G, 0, n_act,
+                                     s.part, s.Np, pl, sim->stream, s.act))
+                return rc;
+            if (sim->timing) {
+                MH_CUDA(cudaEventRecord(ev.second, sim->stream));
+                sim->ev_pending.push_back(ev);
+            }
+            if (heavy) {
+                if (int rc = launch_pair_heavy(s.p, n_act, s.Np, s.m, s.jrec, s.heavy, s.n_heavy, sim->eps, c.G,
+                                               s.part, pl.split, sim->stream, s.act))
+                    return rc;
+                sim->ctr.kernel_launches += 1;
+            }
+            const bool last = it == n_iter - 1;
+            if (int rc = launch_block_phase(s, c, T_next, n_act, 1, last, slots, sim->stream)) return rc;
+            if (!last) s.flip ^= 1;
+            sim->ctr.kernel_launches += 2;
+            sim->ctr.evaluations += 1;
+            sim->ctr.pair_interactions += (double)n_act * (double)(s.N - 1);
+        }
+        sim->ctr.particle_steps += (double)n_act;
+        s.T_now = T_next;
+        if (T_next == target) break;
+    }
+    sim->t += dt;
+    sim->ctr.steps += 1;
+    return MH_OK;
+}
+
 int mh_step(mh_sim *sim, double dt, int n_iter)
 {
     if (int rc = check_handle(sim)) return rc;
     if (!(dt != 0.0) || !std::isfinite(dt)) { set_error("mh_step: dt must be finite and non-zero"); return MH_EINVAL; }
     if (n_iter < 1 || n_iter > 64) { set_error("mh_step: n_iter must be in [1, 64]"); return MH_EINVAL; }
+    if (sim->cfg.step_mode == MH_STEP_BLOCK) return block_advance(sim, dt, n_iter);
     DeviceState &s = sim->s;
     const int prec = sim->cfg.precision;
     int rc = launch_step_phase(s, sim->cfg, dt, 0, false, 0, sim->stream);
@@ -405,6 +489,7 @@ int mh_sync(mh_sim *sim, mh_state *out)
         MH_CUDA(cudaMemcpy(h.data(), s.d0, (size_t)K * 3 * s.Np * sizeof(double), cudaMemcpyDeviceToHost));
         from_soa(h, s.N, K, s.Np, out->derivs);
     }
+    if (out->level && s.level) MH_CUDA(cudaMemcpy(out->level, s.level, s.N * sizeof(int), cudaMemcpyDeviceToHost));
     return check_flag(sim);
 }
 
@@ -425,10 +510,22 @@ int mh_set_state(mh_sim *sim, const mh_state *in)
     if (in->derivs) {
         to_soa(in->derivs, s.N, 2 * s.p, s.Np, h, 0.0);
         MH_CUDA(cudaMemcpy(s.d0, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
-        return MH_OK;
+    } else if (int rc = initialise(sim)) {
+        return rc;
     }
-    int rc = initialise(sim);
-    if (rc) return rc;
+    if (sim->cfg.step_mode == MH_STEP_BLOCK) {
+        // every body restarts at the given time; levels from the caller or the criterion
+        s.T_now = 0;
+        if (int rc = launch_block_init(s, sim->cfg, sim->stream)) return rc;
+        if (in->level) {
+            for (int64_t i = 0; i < s.N; ++i)
+                if (in->level[i] < 0 || in->level[i] > sim->cfg.k_max) {
+                    set_error("mh_set_state: level out of [0, k_max]");
+                    return MH_EINVAL;
+                }
+            MH_CUDA(cudaMemcpyAsync(s.level, in->level, s.N * sizeof(int), cudaMemcpyHostToDevice, sim->stream));
+        }
+    }
     MH_CUDA(cudaStreamSynchronize(sim->stream));
     return MH_OK;
 }

@@ -72,6 +72,14 @@ struct DeviceState {
     // Precision form: source bodies whose pairs are evaluated in FP64.
     int n_heavy = 0;
     int *heavy = nullptr;     // [n_heavy] body indices (device)
+    // Block time steps: per-body tick and level, the active list, and the
+    // device words [next block tick, active count] read back once per block step.
+    long long *T = nullptr;
+    int *level = nullptr;
+    int *act = nullptr;
+    unsigned long long *blk = nullptr;
+    unsigned long long *blk_host = nullptr;   // pinned host mirror of blk
+    long long T_now = 0;
 };
 
 constexpr int kMaxHeavy = 32;
@@ -98,14 +106,20 @@ namespace mh {
 // Evaluation: fills part[0..S) with a^(0..P) partial sums of bodies i0 <= i < i1
 // from bodies 0 <= j < n_j.  Input rows have stride ld: jrec (FP64, 3(P+1) rows)
 // with masses m, or jrec32 (precision form, nf32(P) rows, mass last).
+// ilist (optional, device): position i in [i0, i1) evaluates body ilist[i]; the
+// partial sums are stored by position.
 int launch_pair(int P, int precision, int64_t n_j, int64_t ld, const double *m, const double *jrec,
                 const float *jrec32, double eps, double G, int64_t i0, int64_t i1, double *part,
-                int64_t part_ld, const PairPlan &plan, cudaStream_t st);
+                int64_t part_ld, const PairPlan &plan, cudaStream_t st, const int *ilist = nullptr);
 
 // O(N) step kernels (integrator.cu): phase 0 = predict, 1 = correct.
 int launch_step_phase(const DeviceState &s, const mh_config &cfg, double dt, int phase, bool last,
                       int split, cudaStream_t st);
 int launch_init_rows(const DeviceState &s, int have, cudaStream_t st);
+int launch_block_init(const DeviceState &s, const mh_config &cfg, cudaStream_t st);
+int launch_block_schedule(const DeviceState &s, const mh_config &cfg, cudaStream_t st);
+int launch_block_phase(const DeviceState &s, const mh_config &cfg, long long T_next, int64_t n_act,
+                       int phase, bool last, int split, cudaStream_t st);
 int launch_init_reduce(const DeviceState &s, int nr, int lo, int hi, int split, cudaStream_t st);
 int launch_reduce_out(int64_t n, int64_t ld_part, int nr, int split, const double *part, double *out,
                       cudaStream_t st);
@@ -143,7 +157,7 @@ PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hin
 // to partial slot `slot` (rows (P+1)*3 of stride ld) of part.
 int launch_pair_heavy(int P, int64_t N, int64_t ld, const double *m, const double *jrec,
                       const int *heavy, int n_heavy, double eps, double G, double *part, int slot,
-                      cudaStream_t st);
+                      cudaStream_t st, const int *ilist = nullptr);
 
 // Number of FP32 rows of the precision-form evaluation input for a given P.
 __host__ __device__ constexpr int nf32(int P) { return 12 + 3 * (P >= 2) + 3 * (P >= 3) + 1; }

@@ -131,6 +131,54 @@ __global__ void k_predict(StepArgs a)
     if (live) write_input<p>(a, i, x, v, ad);
 }
 
+// Corrector of one component (velocity, Eq. 6, then position with the new
+// velocity, Eq. 7): d0 = a^(0..2p-1) at t0, d1 = a^(0..p) at t1.
+template <int p>
+__device__ __forceinline__ void correct_comp(double dt, int bm, const double (&d0)[2 * p],
+                                             const double (&d1)[p + 1], double x0, double v0,
+                                             double &xn, double &vn)
+{
+    // velocity (Eq. 6): sum_k kv(k) (a1^(k) + (-1)^k a0^(k)) dt^(k+1)
+    double sv = 0.0;
+#pragma unroll
+    for (int k = p; k >= 0; --k) {
+        const double f = (k & 1) ? d1[k] - d0[k] : d1[k] + d0[k];
+        sv = fma(sv, dt, kv<p>(k) * f);
+    }
+    vn = fma(sv, dt, v0);
+    // position (Eq. 7): kx(0) (v1 + v0) dt + sum_{k>=1} kx(k) (a1^(k-1) +- a0^(k-1)) dt^(k+1)
+    double sx = 0.0;
+#pragma unroll
+    for (int k = p + 1; k >= 1; --k) {
+        const double f = (k & 1) ? d1[k - 1] - d0[k - 1] : d1[k - 1] + d0[k - 1];
+        sx = fma(sx, dt, (bm == 0 ? kx<p>(0, k) : kx<p>(1, k)) * f);
+    }
+    sx = fma(sx, dt, (bm == 0 ? kx<p>(0, 0) : kx<p>(1, 0)) * (vn + v0));
+    xn = fma(sx, dt, x0);
+}
+
+// a^(p+1..2p-1)(t1) of one component from the degree-(2p+1) Hermite interpolant:
+// a^(n)(t1) = sum_k (e1(n,k) a1^(k) + e0(n,k) a0^(k)) dt^(k-n).
+template <int p>
+__device__ __forceinline__ void interp_comp(double dt, const double (&d0)[2 * p],
+                                            const double (&d1)[p + 1],
+                                            double (&hi)[2 * p > p + 1 ? p - 1 : 1])
+{
+    if constexpr (p >= 2) {
+        const double rdt = 1.0 / dt;
+#pragma unroll
+        for (int n = p + 1; n < 2 * p; ++n) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = p; k >= 0; --k) s = fma(s, dt, fma(e1<p>(n, k), d1[k], e0<p>(n, k) * d0[k]));
+            double sc = 1.0;
+#pragma unroll
+            for (int e = 0; e < n; ++e) sc *= rdt;
+            hi[n - p - 1] = s * sc;
+        }
+    }
+}
+
 template <int p, bool kLast>
 __global__ void k_correct(StepArgs a)
 {
@@ -140,7 +188,6 @@ __global__ void k_correct(StepArgs a)
     const bool live = i0 < a.N;
     const int64_t i = live ? i0 : a.N - 1;      // idle lanes recompute the last body, store nothing
     const double dt = a.dt;
-    const int bm = a.beta_mode;
     double x[3], v[3], ad[p > 1 ? p - 1 : 1][3];
     bool finite = true;
 #pragma unroll
@@ -154,24 +201,8 @@ __global__ void k_correct(StepArgs a)
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) d0[k] = a.d0[(3 * k + c) * a.ld + i];
-        const double x0 = a.x0[c * a.ld + i], v0 = a.v0[c * a.ld + i];
-        // velocity (Eq. 6): sum_k kv(k) (a1^(k) + (-1)^k a0^(k)) dt^(k+1)
-        double sv = 0.0;
-#pragma unroll
-        for (int k = p; k >= 0; --k) {
-            const double f = (k & 1) ? d1[k] - d0[k] : d1[k] + d0[k];
-            sv = fma(sv, dt, kv<p>(k) * f);
-        }
-        const double vn = fma(sv, dt, v0);
-        // position (Eq. 7): kx(0) (v1 + v0) dt + sum_{k>=1} kx(k) (a1^(k-1) +- a0^(k-1)) dt^(k+1)
-        double sx = 0.0;
-#pragma unroll
-        for (int k = p + 1; k >= 1; --k) {
-            const double f = (k & 1) ? d1[k - 1] - d0[k - 1] : d1[k - 1] + d0[k - 1];
-            sx = fma(sx, dt, (bm == 0 ? kx<p>(0, k) : kx<p>(1, k)) * f);
-        }
-        sx = fma(sx, dt, (bm == 0 ? kx<p>(0, 0) : kx<p>(1, 0)) * (vn + v0));
-        const double xn = fma(sx, dt, x0);
+        double xn, vn;
+        correct_comp<p>(dt, a.beta_mode, d0, d1, a.x0[c * a.ld + i], a.v0[c * a.ld + i], xn, vn);
         x[c] = xn;
         v[c] = vn;
 #pragma unroll
@@ -181,22 +212,8 @@ __global__ void k_correct(StepArgs a)
         if (kLast) {
             a.x0[c * a.ld + i] = xn;
             a.v0[c * a.ld + i] = vn;
-            double hi[K > p + 1 ? K - p - 1 : 1];
-            if constexpr (p >= 2) {
-                // a^(n)(t1) = sum_k (e1(n,k) a1^(k) + e0(n,k) a0^(k)) dt^(k-n), n = p+1 .. 2p-1
-                const double rdt = 1.0 / dt;
-#pragma unroll
-                for (int n = p + 1; n < K; ++n) {
-                    double s = 0.0;
-#pragma unroll
-                    for (int k = p; k >= 0; --k)
-                        s = fma(s, dt, fma(e1<p>(n, k), d1[k], e0<p>(n, k) * d0[k]));
-                    double sc = 1.0;
-#pragma unroll
-                    for (int e = 0; e < n; ++e) sc *= rdt;
-                    hi[n - p - 1] = s * sc;
-                }
-            }
+            double hi[K > p + 1 ? p - 1 : 1];
+            interp_comp<p>(dt, d0, d1, hi);
 #pragma unroll
             for (int k = 0; k < K; ++k)
                 a.d0[(3 * k + c) * a.ld + i] = k <= p ? d1[k] : hi[k - p - 1];
@@ -207,6 +224,182 @@ __global__ void k_correct(StepArgs a)
     }
     if (live && !finite) atomicOr(a.flag, 1);
     if (!kLast) {
+        track_bounds(a, live, x, v);
+        if (live) write_input<p>(a, i, x, v, ad);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block time steps.  Every body i has a tick T[i] (units of dt_max 2^-k_max)
+// and a level (step dt_max 2^-level).  The next block time is the minimum of
+// T[i] + 2^(k_max - level[i]); the bodies reaching it form the active list.
+// ---------------------------------------------------------------------------
+
+struct BlockArgs {
+    long long *T;
+    int *level;
+    int *act;                   // active list (positions -> bodies)
+    unsigned long long *blk;    // [0] next block tick, [1] active count
+    int k_max;
+    double dt_max, tick, eta;
+    long long T_next;           // host copy for the kernels that follow the readback
+    int64_t n_act;
+    int64_t part_ld;
+};
+
+__device__ __forceinline__ double norm3(double a, double b, double c)
+{
+    // no contraction: the same operation order as a plain C evaluation
+    return sqrt(__dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(c, c)));
+}
+
+// Aarseth-type estimate dt = eta sqrt((|a||a2| + |a1|^2) / (|a1||a3| + |a2|^2)) and
+// the level rule: shrink freely, grow by one level only when T is a multiple of it.
+__device__ int block_level(const double (&n)[4], double eta, double dt_max, int k_max, int k_old,
+                           long long T)
+{
+    const double num = __dadd_rn(__dmul_rn(n[0], n[2]), __dmul_rn(n[1], n[1]));
+    const double den = __dadd_rn(__dmul_rn(n[1], n[3]), __dmul_rn(n[2], n[2]));
+    const double dtc = __dmul_rn(eta, sqrt(__ddiv_rn(num, den)));
+    int k = 0;
+    while (k < k_max && dt_max * ldexp(1.0, -k) > dtc) ++k;
+    if (k_old < 0 || k >= k_old) return k;
+    const int kg = k_old - 1;
+    const long long span = 1LL << (k_max - kg);
+    return (T % span == 0) ? kg : k_old;
+}
+
+__global__ void k_block_init_levels(int64_t N, int64_t ld, const double *d0, BlockArgs b)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double n[4];
+    for (int k = 0; k < 4; ++k)
+        n[k] = norm3(d0[(3 * k) * ld + i], d0[(3 * k + 1) * ld + i], d0[(3 * k + 2) * ld + i]);
+    b.level[i] = block_level(n, b.eta, b.dt_max, b.k_max, -1, 0);
+    b.T[i] = 0;
+}
+
+__global__ void k_block_reset(unsigned long long *blk)
+{
+    blk[0] = ~0ull;
+    blk[1] = 0ull;
+}
+
+__global__ void k_block_next(int64_t N, BlockArgs b)
+{
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long t = ~0ull;
+    if (i0 < N) t = (unsigned long long)(b.T[i0] + (1LL << (b.k_max - b.level[i0])));
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long q = __shfl_xor_sync(0xffffffffu, t, o);
+        t = q < t ? q : t;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMin(b.blk, t);
+}
+
+__global__ void k_block_active(int64_t N, BlockArgs b)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const unsigned long long tn = b.blk[0];
+    if ((unsigned long long)(b.T[i] + (1LL << (b.k_max - b.level[i]))) == tn) {
+        const unsigned long long pos = atomicAdd(b.blk + 1, 1ull);
+        b.act[pos] = (int)i;
+    }
+}
+
+// Prediction of every body to the next block time (its own dt).
+template <int p>
+__global__ void k_block_predict(StepArgs a, BlockArgs b)
+{
+    constexpr int K = 2 * p;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i0 < a.N;
+    const int64_t i = live ? i0 : a.N - 1;
+    const double dt = (double)(b.T_next - b.T[i]) * b.tick;
+    double x[3], v[3], ad[p > 1 ? p - 1 : 1][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double d[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) d[k] = a.d0[(3 * k + c) * a.ld + i];
+        double sx = 0.0, sv = 0.0;
+#pragma unroll
+        for (int k = K - 1; k >= 0; --k) {
+            sx = fma(sx, dt, d[k] * inv_fact(k + 2));
+            sv = fma(sv, dt, d[k] * inv_fact(k + 1));
+        }
+        const double x0 = a.x0[c * a.ld + i], v0 = a.v0[c * a.ld + i];
+        x[c] = fma(fma(sx, dt, v0), dt, x0);
+        v[c] = fma(sv, dt, v0);
+#pragma unroll
+        for (int q = 0; q + 2 <= p; ++q) {
+            double sa = 0.0;
+#pragma unroll
+            for (int k = K - 1; k >= q; --k) sa = fma(sa, dt, d[k] * inv_fact(k - q));
+            ad[q][c] = sa;
+        }
+    }
+    track_bounds(a, live, x, v);
+    if (live) write_input<p>(a, i, x, v, ad);
+}
+
+// Correction of the active bodies (position pos -> body act[pos]) with their own dt.
+template <int p, bool kLast>
+__global__ void k_block_correct(StepArgs a, BlockArgs b)
+{
+    constexpr int K = 2 * p;
+    constexpr int NR = (p + 1) * 3;
+    const int64_t pos0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = pos0 < b.n_act;
+    const int64_t pos = live ? pos0 : 0;
+    const int64_t i = b.act[pos];
+    const double dt = (double)(b.T_next - b.T[i]) * b.tick;
+    double x[3], v[3], ad[p > 1 ? p - 1 : 1][3];
+    double nrm[4][3];
+    bool finite = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double d1[p + 1], d0[K];
+#pragma unroll
+        for (int k = 0; k <= p; ++k) {
+            double s = 0.0;
+            for (int q = 0; q < a.split; ++q) s += a.part[((int64_t)q * NR + 3 * k + c) * b.part_ld + pos];
+            d1[k] = s;
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) d0[k] = a.d0[(3 * k + c) * a.ld + i];
+        double xn, vn;
+        correct_comp<p>(dt, a.beta_mode, d0, d1, a.x0[c * a.ld + i], a.v0[c * a.ld + i], xn, vn);
+        x[c] = xn;
+        v[c] = vn;
+#pragma unroll
+        for (int q = 0; q + 2 <= p; ++q) ad[q][c] = d1[q];
+        finite = finite && isfinite(xn) && isfinite(vn);
+        if (kLast) {
+            double hi[K > p + 1 ? p - 1 : 1];
+            interp_comp<p>(dt, d0, d1, hi);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) nrm[k][c] = k <= p ? d1[k] : hi[k - p - 1];
+            if (live) {
+                a.x0[c * a.ld + i] = xn;
+                a.v0[c * a.ld + i] = vn;
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+                    a.d0[(3 * k + c) * a.ld + i] = k <= p ? d1[k] : hi[k - p - 1];
+            }
+        }
+    }
+    if (live && !finite) atomicOr(a.flag, 1);
+    if (kLast) {
+        if (live) {
+            double n[4];
+            for (int k = 0; k < 4; ++k) n[k] = norm3(nrm[k][0], nrm[k][1], nrm[k][2]);
+            b.level[i] = block_level(n, b.eta, b.dt_max, b.k_max, b.level[i], b.T_next);
+            b.T[i] = b.T_next;
+        }
+    } else {
         track_bounds(a, live, x, v);
         if (live) write_input<p>(a, i, x, v, ad);
     }
@@ -313,6 +506,65 @@ int launch_step_kernels(const StepArgs &a, int phase, bool last, cudaStream_t st
 }
 
 }  // namespace
+
+template <int p>
+int launch_block_kernels(const StepArgs &a, const BlockArgs &b, int phase, bool last, cudaStream_t st)
+{
+    const int T = 128;
+    if (phase == 0) {
+        k_block_predict<p><<<blocks_for(a.N, T), T, 0, st>>>(a, b);
+        MH_LAUNCHED("k_block_predict");
+    } else if (last) {
+        k_block_correct<p, true><<<blocks_for(b.n_act, T), T, 0, st>>>(a, b);
+        MH_LAUNCHED("k_block_correct(last)");
+    } else {
+        k_block_correct<p, false><<<blocks_for(b.n_act, T), T, 0, st>>>(a, b);
+        MH_LAUNCHED("k_block_correct");
+    }
+    return MH_OK;
+}
+
+static BlockArgs block_args(const DeviceState &s, const mh_config &cfg, long long T_next, int64_t n_act)
+{
+    BlockArgs b{s.T, s.level, s.act, s.blk, cfg.k_max, cfg.dt_max, ldexp(cfg.dt_max, -cfg.k_max),
+                cfg.eta, T_next, n_act, s.Np};
+    return b;
+}
+
+int launch_block_init(const DeviceState &s, const mh_config &cfg, cudaStream_t st)
+{
+    k_block_init_levels<<<blocks_for(s.N, 128), 128, 0, st>>>(s.N, s.Np, s.d0, block_args(s, cfg, 0, 0));
+    MH_LAUNCHED("k_block_init_levels");
+    return MH_OK;
+}
+
+int launch_block_schedule(const DeviceState &s, const mh_config &cfg, cudaStream_t st)
+{
+    const BlockArgs b = block_args(s, cfg, 0, 0);
+    k_block_reset<<<1, 1, 0, st>>>(s.blk);
+    MH_LAUNCHED("k_block_reset");
+    k_block_next<<<blocks_for(s.N, 128), 128, 0, st>>>(s.N, b);
+    MH_LAUNCHED("k_block_next");
+    k_block_active<<<blocks_for(s.N, 128), 128, 0, st>>>(s.N, b);
+    MH_LAUNCHED("k_block_active");
+    return MH_OK;
+}
+
+// phase 0: predict all bodies to T_next; phase 1: correct the active list.
+int launch_block_phase(const DeviceState &s, const mh_config &cfg, long long T_next, int64_t n_act,
+                       int phase, bool last, int split, cudaStream_t st)
+{
+    StepArgs a{s.N, s.Np, 0.0, s.m, s.x0, s.v0, s.d0, s.x1, s.v1, s.jrec, s.jrec32, s.part,
+               split, cfg.precision, cfg.beta_mode, s.flag,
+               s.bound ? s.bound + 2 * s.flip : nullptr, s.bound ? s.bound + 2 * (1 - s.flip) : nullptr};
+    const BlockArgs b = block_args(s, cfg, T_next, n_act);
+    switch (s.p) {
+    case 2: return launch_block_kernels<2>(a, b, phase, last, st);
+    case 3: return launch_block_kernels<3>(a, b, phase, last, st);
+    }
+    set_error("block steps need order 6 or 8");
+    return MH_EINVAL;
+}
 
 // phase 0: predict; phase 1: correct (last = final pass of the step).
 int launch_step_phase(const DeviceState &s, const mh_config &cfg, double dt, int phase, bool last,

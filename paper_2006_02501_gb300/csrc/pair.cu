@@ -169,6 +169,7 @@ struct PairArgs64 {
     int64_t part_ld;
     int64_t n_itiles, chunk;
     int split, tj;
+    const int *ilist;     // optional: body index of position i (active list); else i itself
 };
 
 template <int P, bool kGuard>
@@ -206,7 +207,8 @@ __global__ void __launch_bounds__(128) k_pair_fp64(PairArgs64<P> a)
         const int jc = (int)(item / a.n_itiles);
         const int64_t i = a.i0 + itile * blockDim.x + threadIdx.x;
         const bool live = i < a.i1;
-        const int64_t ic = live ? i : a.i0;
+        const int64_t ipos = live ? i : a.i0;
+        const int64_t ic = a.ilist ? (int64_t)a.ilist[ipos] : ipos;
         double ri[P + 1][3];
 #pragma unroll
         for (int k = 0; k <= P; ++k)
@@ -231,8 +233,9 @@ __global__ void __launch_bounds__(128) k_pair_fp64(PairArgs64<P> a)
             }
             __syncthreads();
             // the i == j pair can only occur when this tile overlaps the CTA's i-range
+            // (with an index list any tile may hold it)
             const int64_t ib = a.i0 + itile * blockDim.x;
-            if (j0 < ib + (int64_t)blockDim.x && ib < j0 + tj) {
+            if (a.ilist || (j0 < ib + (int64_t)blockDim.x && ib < j0 + tj)) {
                 for (int jj = 0; jj < tj; ++jj) interact64<P, true>(sh, tj, jj, j0 + jj == ic, ri, a, acc);
             } else {
                 for (int jj = 0; jj < tj; ++jj) interact64<P, false>(sh, tj, jj, false, ri, a, acc);
@@ -270,6 +273,7 @@ struct PairArgs32 {
     double *part;
     int64_t part_ld, n_itiles, chunk;
     int split, tj;
+    const int *ilist;     // optional: body index of position i (active list)
 };
 
 constexpr int kThreads32 = 256;
@@ -326,7 +330,8 @@ __global__ void __launch_bounds__(kThreads32, 2) k_pair_fp32(PairArgs32<P> a)
         const int64_t ib = a.i0 + itile * kThreads32;
         const int64_t i = ib + threadIdx.x;
         const bool live = i < a.i1;
-        const int64_t ic = live ? i : a.i0;
+        const int64_t ipos = live ? i : a.i0;
+        const int64_t ic = a.ilist ? (int64_t)a.ilist[ipos] : ipos;
         float xh[3], xl[3], vh[3], vl[3], ai[3], ji[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -355,8 +360,8 @@ __global__ void __launch_bounds__(kThreads32, 2) k_pair_fp32(PairArgs32<P> a)
             for (int k = 0; k <= P; ++k)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) acc[k][c] = 0.0f;
-            if (j0 < ib + kThreads32 && ib < j0 + tj) {
-                // the tile overlaps this CTA's i-range: guard the i == j pair
+            if (a.ilist || (j0 < ib + kThreads32 && ib < j0 + tj)) {
+                // the tile may hold this thread's own body: guard the i == j pair
 #pragma unroll 2
                 for (int jj = 0; jj < tj; ++jj)
                     interact32<P, true>(sh4, jj, j0 + jj == ic, xh, xl, vh, vl, ai, ji, a.eps2, acc);
@@ -383,10 +388,12 @@ __global__ void __launch_bounds__(kThreads32, 2) k_pair_fp32(PairArgs32<P> a)
 template <int P>
 __global__ void k_pair_heavy(int64_t N, int64_t ld, const double *__restrict__ m,
                              const double *__restrict__ jrec, const int *__restrict__ heavy,
-                             int n_heavy, double eps2, double G, double *__restrict__ out)
+                             int n_heavy, double eps2, double G, double *__restrict__ out,
+                             const int *__restrict__ ilist)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= N) return;                       // N: number of positions (bodies or active list)
+    const int64_t i = ilist ? (int64_t)ilist[pos] : pos;
     double ri[P + 1][3], acc[P + 1][3];
 #pragma unroll
     for (int k = 0; k <= P; ++k)
@@ -412,16 +419,16 @@ __global__ void k_pair_heavy(int64_t N, int64_t ld, const double *__restrict__ m
 #pragma unroll
     for (int k = 0; k <= P; ++k)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) out[(3 * k + c) * ld + i] = acc[k][c];
+        for (int c = 0; c < 3; ++c) out[(3 * k + c) * ld + pos] = acc[k][c];
 }
 
 template <int P>
 int launch_fp64(const double *jrec, const double *m, int64_t ld, int64_t n_j, double eps,
                 double G, int64_t i0, int64_t i1, double *part, int64_t part_ld,
-                const PairPlan &pl, cudaStream_t st)
+                const PairPlan &pl, const int *ilist, cudaStream_t st)
 {
     PairArgs64<P> a{jrec, m, ld, n_j, i0, i1, eps * eps, G, part, part_ld,
-                    pl.n_itiles, pl.chunk, pl.split, pl.tj};
+                    pl.n_itiles, pl.chunk, pl.split, pl.tj, ilist};
     const size_t smem = sizeof(double) * (3 * (P + 1) + 1) * pl.tj;
     k_pair_fp64<P><<<pl.grid, pl.threads, smem, st>>>(a);
     MH_LAUNCHED("k_pair_fp64");
@@ -430,10 +437,11 @@ int launch_fp64(const double *jrec, const double *m, int64_t ld, int64_t n_j, do
 
 template <int P>
 int launch_fp32(const float *jrec32, int64_t ld, int64_t n_j, double eps, int64_t i0,
-                int64_t i1, double *part, int64_t part_ld, const PairPlan &pl, cudaStream_t st)
+                int64_t i1, double *part, int64_t part_ld, const PairPlan &pl, const int *ilist,
+                cudaStream_t st)
 {
     PairArgs32<P> a{jrec32, ld, n_j, i0, i1, (float)(eps * eps), part, part_ld,
-                    pl.n_itiles, pl.chunk, pl.split, pl.tj};
+                    pl.n_itiles, pl.chunk, pl.split, pl.tj, ilist};
     const size_t smem = sizeof(float) * Rec32<P>::RS * pl.tj + sizeof(double) * (P + 1) * 3 * kThreads32;
     k_pair_fp32<P><<<pl.grid, pl.threads, smem, st>>>(a);
     MH_LAUNCHED("k_pair_fp32");
@@ -444,14 +452,14 @@ int launch_fp32(const float *jrec32, int64_t ld, int64_t n_j, double eps, int64_
 
 int launch_pair_heavy(int P, int64_t N, int64_t ld, const double *m, const double *jrec,
                       const int *heavy, int n_heavy, double eps, double G, double *part, int slot,
-                      cudaStream_t st)
+                      cudaStream_t st, const int *ilist)
 {
     double *out = part + (int64_t)slot * (P + 1) * 3 * ld;
     const unsigned g = (unsigned)((N + 127) / 128);
     switch (P) {
-    case 1: k_pair_heavy<1><<<g, 128, 0, st>>>(N, ld, m, jrec, heavy, n_heavy, eps * eps, G, out); break;
-    case 2: k_pair_heavy<2><<<g, 128, 0, st>>>(N, ld, m, jrec, heavy, n_heavy, eps * eps, G, out); break;
-    case 3: k_pair_heavy<3><<<g, 128, 0, st>>>(N, ld, m, jrec, heavy, n_heavy, eps * eps, G, out); break;
+    case 1: k_pair_heavy<1><<<g, 128, 0, st>>>(N, ld, m, jrec, heavy, n_heavy, eps * eps, G, out, ilist); break;
+    case 2: k_pair_heavy<2><<<g, 128, 0, st>>>(N, ld, m, jrec, heavy, n_heavy, eps * eps, G, out, ilist); break;
+    case 3: k_pair_heavy<3><<<g, 128, 0, st>>>(N, ld, m, jrec, heavy, n_heavy, eps * eps, G, out, ilist); break;
     default: set_error("launch_pair_heavy: P must be 1..3"); return MH_EINVAL;
     }
     MH_LAUNCHED("k_pair_heavy");
@@ -499,22 +507,22 @@ PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hin
 
 int launch_pair(int P, int precision, int64_t n_j, int64_t ld, const double *m, const double *jrec,
                 const float *jrec32, double eps, double G, int64_t i0, int64_t i1, double *part,
-                int64_t part_ld, const PairPlan &pl, cudaStream_t st)
+                int64_t part_ld, const PairPlan &pl, cudaStream_t st, const int *ilist)
 {
     if (precision == MH_PREC_FP64) {
         switch (P) {
-        case 1: return launch_fp64<1>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, st);
-        case 2: return launch_fp64<2>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, st);
-        case 3: return launch_fp64<3>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, st);
-        case 4: return launch_fp64<4>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, st);
-        case 5: return launch_fp64<5>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, st);
+        case 1: return launch_fp64<1>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st);
+        case 2: return launch_fp64<2>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st);
+        case 3: return launch_fp64<3>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st);
+        case 4: return launch_fp64<4>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st);
+        case 5: return launch_fp64<5>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st);
         }
     } else {
         switch (P) {
         // the FP32 input rows carry G m: G is applied when they are written
-        case 1: return launch_fp32<1>(jrec32, ld, n_j, eps, i0, i1, part, part_ld, pl, st);
-        case 2: return launch_fp32<2>(jrec32, ld, n_j, eps, i0, i1, part, part_ld, pl, st);
-        case 3: return launch_fp32<3>(jrec32, ld, n_j, eps, i0, i1, part, part_ld, pl, st);
+        case 1: return launch_fp32<1>(jrec32, ld, n_j, eps, i0, i1, part, part_ld, pl, ilist, st);
+        case 2: return launch_fp32<2>(jrec32, ld, n_j, eps, i0, i1, part, part_ld, pl, ilist, st);
+        case 3: return launch_fp32<3>(jrec32, ld, n_j, eps, i0, i1, part, part_ld, pl, ilist, st);
         }
     }
     set_error("launch_pair: unsupported P/precision");

@@ -1,0 +1,93 @@
+"""GPU parity of block time steps (active-list evaluation) against the oracle.
+
+Levels are integers decided in FP64 on both sides from the same formula; a
+level may differ only where the estimate lies within 1e-9 (relative) of a
+power-of-two boundary, which the test checks before comparing states."""
+import numpy as np
+import pytest
+
+from helpers import rel_rows, scaled_stack_err
+from paper_2006_02501_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mh():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2006_02501_gb300 as pkg
+    pkg.build_library()
+    return pkg
+
+
+def _borderline(orc, derivs, eta, dt_max, k_max):
+    out = []
+    for d in derivs:
+        dtc = orc.aarseth_dt(d[:4], eta)
+        q = np.log2(dt_max / dtc)
+        out.append(abs(q - round(q)) < 1e-9 and 0 < round(q) <= k_max)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("order", [6, 8])
+def test_block_levels_at_creation(mh, orc, order):
+    m, x, v = I.smbh_disc(seed=31, N=800)
+    blk = dict(dt_max=2.0 ** -5, k_max=12, eta=0.05)
+    with mh.Simulation(order, m, x, v, 1e-4, block=blk) as sim:
+        lv = sim.levels()
+    B = orc.BlockState(order, m, x, v, 1e-4, blk["dt_max"], blk["k_max"], blk["eta"])
+    diff = lv != B.level
+    assert not np.any(diff & ~_borderline(orc, B.derivs, blk["eta"], blk["dt_max"], blk["k_max"]))
+    assert len(set(lv.tolist())) >= 3
+
+
+@pytest.mark.parametrize("order", [6, 8])
+def test_block_step_parity_fp64(mh, orc, order):
+    m, x, v = I.smbh_disc(seed=32, N=700)
+    blk = dict(dt_max=2.0 ** -5, k_max=10, eta=0.05)
+    eps = 1e-4
+    B = orc.BlockState(order, m, x, v, eps, blk["dt_max"], blk["k_max"], blk["eta"])
+    with mh.Simulation(order, m, x, v, eps, block=blk) as sim:
+        sim.set_state(x, v, B.derivs, level=B.level)         # identical start
+        B.advance(2 * blk["dt_max"], 3)
+        sim.step(2 * blk["dt_max"], 3)
+        t, xg, vg, dg = sim.sync()
+        lv = sim.levels()
+        c = sim.counters()
+    assert np.array_equal(lv, B.level)
+    assert c["particle_steps"] == B.active_total
+    assert rel_rows(xg, B.x) < 1e-12
+    assert rel_rows(vg, B.v, 1e-3) < 1e-11
+    assert scaled_stack_err(dg[:, :4], B.derivs[:, :4], blk["dt_max"] * 2.0 ** -lv.max()) < 1e-9
+
+
+def test_block_step_fp32_precision_form(mh, orc):
+    """Precision form with block steps: accelerations within 2e-6 of the oracle
+    after two dt_max of block steps from the same start."""
+    m, x, v = I.smbh_disc(seed=33, N=900)
+    blk = dict(dt_max=2.0 ** -5, k_max=10, eta=0.05)
+    eps = 1e-4
+    B = orc.BlockState(8, m, x, v, eps, blk["dt_max"], blk["k_max"], blk["eta"])
+    with mh.Simulation(8, m, x, v, eps, block=blk, precision=mh.MH_PREC_FP32PAIR) as sim:
+        sim.set_state(x, v, B.derivs, level=B.level)
+        E0 = sim.energy()
+        B.advance(2 * blk["dt_max"], 3)
+        sim.step(2 * blk["dt_max"], 3)
+        t, xg, vg, dg = sim.sync()
+        E1 = sim.energy()
+        lv = sim.levels()
+    same = lv == B.level
+    assert same.mean() > 0.99
+    assert rel_rows(dg[same, 0], B.derivs[same, 0]) < 2e-6
+    dE_ref = B.energy() / orc.energy(m, x, v, eps) - 1
+    assert abs((E1 / E0 - 1) - dE_ref) < 1e-9
+
+
+def test_block_mode_rejects_bad_dt(mh):
+    m, x, v = I.smbh_disc(seed=34, N=100)
+    with mh.Simulation(8, m, x, v, 1e-4, block=dict(dt_max=2.0 ** -5, k_max=8, eta=0.05)) as sim:
+        with pytest.raises(mh.MHError):
+            sim.step(0.7 * 2.0 ** -5, 3)
