@@ -143,6 +143,37 @@ int mh_set_state(mh_sim *sim, const mh_state *in);
  * the central body's row is zero. */
 int mh_diagnostics(mh_sim *sim, double *energy, double *ecc, int central);
 
+/* ------------------------------------------------------------------------- */
+/* Batched form: many independent small systems in one persistent launch.     */
+/* ------------------------------------------------------------------------- */
+
+/* Create S independent systems (1 to 64 bodies each) integrated in FP64 with
+ * shared steps.  offsets: S+1 body offsets (offsets[0] = 0); m, x, v: the
+ * systems' bodies back to back (offsets[S] bodies, rows N x 3); dt: S steps,
+ * one per system; eps, order, cfg, stream as for mh_create (cfg->precision must
+ * be MH_PREC_FP64, cfg->step_mode MH_STEP_SHARED).  Each system's
+ * a^(0..2p-1) at t = 0 come from the explicit initialisation (Section 3 intro).
+ * mh_sync / mh_set_state see the concatenated bodies; mh_step and the energy
+ * of mh_diagnostics are rejected (use mh_step_batch, mh_batch_energy). */
+int mh_create_batch(mh_sim **out, int64_t S, const int64_t *offsets, const double *m, const double *x,
+                    const double *v, const double *dt, double eps, int order, const mh_config *cfg,
+                    void *stream);
+
+/* Advance every system by n_steps steps of its own dt, P(EC)^n_iter each, in
+ * one persistent kernel launch replayed from a CUDA graph (captured on the
+ * first call for each (n_steps, n_iter) and launch configuration).  The first
+ * call runs the autotuner unless mh_batch_tune ran before.  Stream-ordered. */
+int mh_step_batch(mh_sim *sim, int64_t n_steps, int n_iter);
+
+/* Autotuner of the batched launch: times warps per CTA {2, 4, 6, 8} and the
+ * work order (largest systems first, or as given) over probe_steps steps on a
+ * scratch copy of the state, keeps the fastest (cached per order, number of
+ * systems, size histogram and device) and reports it (either output may be NULL). */
+int mh_batch_tune(mh_sim *sim, int probe_steps, int n_iter, int *warps, int *order_kind);
+
+/* Total energy of every system (S values, FP64; waits). */
+int mh_batch_energy(mh_sim *sim, double *energy);
+
 /* Number of bodies, order and counters of a handle. */
 int mh_info(mh_sim *sim, int64_t *N, int *order, mh_counters *counters);
 

@@ -20,7 +20,7 @@ from . import _capi
 from ._capi import (MH_BETA_MODIFIED, MH_BETA_STANDARD, MH_PREC_FP32PAIR, MH_PREC_FP64,  # noqa: F401
                     MHError, check)
 
-__all__ = ["Simulation", "pair_eval", "MHError", "build_library", "MH_PREC_FP64", "MH_PREC_FP32PAIR",
+__all__ = ["Simulation", "Batch", "pair_eval", "MHError", "build_library", "MH_PREC_FP64", "MH_PREC_FP32PAIR",
            "MH_BETA_MODIFIED", "MH_BETA_STANDARD"]
 
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -156,6 +156,54 @@ class Simulation:
         n, o, c = ctypes.c_int64(), ctypes.c_int(), _capi.Counters()
         check(_capi.lib().mh_info(self._h, ctypes.byref(n), ctypes.byref(o), ctypes.byref(c)))
         return {f: getattr(c, f) for f, _ in c._fields_}
+
+
+class Batch:
+    """Many independent small systems (1..64 bodies each) advanced together by
+    one persistent kernel launch per call (FP64, shared steps per system).
+
+    offsets: (S+1,) int64 body offsets; m, x, v: the concatenated bodies;
+    dt: (S,) step of each system.
+    """
+
+    def __init__(self, order: int, offsets, m, x, v, dt, eps: float, beta: int = MH_BETA_MODIFIED,
+                 G: float = 1.0, stream=None):
+        L = _capi.lib()
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        S = offsets.shape[0] - 1
+        m = _host(m)
+        N = m.shape[0]
+        x, v, dt = _host(x, (N, 3)), _host(v, (N, 3)), _host(dt, (S,))
+        cfg = _capi.Config()
+        L.mh_config_default(ctypes.byref(cfg))
+        cfg.order, cfg.beta_mode, cfg.G = order, beta, G
+        h = ctypes.c_void_p()
+        check(L.mh_create_batch(ctypes.byref(h), S, offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                _ptr(m), _ptr(x), _ptr(v), _ptr(dt), float(eps), order, ctypes.byref(cfg),
+                                _stream_handle(stream)))
+        self._h = h
+        self.S, self.N, self.order, self.p = S, N, order, order // 2 - 1
+        self.offsets = offsets
+
+    close = Simulation.close
+    __del__ = Simulation.__del__
+    __enter__ = Simulation.__enter__
+    __exit__ = Simulation.__exit__
+    sync = Simulation.sync
+    counters = Simulation.counters
+
+    def step(self, n_steps: int, n_iter: int) -> None:
+        check(_capi.lib().mh_step_batch(self._h, int(n_steps), int(n_iter)))
+
+    def tune(self, probe_steps: int = 8, n_iter: int = 2):
+        w, o = ctypes.c_int(), ctypes.c_int()
+        check(_capi.lib().mh_batch_tune(self._h, int(probe_steps), int(n_iter), ctypes.byref(w), ctypes.byref(o)))
+        return w.value, o.value
+
+    def energies(self) -> np.ndarray:
+        e = np.zeros(self.S)
+        check(_capi.lib().mh_batch_energy(self._h, _ptr(e)))
+        return e
 
 
 def _dev_ptr(t) -> int:

@@ -29,7 +29,8 @@ MH_STEP_SHARED, MH_STEP_BLOCK = 0, 1
 EXPORTS = [
     "mh_config_default", "mh_create", "mh_destroy", "mh_step", "mh_sync", "mh_set_state",
     "mh_diagnostics", "mh_info", "mh_last_error", "mh_pair_eval", "mh_release_scratch",
-    "mh_set_timing", "mh_pair_eval_noalloc",
+    "mh_set_timing", "mh_pair_eval_noalloc", "mh_create_batch", "mh_step_batch", "mh_batch_tune",
+    "mh_batch_energy",
 ]
 
 
@@ -90,6 +91,13 @@ def lib() -> ctypes.CDLL:
             L.mh_release_scratch.argtypes = []
             L.mh_set_timing.argtypes = [P, I]
             L.mh_pair_eval_noalloc.argtypes = [I, I, I64, P, P, D, D, I64, I64, P, P]
+            I64P = ctypes.POINTER(ctypes.c_int64)
+            IP = ctypes.POINTER(ctypes.c_int)
+            L.mh_create_batch.argtypes = [ctypes.POINTER(P), I64, I64P, DP, DP, DP, DP, D, I,
+                                          ctypes.POINTER(Config), P]
+            L.mh_step_batch.argtypes = [P, I64, I]
+            L.mh_batch_tune.argtypes = [P, I, I, IP, IP]
+            L.mh_batch_energy.argtypes = [P, DP]
             for name in EXPORTS:
                 if name not in ("mh_destroy", "mh_config_default", "mh_last_error"):
                     getattr(L, name).restype = ctypes.c_int

@@ -221,8 +221,12 @@ void mh_config_default(mh_config *cfg)
 
 const char *mh_last_error(void) { return g_last_error.c_str(); }
 
-int mh_create(mh_sim **out, int64_t N, int order, const double *m, const double *x, const double *v,
-              double eps, const mh_config *cfg, void *stream)
+}  // extern "C"
+
+// Allocate a simulation, upload m, x, v and (if initialise) compute the initial
+// derivatives of one system of N bodies.
+int mh::create_shell(mh_sim **out, int64_t N, int order, const double *m, const double *x,
+                     const double *v, double eps, const mh_config *cfg, void *stream, bool init)
 {
     if (!out) {
         set_error("mh_create: out is NULL");
@@ -258,7 +262,7 @@ int mh_create(mh_sim **out, int64_t N, int order, const double *m, const double 
     sim->cfg = c;
     sim->eps = eps;
     cudaGetDevice(&sim->device);
-    if (stream) {
+    if (stream && stream != (void *)cudaStreamLegacy && stream != (void *)cudaStreamPerThread) {
         sim->stream = (cudaStream_t)stream;
     } else {
         cudaError_t e = cudaStreamCreateWithFlags(&sim->stream, cudaStreamNonBlocking);
@@ -337,18 +341,35 @@ int mh_create(mh_sim **out, int64_t N, int order, const double *m, const double 
     if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);   // host buffers go out of scope
     if (e != cudaSuccess) return fail(cuda_fail(e, "upload state"));
     if ((rc = upload_bounds(s, x, v, sim->stream))) return fail(rc);
-    if ((rc = initialise(sim))) return fail(rc);
-    if (c.step_mode == MH_STEP_BLOCK && (rc = launch_block_init(s, c, sim->stream))) return fail(rc);
+    if (init) {
+        if ((rc = initialise(sim))) return fail(rc);
+        if (c.step_mode == MH_STEP_BLOCK && (rc = launch_block_init(s, c, sim->stream))) return fail(rc);
+    }
     e = cudaStreamSynchronize(sim->stream);
     if (e != cudaSuccess) return fail(cuda_fail(e, "initialisation"));
     *out = sim;
     return MH_OK;
 }
 
+int mh::mh_create_shell(mh_sim **out, int64_t N, int order, const double *m, const double *x,
+                        const double *v, double eps, const mh_config *cfg, void *stream)
+{
+    return create_shell(out, N, order, m, x, v, eps, cfg, stream, false);
+}
+
+extern "C" {
+
+int mh_create(mh_sim **out, int64_t N, int order, const double *m, const double *x, const double *v,
+              double eps, const mh_config *cfg, void *stream)
+{
+    return create_shell(out, N, order, m, x, v, eps, cfg, stream, true);
+}
+
 void mh_destroy(mh_sim *sim)
 {
     if (!sim) return;
     if (sim->stream) cudaStreamSynchronize(sim->stream);
+    free_batch(sim);
     for (auto &pr : sim->ev_pending) sim->ev_free.push_back(pr);
     for (auto &pr : sim->ev_free) {
         cudaEventDestroy(pr.first);
@@ -431,6 +452,7 @@ int mh_step(mh_sim *sim, double dt, int n_iter)
     if (int rc = check_handle(sim)) return rc;
     if (!(dt != 0.0) || !std::isfinite(dt)) { set_error("mh_step: dt must be finite and non-zero"); return MH_EINVAL; }
     if (n_iter < 1 || n_iter > 64) { set_error("mh_step: n_iter must be in [1, 64]"); return MH_EINVAL; }
+    if (sim->batch) { set_error("mh_step: batched simulations advance with mh_step_batch"); return MH_EINVAL; }
     if (sim->cfg.step_mode == MH_STEP_BLOCK) return block_advance(sim, dt, n_iter);
     DeviceState &s = sim->s;
     const int prec = sim->cfg.precision;
@@ -496,6 +518,7 @@ int mh_sync(mh_sim *sim, mh_state *out)
 int mh_set_state(mh_sim *sim, const mh_state *in)
 {
     if (int rc = check_handle(sim)) return rc;
+    if (sim->batch && !in->derivs) { set_error("mh_set_state: a batched simulation needs derivs"); return MH_EINVAL; }
     if (!in || !in->x || !in->v) { set_error("mh_set_state: x and v are required"); return MH_EINVAL; }
     DeviceState &s = sim->s;
     MH_CUDA(cudaStreamSynchronize(sim->stream));
@@ -533,6 +556,7 @@ int mh_set_state(mh_sim *sim, const mh_state *in)
 int mh_diagnostics(mh_sim *sim, double *energy, double *ecc, int central)
 {
     if (int rc = check_handle(sim)) return rc;
+    if (sim->batch && energy) { set_error("mh_diagnostics: use mh_batch_energy for batched simulations"); return MH_EINVAL; }
     DeviceState &s = sim->s;
     if (ecc && (central < 0 || central >= s.N)) { set_error("mh_diagnostics: central index out of range"); return MH_EINVAL; }
     double *e_rows = s.diag;

@@ -97,9 +97,17 @@ struct mh_sim {
     int device = 0;
     mh::DeviceState s;
     mh_counters ctr{};
+    void *batch = nullptr;        // batched integrator bookkeeping (batch.cu), or null
 };
 
 namespace mh {
+
+// Simulation construction (api.cu): allocate, upload, optionally initialise.
+int create_shell(mh_sim **out, int64_t N, int order, const double *m, const double *x,
+                 const double *v, double eps, const mh_config *cfg, void *stream, bool init);
+int mh_create_shell(mh_sim **out, int64_t N, int order, const double *m, const double *x,
+                    const double *v, double eps, const mh_config *cfg, void *stream);
+void free_batch(mh_sim *sim);
 
 // ---- kernels' host launchers (integrator.cu, pair.cu, diag.cu) ----
 

@@ -95,3 +95,22 @@ def test_python_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(_capi, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         _capi.lib()
+
+
+def test_create_batch_argument_checks(L):
+    import ctypes
+    dp = ctypes.POINTER(ctypes.c_double)
+    m = np.ones(70)
+    x = np.zeros((70, 3))
+    dt = np.full(2, 0.01)
+    ptr = lambda a: a.ctypes.data_as(dp)
+    h = ctypes.c_void_p()
+    off = np.array([0, 5, 70], dtype=np.int64)                 # second system has 65 bodies
+    rc = L.mh_create_batch(ctypes.byref(h), 2, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                           ptr(m), ptr(x), ptr(x), ptr(dt), 1e-3, 6, None, None)
+    assert rc == -1 and b"64" in L.mh_last_error()
+    off = np.array([1, 5, 9], dtype=np.int64)                  # offsets[0] != 0
+    rc = L.mh_create_batch(ctypes.byref(h), 2, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                           ptr(m), ptr(x), ptr(x), ptr(dt), 1e-3, 6, None, None)
+    assert rc == -1
+    assert L.mh_step_batch(None, 10, 2) == -1
