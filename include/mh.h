@@ -39,6 +39,7 @@ extern "C" {
 #endif
 
 typedef struct mh_sim mh_sim;
+typedef struct mh_mlp mh_mlp;
 
 typedef enum {
     MH_OK = 0,
@@ -173,6 +174,72 @@ int mh_batch_tune(mh_sim *sim, int probe_steps, int n_iter, int *warps, int *ord
 
 /* Total energy of every system (S values, FP64; waits). */
 int mh_batch_energy(mh_sim *sim, double *energy);
+
+/* ------------------------------------------------------------------------- */
+/* Convergence-controlled stepping and the learned predictor residual.        */
+/* The paper has no learned component; it iterates P(EC)^n (Section 2.1, end)  */
+/* and these entry points measure how many passes a step needs.               */
+/* ------------------------------------------------------------------------- */
+
+/* Shared step with as many evaluate-correct passes as needed: stop after the
+ * first pass whose largest change of a position component is at most
+ * tol * max|x| (the changes of the first pass are measured against the
+ * prediction), or after max_iter passes.  *n_used (may be NULL) receives the
+ * number of evaluations.  One 16-byte device-to-host read per pass. */
+int mh_step_converge(mh_sim *sim, double dt, double tol, int max_iter, int *n_used);
+
+/* Use (net != NULL) or stop using (NULL) a learned residual on the Taylor
+ * predictor of a shared-step simulation.  Before each step the features of
+ * every body (its scaled derivative stack F_k = h^k a^(k)/k!, k < 2p, Eq. 1, in
+ * a frame with e1 along a and e2 in the a, a-dot plane, divided by
+ * |a| sigma^k with sigma = max_{1<=k<2p} (|F_k|/|F_0|)^(1/k), the shortest time
+ * scale of the stack in units of h; then 1 + log10(sigma)) go through the network, whose 6
+ * outputs (clamped to +-1000) scaled by |a| h^2 sigma^6 and |a| h sigma^6 are
+ * added to the predicted x and v; read as the two next Taylor terms a^(2p),
+ * a^(2p+1), they extend the predicted a and a-dot the same way.  Bodies with
+ * a = 0 or sigma outside (0, 0.5]
+ * keep the plain prediction.  net must map 6p + 1 inputs to 6 outputs; the handle
+ * does not own it. */
+int mh_set_predictor(mh_sim *sim, mh_mlp *net);
+
+/* The predicted x, v at t + dt (Taylor predictor of Section 3 intro, plus the
+ * learned residual when a network is set) copied to host N x 3 arrays; the
+ * state is not advanced.  Waits. */
+int mh_predict(mh_sim *sim, double dt, double *x, double *v);
+
+/* Training samples of one step: advance the simulation by one plain step with
+ * n_iter passes (use enough passes to converge), then write for every body the
+ * 6p + 1 features at the start of the step and the 6 scaled components of
+ * (converged - Taylor-predicted) x and v, in the same frame and scaling.
+ * feats: device, N x (6p + 1) floats; targets: device, N x 6 floats (rows of bodies
+ * without a frame are zero).  Waits for completion. */
+int mh_collect_samples(mh_sim *sim, double dt, int n_iter, float *feats, float *targets);
+
+/* Multilayer perceptron n_in -> n_hidden -> n_hidden -> n_out with SiLU
+ * activations.  Parameters live on the device as an FP32 master copy
+ * [W1 (n_hidden x n_in), b1, W2 (n_hidden x n_hidden), b2, W3 (n_out x n_hidden),
+ * b3] and a bfloat16 copy; every matrix product runs on the tensor cores with
+ * bfloat16 operands (inputs, weights, activations, back-propagated errors) and
+ * FP32 accumulation.  Weights start uniform in +-1/sqrt(fan_in) from seed,
+ * biases at zero. */
+int mh_mlp_create(mh_mlp **out, int n_in, int n_hidden, int n_out, uint64_t seed);
+void mh_mlp_destroy(mh_mlp *net);
+int mh_mlp_num_params(const mh_mlp *net, int64_t *count);
+/* Copy the FP32 master parameters to / from the host (set also resets Adam). */
+int mh_mlp_get_params(mh_mlp *net, float *host, int64_t count);
+int mh_mlp_set_params(mh_mlp *net, const float *host, int64_t count);
+/* y = net(x): x device rows x n_in floats, y device rows x n_out floats. */
+int mh_mlp_forward(mh_mlp *net, const float *x, float *y, int64_t rows, void *stream);
+/* Mean-squared-error loss over all outputs of (x, t) (device) and its gradient
+ * with respect to the parameters (copied to grad_host, n_params floats; NULL
+ * to skip).  Waits. */
+int mh_mlp_loss_grad(mh_mlp *net, const float *x, const float *t, int64_t rows, double *loss,
+                     float *grad_host, void *stream);
+/* Adam (beta1 0.9, beta2 0.999, eps 1e-8) on shuffled mini-batches of `batch`
+ * rows of (x, t) for `epochs` epochs; *final_loss (may be NULL) receives the
+ * loss of the last batch.  Waits. */
+int mh_mlp_train(mh_mlp *net, const float *x, const float *t, int64_t rows, int epochs, int batch,
+                 float lr, uint64_t seed, double *final_loss, void *stream);
 
 /* Number of bodies, order and counters of a handle. */
 int mh_info(mh_sim *sim, int64_t *N, int *order, mh_counters *counters);

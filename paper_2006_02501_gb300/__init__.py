@@ -20,7 +20,7 @@ from . import _capi
 from ._capi import (MH_BETA_MODIFIED, MH_BETA_STANDARD, MH_PREC_FP32PAIR, MH_PREC_FP64,  # noqa: F401
                     MHError, check)
 
-__all__ = ["Simulation", "Batch", "pair_eval", "MHError", "build_library", "MH_PREC_FP64", "MH_PREC_FP32PAIR",
+__all__ = ["Simulation", "Batch", "MLP", "pair_eval", "MHError", "build_library", "MH_PREC_FP64", "MH_PREC_FP32PAIR",
            "MH_BETA_MODIFIED", "MH_BETA_STANDARD"]
 
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -148,6 +148,31 @@ class Simulation:
     def energy(self) -> float:
         return self.diagnostics(energy=True, ecc=False)[0]
 
+    def step_converge(self, dt: float, tol: float, max_iter: int) -> int:
+        """One step with evaluate-correct passes until the largest position change
+        is at most tol * max|x| (at most max_iter); returns the passes used."""
+        n = ctypes.c_int(0)
+        check(_capi.lib().mh_step_converge(self._h, float(dt), float(tol), int(max_iter), ctypes.byref(n)))
+        return n.value
+
+    def predict(self, dt: float):
+        """(x, v) the predictor gives for t + dt (Taylor, plus the learned residual
+        when a network is set); the state is not advanced."""
+        x = np.zeros((self.N, 3))
+        v = np.zeros((self.N, 3))
+        check(_capi.lib().mh_predict(self._h, float(dt), _ptr(x), _ptr(v)))
+        return x, v
+
+    def set_predictor(self, net) -> None:
+        """Use the learned residual of `net` (an MLP) on the Taylor predictor; None = plain."""
+        check(_capi.lib().mh_set_predictor(self._h, None if net is None else net._h))
+        self._net = net                     # keep the network alive while it is used
+
+    def collect_samples(self, dt: float, n_iter: int, feats, targets) -> None:
+        """One plain step with n_iter passes; writes N rows of features and targets
+        into the device tensors feats (N x (6p+1) float32) and targets (N x 6 float32)."""
+        check(_capi.lib().mh_collect_samples(self._h, float(dt), int(n_iter), _dev_ptr(feats), _dev_ptr(targets)))
+
     def set_timing(self, on: bool) -> None:
         """Bracket every O(N^2) evaluation launch with CUDA events (see counters())."""
         check(_capi.lib().mh_set_timing(self._h, 1 if on else 0))
@@ -156,6 +181,59 @@ class Simulation:
         n, o, c = ctypes.c_int64(), ctypes.c_int(), _capi.Counters()
         check(_capi.lib().mh_info(self._h, ctypes.byref(n), ctypes.byref(o), ctypes.byref(c)))
         return {f: getattr(c, f) for f, _ in c._fields_}
+
+
+class MLP:
+    """n_in -> hidden -> hidden -> n_out SiLU network on the GPU (BF16 operands,
+    FP32 accumulation on the tensor cores); trained by the library's kernels."""
+
+    def __init__(self, n_in: int, n_hidden: int = 128, n_out: int = 6, seed: int = 0):
+        h = ctypes.c_void_p()
+        check(_capi.lib().mh_mlp_create(ctypes.byref(h), int(n_in), int(n_hidden), int(n_out), int(seed)))
+        self._h = h
+        self.n_in, self.n_hidden, self.n_out = n_in, n_hidden, n_out
+        c = ctypes.c_int64()
+        check(_capi.lib().mh_mlp_num_params(self._h, ctypes.byref(c)))
+        self.n_params = c.value
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _capi.lib().mh_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, dtype=np.float32)
+        check(_capi.lib().mh_mlp_get_params(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), out.size))
+        return out
+
+    def set_params(self, flat) -> None:
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        check(_capi.lib().mh_mlp_set_params(self._h, flat.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), flat.size))
+
+    def forward(self, x, y, stream=None) -> None:
+        """y = net(x) on device tensors (rows x n_in, rows x n_out, float32)."""
+        check(_capi.lib().mh_mlp_forward(self._h, _dev_ptr(x), _dev_ptr(y), int(x.shape[0]),
+                                         _stream_handle(stream)))
+
+    def loss_grad(self, x, t, stream=None):
+        """(loss, gradient as n_params float32 on the host)."""
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = ctypes.c_double()
+        check(_capi.lib().mh_mlp_loss_grad(self._h, _dev_ptr(x), _dev_ptr(t), int(x.shape[0]), ctypes.byref(loss),
+                                           g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _stream_handle(stream)))
+        return loss.value, g
+
+    def train(self, x, t, epochs: int, batch: int, lr: float, seed: int = 0, stream=None) -> float:
+        loss = ctypes.c_double()
+        check(_capi.lib().mh_mlp_train(self._h, _dev_ptr(x), _dev_ptr(t), int(x.shape[0]), int(epochs), int(batch),
+                                       float(lr), int(seed), ctypes.byref(loss), _stream_handle(stream)))
+        return loss.value
 
 
 class Batch:

@@ -30,7 +30,9 @@ EXPORTS = [
     "mh_config_default", "mh_create", "mh_destroy", "mh_step", "mh_sync", "mh_set_state",
     "mh_diagnostics", "mh_info", "mh_last_error", "mh_pair_eval", "mh_release_scratch",
     "mh_set_timing", "mh_pair_eval_noalloc", "mh_create_batch", "mh_step_batch", "mh_batch_tune",
-    "mh_batch_energy",
+    "mh_batch_energy", "mh_step_converge", "mh_set_predictor", "mh_collect_samples", "mh_mlp_create",
+    "mh_mlp_destroy", "mh_mlp_num_params", "mh_mlp_get_params", "mh_mlp_set_params", "mh_mlp_forward",
+    "mh_mlp_loss_grad", "mh_mlp_train", "mh_predict",
 ]
 
 
@@ -80,6 +82,7 @@ def lib() -> ctypes.CDLL:
             L.mh_create.argtypes = [ctypes.POINTER(P), I64, I, DP, DP, DP, D, ctypes.POINTER(Config), P]
             L.mh_destroy.argtypes = [P]
             L.mh_destroy.restype = None
+            L.mh_mlp_destroy.restype = None
             L.mh_step.argtypes = [P, D, I]
             L.mh_sync.argtypes = [P, ctypes.POINTER(StateC)]
             L.mh_set_state.argtypes = [P, ctypes.POINTER(StateC)]
@@ -98,8 +101,22 @@ def lib() -> ctypes.CDLL:
             L.mh_step_batch.argtypes = [P, I64, I]
             L.mh_batch_tune.argtypes = [P, I, I, IP, IP]
             L.mh_batch_energy.argtypes = [P, DP]
+            FP = ctypes.POINTER(ctypes.c_float)
+            U64 = ctypes.c_uint64
+            L.mh_step_converge.argtypes = [P, D, D, I, IP]
+            L.mh_set_predictor.argtypes = [P, P]
+            L.mh_collect_samples.argtypes = [P, D, I, P, P]
+            L.mh_predict.argtypes = [P, D, DP, DP]
+            L.mh_mlp_create.argtypes = [ctypes.POINTER(P), I, I, I, U64]
+            L.mh_mlp_destroy.argtypes = [P]
+            L.mh_mlp_num_params.argtypes = [P, I64P]
+            L.mh_mlp_get_params.argtypes = [P, FP, I64]
+            L.mh_mlp_set_params.argtypes = [P, FP, I64]
+            L.mh_mlp_forward.argtypes = [P, P, P, I64, P]
+            L.mh_mlp_loss_grad.argtypes = [P, P, P, I64, DP, FP, P]
+            L.mh_mlp_train.argtypes = [P, P, P, I64, I, I, ctypes.c_float, U64, DP, P]
             for name in EXPORTS:
-                if name not in ("mh_destroy", "mh_config_default", "mh_last_error"):
+                if name not in ("mh_destroy", "mh_config_default", "mh_last_error", "mh_mlp_destroy"):
                     getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib

@@ -375,6 +375,11 @@ void mh_destroy(mh_sim *sim)
         cudaEventDestroy(pr.first);
         cudaEventDestroy(pr.second);
     }
+    if (sim->lfeat) cudaFree(sim->lfeat);
+    if (sim->lout) cudaFree(sim->lout);
+    if (sim->lsave) cudaFree(sim->lsave);
+    if (sim->conv) cudaFree(sim->conv);
+    if (sim->conv_host) cudaFreeHost(sim->conv_host);
     free_state(sim->s);
     if (sim->own_stream && sim->stream) cudaStreamDestroy(sim->stream);
     delete sim;
@@ -447,6 +452,62 @@ static int block_advance(mh_sim *sim, double dt, int n_iter)
     return MH_OK;
 }
 
+// One shared step: P (plus the learned residual when a network is set), then
+// E, C passes: exactly n_iter of them (tol < 0), or until the largest position
+// change of a pass is at most tol * max|x| (at most n_iter passes).
+static int shared_step(mh_sim *sim, double dt, int n_iter, double tol, int *n_used)
+{
+    DeviceState &s = sim->s;
+    const int prec = sim->cfg.precision;
+    int rc = launch_step_phase(s, sim->cfg, dt, 0, false, 0, sim->stream);
+    if (rc) return rc;
+    s.flip ^= 1;                        // the predictor raised the other bound slot
+    sim->ctr.kernel_launches += 1;
+    if (sim->mlp) {
+        if ((rc = launch_learned_features(s, dt, sim->lfeat, sim->stream))) return rc;
+        if ((rc = mlp_infer(sim->mlp, sim->lfeat, sim->lout, s.N, sim->stream))) return rc;
+        if ((rc = launch_learned_apply(s, sim->cfg, dt, sim->lout, 1e3f, sim->stream))) return rc;
+        s.flip ^= 1;
+        sim->ctr.kernel_launches += 9;
+    }
+    const bool adaptive = tol >= 0.0;
+    int used = n_iter;
+    for (int it = 0; it < n_iter; ++it) {
+        int split = 0;
+        if ((rc = evaluate(sim, s.p, prec, &split))) return rc;
+        bool last = it == n_iter - 1;
+        if (adaptive) {
+            MH_CUDA(cudaMemsetAsync(sim->conv, 0, 2 * sizeof(unsigned long long), sim->stream));
+            if ((rc = launch_step_phase(s, sim->cfg, dt, 1, false, split, sim->stream, sim->conv))) return rc;
+            s.flip ^= 1;
+            MH_CUDA(cudaMemcpyAsync(sim->conv_host, sim->conv, 2 * sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, sim->stream));
+            MH_CUDA(cudaStreamSynchronize(sim->stream));
+            double dx = 0.0, xm = 0.0;
+            std::memcpy(&dx, &sim->conv_host[0], 8);
+            std::memcpy(&xm, &sim->conv_host[1], 8);
+            sim->ctr.kernel_launches += 1;
+            if (dx <= tol * xm) last = true;
+            if (last) {
+                used = it + 1;
+                // the converged pass again, now committing (same inputs, same result)
+                if ((rc = launch_step_phase(s, sim->cfg, dt, 1, true, split, sim->stream))) return rc;
+                sim->ctr.kernel_launches += 1;
+                break;
+            }
+        } else {
+            if ((rc = launch_step_phase(s, sim->cfg, dt, 1, last, split, sim->stream))) return rc;
+            if (!last) s.flip ^= 1;
+            sim->ctr.kernel_launches += 1;
+        }
+    }
+    if (n_used) *n_used = used;
+    sim->t += dt;
+    sim->ctr.steps += 1;
+    sim->ctr.particle_steps += (double)s.N;
+    return MH_OK;
+}
+
 int mh_step(mh_sim *sim, double dt, int n_iter)
 {
     if (int rc = check_handle(sim)) return rc;
@@ -454,23 +515,106 @@ int mh_step(mh_sim *sim, double dt, int n_iter)
     if (n_iter < 1 || n_iter > 64) { set_error("mh_step: n_iter must be in [1, 64]"); return MH_EINVAL; }
     if (sim->batch) { set_error("mh_step: batched simulations advance with mh_step_batch"); return MH_EINVAL; }
     if (sim->cfg.step_mode == MH_STEP_BLOCK) return block_advance(sim, dt, n_iter);
+    return shared_step(sim, dt, n_iter, -1.0, nullptr);
+}
+
+static int ensure_conv(mh_sim *sim)
+{
+    if (sim->conv) return MH_OK;
+    MH_CUDA(cudaMalloc((void **)&sim->conv, 2 * sizeof(unsigned long long)));
+    MH_CUDA(cudaMallocHost((void **)&sim->conv_host, 2 * sizeof(unsigned long long)));
+    return MH_OK;
+}
+
+int mh_step_converge(mh_sim *sim, double dt, double tol, int max_iter, int *n_used)
+{
+    if (int rc = check_handle(sim)) return rc;
+    if (!(dt != 0.0) || !std::isfinite(dt) || !(tol >= 0.0) || max_iter < 1 || max_iter > 64) {
+        set_error("mh_step_converge: dt finite and non-zero, tol >= 0, 1 <= max_iter <= 64");
+        return MH_EINVAL;
+    }
+    if (sim->batch || sim->cfg.step_mode != MH_STEP_SHARED) {
+        set_error("mh_step_converge: shared-step simulations only");
+        return MH_EINVAL;
+    }
+    if (int rc = ensure_conv(sim)) return rc;
+    return shared_step(sim, dt, max_iter, tol, n_used);
+}
+
+int mh_set_predictor(mh_sim *sim, mh_mlp *net)
+{
+    if (int rc = check_handle(sim)) return rc;
+    if (sim->batch || sim->cfg.step_mode != MH_STEP_SHARED) {
+        set_error("mh_set_predictor: shared-step simulations only");
+        return MH_EINVAL;
+    }
+    if (net) {
+        int n_in = 0, n_out = 0;
+        mlp_dims(net, &n_in, &n_out);
+        if (n_in != 6 * sim->s.p + 1 || n_out != 6) {
+            set_error("mh_set_predictor: the network must map 6p + 1 features to 6 outputs");
+            return MH_EINVAL;
+        }
+        if (!sim->lfeat) {
+            MH_CUDA(cudaMalloc((void **)&sim->lfeat, (size_t)sim->s.N * (6 * sim->s.p + 1) * sizeof(float)));
+            MH_CUDA(cudaMalloc((void **)&sim->lout, (size_t)sim->s.N * 6 * sizeof(float)));
+        }
+    }
+    sim->mlp = net;
+    return MH_OK;
+}
+
+int mh_predict(mh_sim *sim, double dt, double *x, double *v)
+{
+    if (int rc = check_handle(sim)) return rc;
+    if (!x || !v || !(dt != 0.0) || !std::isfinite(dt)) { set_error("mh_predict: host x, v and dt != 0"); return MH_EINVAL; }
+    if (sim->batch || sim->cfg.step_mode != MH_STEP_SHARED) { set_error("mh_predict: shared-step simulations only"); return MH_EINVAL; }
     DeviceState &s = sim->s;
-    const int prec = sim->cfg.precision;
     int rc = launch_step_phase(s, sim->cfg, dt, 0, false, 0, sim->stream);
     if (rc) return rc;
-    s.flip ^= 1;                        // the predictor raised the other bound slot
-    sim->ctr.kernel_launches += 1;
-    for (int it = 0; it < n_iter; ++it) {
-        int split = 0;
-        if ((rc = evaluate(sim, s.p, prec, &split))) return rc;
-        const bool last = it == n_iter - 1;
-        if ((rc = launch_step_phase(s, sim->cfg, dt, 1, last, split, sim->stream))) return rc;
-        if (!last) s.flip ^= 1;
-        sim->ctr.kernel_launches += 1;
+    s.flip ^= 1;
+    if (sim->mlp) {
+        if ((rc = launch_learned_features(s, dt, sim->lfeat, sim->stream))) return rc;
+        if ((rc = mlp_infer(sim->mlp, sim->lfeat, sim->lout, s.N, sim->stream))) return rc;
+        if ((rc = launch_learned_apply(s, sim->cfg, dt, sim->lout, 1e3f, sim->stream))) return rc;
+        s.flip ^= 1;
     }
-    sim->t += dt;
-    sim->ctr.steps += 1;
-    sim->ctr.particle_steps += (double)s.N;
+    MH_CUDA(cudaStreamSynchronize(sim->stream));
+    std::vector<double> h(3 * s.Np);
+    MH_CUDA(cudaMemcpy(h.data(), s.x1, 3 * s.Np * sizeof(double), cudaMemcpyDeviceToHost));
+    from_soa(h, s.N, 1, s.Np, x);
+    MH_CUDA(cudaMemcpy(h.data(), s.v1, 3 * s.Np * sizeof(double), cudaMemcpyDeviceToHost));
+    from_soa(h, s.N, 1, s.Np, v);
+    return MH_OK;
+}
+
+int mh_collect_samples(mh_sim *sim, double dt, int n_iter, float *feats, float *targets)
+{
+    if (int rc = check_handle(sim)) return rc;
+    if (!feats || !targets || !(dt != 0.0) || !std::isfinite(dt) || n_iter < 1 || n_iter > 64) {
+        set_error("mh_collect_samples: device feats/targets, dt != 0, 1 <= n_iter <= 64");
+        return MH_EINVAL;
+    }
+    if (sim->batch || sim->cfg.step_mode != MH_STEP_SHARED) {
+        set_error("mh_collect_samples: shared-step simulations only");
+        return MH_EINVAL;
+    }
+    DeviceState &s = sim->s;
+    const size_t K = 2 * s.p;
+    if (!sim->lsave) MH_CUDA(cudaMalloc((void **)&sim->lsave, (6 + 3 * K) * s.Np * sizeof(double)));
+    double *xs = sim->lsave, *vs = xs + 3 * s.Np, *ds = vs + 3 * s.Np;
+    MH_CUDA(cudaMemcpyAsync(xs, s.x0, 3 * s.Np * sizeof(double), cudaMemcpyDeviceToDevice, sim->stream));
+    MH_CUDA(cudaMemcpyAsync(vs, s.v0, 3 * s.Np * sizeof(double), cudaMemcpyDeviceToDevice, sim->stream));
+    MH_CUDA(cudaMemcpyAsync(ds, s.d0, 3 * K * s.Np * sizeof(double), cudaMemcpyDeviceToDevice, sim->stream));
+    mh_mlp *keep = sim->mlp;
+    sim->mlp = nullptr;                 // samples come from the plain predictor and a converged corrector
+    int rc = shared_step(sim, dt, n_iter, -1.0, nullptr);
+    sim->mlp = keep;
+    if (rc) return rc;
+    rc = launch_collect(s, dt, xs, vs, ds, feats, targets, sim->stream);
+    if (rc) return rc;
+    sim->ctr.kernel_launches += 1;
+    MH_CUDA(cudaStreamSynchronize(sim->stream));
     return MH_OK;
 }
 

@@ -10,6 +10,8 @@
 
 #include "../../include/mh.h"
 
+struct mh_mlp;
+
 namespace mh {
 
 constexpr int kPad = 256;          // particle arrays are padded to a multiple of this
@@ -98,6 +100,11 @@ struct mh_sim {
     mh::DeviceState s;
     mh_counters ctr{};
     void *batch = nullptr;        // batched integrator bookkeeping (batch.cu), or null
+    // learned predictor (optional): network, feature/output buffers, saved state for sampling
+    mh_mlp *mlp = nullptr;
+    float *lfeat = nullptr, *lout = nullptr;
+    double *lsave = nullptr;      // x0, v0, d0 copies for mh_collect_samples
+    unsigned long long *conv = nullptr, *conv_host = nullptr;
 };
 
 namespace mh {
@@ -122,7 +129,15 @@ int launch_pair(int P, int precision, int64_t n_j, int64_t ld, const double *m, 
 
 // O(N) step kernels (integrator.cu): phase 0 = predict, 1 = correct.
 int launch_step_phase(const DeviceState &s, const mh_config &cfg, double dt, int phase, bool last,
-                      int split, cudaStream_t st);
+                      int split, cudaStream_t st, unsigned long long *conv = nullptr);
+int launch_collect(const DeviceState &s, double dt, const double *x0s, const double *v0s, const double *d0s,
+                   float *feats, float *targ, cudaStream_t st);
+int launch_learned_features(const DeviceState &s, double dt, float *feats, cudaStream_t st);
+int launch_learned_apply(const DeviceState &s, const mh_config &cfg, double dt, const float *y, float clamp,
+                         cudaStream_t st);
+// MLP inference (mlp.cu)
+int mlp_infer(mh_mlp *n, const float *X, float *Y, int64_t rows, cudaStream_t st);
+int mlp_dims(const mh_mlp *n, int *n_in, int *n_out);
 int launch_init_rows(const DeviceState &s, int have, cudaStream_t st);
 int launch_block_init(const DeviceState &s, const mh_config &cfg, cudaStream_t st);
 int launch_block_schedule(const DeviceState &s, const mh_config &cfg, cudaStream_t st);

@@ -32,6 +32,7 @@ struct StepArgs {
     int *flag;
     const unsigned long long *bound_rd;   // [x, v] grid bounds read by this kernel
     unsigned long long *bound_wr;         // [x, v] raised with this kernel's values
+    unsigned long long *conv = nullptr;   // optional [max |x_new - x_old|, max |x_new|] (double bits)
 };
 
 __device__ __forceinline__ void raise_bound(unsigned long long *slot, double val)
@@ -170,16 +171,207 @@ __global__ void k_correct(StepArgs a)
 #pragma unroll
             for (int k = 0; k < K; ++k)
                 a.d0[(3 * k + c) * a.ld + i] = k <= p ? d1[k] : hi[k - p - 1];
-        } else {
-            a.x1[c * a.ld + i] = xn;
-            a.v1[c * a.ld + i] = vn;
         }
     }
     if (live && !finite) atomicOr(a.flag, 1);
     if (!kLast) {
+        if (a.conv) {
+            // convergence of P(EC)^n: largest change of a position component, and the scale
+            double dx = 0.0, xm = 0.0;
+            if (live)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    dx = fmax(dx, fabs(x[c] - a.x1[c * a.ld + i]));
+                    xm = fmax(xm, fabs(x[c]));
+                }
+            if (!(dx <= 1e300)) dx = 1e300;
+            raise_bound(a.conv + 0, dx);
+            raise_bound(a.conv + 1, xm);
+        }
+        if (live)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                a.x1[c * a.ld + i] = x[c];
+                a.v1[c * a.ld + i] = v[c];
+            }
         track_bounds(a, live, x, v);
         if (live) write_input<p>(a, i, x, v, ad);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Learned residual on the Taylor predictor (reading R13 of the design notes).
+// Frame: e1 = a/|a|, e2 along the part of a-dot normal to a, e3 = e1 x e2.
+// Features u_k = R^T F_k / (|a| sigma^k), F_k = h^k a^(k)/k!, then 1 + log10(sigma),
+// sigma = max_{1<=k<2p} (|F_k|/|F_0|)^(1/k) (the shortest time scale of the stack, so |u_k| <= 1);
+// targets/outputs y = (R^T dx / (|a| h^2 sigma^6), R^T dv / (|a| h sigma^6)).
+// ---------------------------------------------------------------------------
+
+constexpr double kSigmaMax = 0.5;
+
+struct Frame {
+    double R[3][3];   // R[i][c]: component c of e_i
+    double na, sigma;
+    bool ok;
+};
+
+// Frame and scales of body i from its derivative stack at t0.
+template <int p>
+__device__ Frame make_frame(const double *d0, int64_t ld, int64_t i, double h)
+{
+    Frame f{};
+    double a[3], j[3];
+    for (int c = 0; c < 3; ++c) {
+        a[c] = d0[(0 * 3 + c) * ld + i];
+        j[c] = d0[(1 * 3 + c) * ld + i];
+    }
+    f.na = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    f.sigma = 0.0;
+    if (f.na > 0.0) {
+        double hk = h;
+#pragma unroll
+        for (int k = 1; k < 2 * p; ++k) {
+            const double dx = d0[(3 * k) * ld + i], dy = d0[(3 * k + 1) * ld + i], dz = d0[(3 * k + 2) * ld + i];
+            const double r = sqrt(dx * dx + dy * dy + dz * dz) * hk * inv_fact(k) / f.na;
+            f.sigma = fmax(f.sigma, pow(r, 1.0 / k));
+            hk *= h;
+        }
+    }
+    f.ok = f.na > 0.0 && f.sigma > 0.0 && f.sigma <= kSigmaMax;
+    if (!f.ok) return f;
+    double e1[3] = {a[0] / f.na, a[1] / f.na, a[2] / f.na};
+    const double pj = j[0] * e1[0] + j[1] * e1[1] + j[2] * e1[2];
+    double u[3] = {j[0] - pj * e1[0], j[1] - pj * e1[1], j[2] - pj * e1[2]};
+    double nu = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    if (!(nu > 1e-300)) {
+        const double alt[3] = {fabs(e1[0]) < 0.9 ? 1.0 : 0.0, fabs(e1[0]) < 0.9 ? 0.0 : 1.0, 0.0};
+        const double pa = alt[0] * e1[0] + alt[1] * e1[1];
+        for (int c = 0; c < 3; ++c) u[c] = alt[c] - pa * e1[c];
+        nu = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    }
+    double e2[3] = {u[0] / nu, u[1] / nu, u[2] / nu};
+    double e3[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    for (int c = 0; c < 3; ++c) {
+        f.R[0][c] = e1[c];
+        f.R[1][c] = e2[c];
+        f.R[2][c] = e3[c];
+    }
+    return f;
+}
+
+template <int p>
+__device__ void write_features(const Frame &f, const double *d0, int64_t ld, int64_t i, double h, float *out)
+{
+    constexpr int K = 2 * p;
+    double hk = 1.0, sk = 1.0;
+    for (int k = 0; k < K; ++k) {
+        double F[3];
+        for (int c = 0; c < 3; ++c) F[c] = d0[(3 * k + c) * ld + i] * hk * inv_fact(k);
+        for (int e = 0; e < 3; ++e) {
+            const double r = f.R[e][0] * F[0] + f.R[e][1] * F[1] + f.R[e][2] * F[2];
+            out[3 * k + e] = f.ok ? (float)(r / (f.na * sk)) : 0.0f;
+        }
+        hk *= h;
+        sk *= f.ok ? f.sigma : 1.0;
+    }
+    out[3 * K] = f.ok ? (float)(1.0 + log10(f.sigma)) : 0.0f;
+}
+
+// Training samples: features at t0 and the scaled converged-minus-predicted residual.
+template <int p>
+__global__ void k_collect(int64_t N, int64_t ld, double dt, const double *x0s, const double *v0s,
+                          const double *d0s, const double *x1, const double *v1, float *feats, float *targ)
+{
+    constexpr int K = 2 * p;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double h = 0.5 * dt;
+    const Frame f = make_frame<p>(d0s, ld, i, h);
+    write_features<p>(f, d0s, ld, i, h, feats + i * (3 * K + 1));
+    double dx[3], dv[3];
+    for (int c = 0; c < 3; ++c) {
+        double dk[K], xp, vp, ad[p > 1 ? p - 1 : 1];
+        for (int k = 0; k < K; ++k) dk[k] = d0s[(3 * k + c) * ld + i];
+        predict_comp<p>(dt, dk, x0s[c * ld + i], v0s[c * ld + i], xp, vp, ad);
+        dx[c] = x1[c * ld + i] - xp;
+        dv[c] = v1[c * ld + i] - vp;
+    }
+    double s6 = f.sigma * f.sigma * f.sigma;
+    s6 *= s6;
+    const double den = f.na * s6;
+    for (int e = 0; e < 3; ++e) {
+        const double rx = f.R[e][0] * dx[0] + f.R[e][1] * dx[1] + f.R[e][2] * dx[2];
+        const double rv = f.R[e][0] * dv[0] + f.R[e][1] * dv[1] + f.R[e][2] * dv[2];
+        targ[i * 6 + e] = f.ok ? (float)(rx / (den * h * h)) : 0.0f;
+        targ[i * 6 + 3 + e] = f.ok ? (float)(rv / (den * h)) : 0.0f;
+    }
+}
+
+// Features of every body for the predictor (written to feats [N x 3K]).
+template <int p>
+__global__ void k_learned_features(int64_t N, int64_t ld, double dt, const double *d0, float *feats)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double h = 0.5 * dt;
+    const Frame f = make_frame<p>(d0, ld, i, h);
+    write_features<p>(f, d0, ld, i, h, feats + i * (6 * p + 1));
+}
+
+// Adds the network's residual to the prediction (bodies whose frame is defined;
+// the plain prediction otherwise) and rewrites every evaluation input.  The
+// residual (dx, dv) is read as the two next Taylor terms: the derivatives
+// a^(2p), a^(2p+1) that produce exactly (dx, dv) at t0 + dt, which then extend
+// the predicted a^(q) (q <= p-2) too, so the predicted x, v, a, a-dot stay one
+// consistent polynomial.
+template <int p>
+__global__ void k_learned_apply(StepArgs a, const float *y, float clamp)
+{
+    constexpr int K = 2 * p;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i0 < a.N;
+    const int64_t i = live ? i0 : a.N - 1;
+    const double dt = a.dt, h = 0.5 * dt;
+    const Frame f = make_frame<p>(a.d0, a.ld, i, h);
+    double x[3], v[3], ad[p > 1 ? p - 1 : 1][3];
+    for (int c = 0; c < 3; ++c) {
+        x[c] = a.jrec[(0 + c) * a.ld + i];
+        v[c] = a.jrec[(3 + c) * a.ld + i];
+        for (int q = 0; q + 2 <= p; ++q) ad[q][c] = a.jrec[(6 + 3 * q + c) * a.ld + i];
+    }
+    if (f.ok) {
+        double s6 = f.sigma * f.sigma * f.sigma;
+        s6 *= s6;
+        const double den = f.na * s6;
+        double yx[3], yv[3];
+        const double cl = (double)clamp;
+        for (int e = 0; e < 3; ++e) {
+            yx[e] = fmin(fmax((double)y[i * 6 + e], -cl), cl);
+            yv[e] = fmin(fmax((double)y[i * 6 + 3 + e], -cl), cl);
+        }
+        // Taylor weights t_n = dt^n / n! of the two next terms
+        double tw[K + 4];
+        tw[0] = 1.0;
+        for (int n = 1; n < K + 4; ++n) tw[n] = tw[n - 1] * dt / n;
+        // dx = t_{K+2} A + t_{K+3} B,  dv = t_{K+1} A + t_{K+2} B
+        const double det = tw[K + 2] * tw[K + 2] - tw[K + 3] * tw[K + 1];
+        for (int c = 0; c < 3; ++c) {
+            const double dx = (f.R[0][c] * yx[0] + f.R[1][c] * yx[1] + f.R[2][c] * yx[2]) * den * h * h;
+            const double dv = (f.R[0][c] * yv[0] + f.R[1][c] * yv[1] + f.R[2][c] * yv[2]) * den * h;
+            const double A = (dx * tw[K + 2] - dv * tw[K + 3]) / det;
+            const double B = (dv * tw[K + 2] - dx * tw[K + 1]) / det;
+            x[c] += dx;
+            v[c] += dv;
+            for (int q = 0; q + 2 <= p; ++q) ad[q][c] += tw[K - q] * A + tw[K + 1 - q] * B;
+        }
+    }
+    if (live)
+        for (int c = 0; c < 3; ++c) {
+            a.x1[c * a.ld + i] = x[c];
+            a.v1[c * a.ld + i] = v[c];
+        }
+    track_bounds(a, live, x, v);
+    if (live) write_input<p>(a, i, x, v, ad);
 }
 
 // ---------------------------------------------------------------------------
@@ -484,6 +676,47 @@ static BlockArgs block_args(const DeviceState &s, const mh_config &cfg, long lon
     return b;
 }
 
+int launch_collect(const DeviceState &s, double dt, const double *x0s, const double *v0s, const double *d0s,
+                   float *feats, float *targ, cudaStream_t st)
+{
+    const unsigned g = blocks_for(s.N, 128);
+    switch (s.p) {
+    case 1: k_collect<1><<<g, 128, 0, st>>>(s.N, s.Np, dt, x0s, v0s, d0s, s.x0, s.v0, feats, targ); break;
+    case 2: k_collect<2><<<g, 128, 0, st>>>(s.N, s.Np, dt, x0s, v0s, d0s, s.x0, s.v0, feats, targ); break;
+    case 3: k_collect<3><<<g, 128, 0, st>>>(s.N, s.Np, dt, x0s, v0s, d0s, s.x0, s.v0, feats, targ); break;
+    }
+    MH_LAUNCHED("k_collect");
+    return MH_OK;
+}
+
+int launch_learned_features(const DeviceState &s, double dt, float *feats, cudaStream_t st)
+{
+    const unsigned g = blocks_for(s.N, 128);
+    switch (s.p) {
+    case 1: k_learned_features<1><<<g, 128, 0, st>>>(s.N, s.Np, dt, s.d0, feats); break;
+    case 2: k_learned_features<2><<<g, 128, 0, st>>>(s.N, s.Np, dt, s.d0, feats); break;
+    case 3: k_learned_features<3><<<g, 128, 0, st>>>(s.N, s.Np, dt, s.d0, feats); break;
+    }
+    MH_LAUNCHED("k_learned_features");
+    return MH_OK;
+}
+
+int launch_learned_apply(const DeviceState &s, const mh_config &cfg, double dt, const float *y, float clamp,
+                         cudaStream_t st)
+{
+    StepArgs a{s.N, s.Np, dt, s.m, s.x0, s.v0, s.d0, s.x1, s.v1, s.jrec, s.jrec32, s.part,
+               0, cfg.precision, cfg.beta_mode, s.flag,
+               s.bound ? s.bound + 2 * s.flip : nullptr, s.bound ? s.bound + 2 * (1 - s.flip) : nullptr};
+    const unsigned g = blocks_for(s.N, 128);
+    switch (s.p) {
+    case 1: k_learned_apply<1><<<g, 128, 0, st>>>(a, y, clamp); break;
+    case 2: k_learned_apply<2><<<g, 128, 0, st>>>(a, y, clamp); break;
+    case 3: k_learned_apply<3><<<g, 128, 0, st>>>(a, y, clamp); break;
+    }
+    MH_LAUNCHED("k_learned_apply");
+    return MH_OK;
+}
+
 int launch_block_init(const DeviceState &s, const mh_config &cfg, cudaStream_t st)
 {
     k_block_init_levels<<<blocks_for(s.N, 128), 128, 0, st>>>(s.N, s.Np, s.d0, block_args(s, cfg, 0, 0));
@@ -521,11 +754,12 @@ int launch_block_phase(const DeviceState &s, const mh_config &cfg, long long T_n
 
 // phase 0: predict; phase 1: correct (last = final pass of the step).
 int launch_step_phase(const DeviceState &s, const mh_config &cfg, double dt, int phase, bool last,
-                      int split, cudaStream_t st)
+                      int split, cudaStream_t st, unsigned long long *conv)
 {
     StepArgs a{s.N, s.Np, dt, s.m, s.x0, s.v0, s.d0, s.x1, s.v1, s.jrec, s.jrec32, s.part,
                split, cfg.precision, cfg.beta_mode, s.flag,
-               s.bound ? s.bound + 2 * s.flip : nullptr, s.bound ? s.bound + 2 * (1 - s.flip) : nullptr};
+               s.bound ? s.bound + 2 * s.flip : nullptr, s.bound ? s.bound + 2 * (1 - s.flip) : nullptr,
+               conv};
     switch (s.p) {
     case 1: return launch_step_kernels<1>(a, phase, last, st);
     case 2: return launch_step_kernels<2>(a, phase, last, st);
