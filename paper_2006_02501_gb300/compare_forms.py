@@ -1,0 +1,222 @@
+"""Measurements across the forms of the integrator (one GPU).
+
+    python -m paper_2006_02501_gb300.compare_forms ecc      # FP64 vs FP32-pair at equal ecc-vector error
+    python -m paper_2006_02501_gb300.compare_forms block    # block steps, FP32-pair vs FP64, N = 262144
+    python -m paper_2006_02501_gb300.compare_forms batch    # 4096 planetary systems, 10^4 steps
+    python -m paper_2006_02501_gb300.compare_forms learned  # learned predictor on the N = 65536 disc
+
+Each prints JSON lines.  Throughputs are timed with CUDA events on the
+simulation's stream; pair interactions and particle steps come from the
+library's counters.  Eccentricity-vector error: the median over the stars of
+|e_i - e_i^ref| at the end time, e about the SMBH (Appendix A, Eq. A1), with the
+reference an 8th-order FP64 run at a quarter of the step and P(EC)^4.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+
+def _setup():
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import torch
+    import paper_2006_02501_gb300 as mh
+    from paper_2006_02501_gb300 import inputs
+    mh.build_library()
+    torch.cuda.set_device(0)
+    return torch, mh, inputs
+
+
+def _timed(torch, stream, fn):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) * 1e-3
+
+
+def _ecc_err(e, e_ref):
+    return float(np.median(np.linalg.norm(e[1:] - e_ref[1:], axis=1)))
+
+
+def run_ecc(args):
+    """SMBH disc (N stars + SMBH), 8th order, shared steps P(EC)^3: FP64 and
+    FP32-pair forms at dt0 and dt0/2 over the same time, against a reference."""
+    torch, mh, I = _setup()
+    st = torch.cuda.Stream()
+    m, x, v = I.smbh_disc(seed=2, N=args.N)
+    eps, dt0, nst = 1e-4, 2 * np.pi * 1e-3, args.steps
+    T = nst * dt0
+    with mh.Simulation(8, m, x, v, eps, stream=st) as ref:
+        ref.step(dt0 / 4, 4, nsteps=4 * nst)
+        _, e_ref = ref.diagnostics(central=0)
+    rows = []
+    for prec, name in ((mh.MH_PREC_FP64, "fp64"), (mh.MH_PREC_FP32PAIR, "fp32pair")):
+        for div in (1, 2):
+            dt = dt0 / div
+            with mh.Simulation(8, m, x, v, eps, stream=st, precision=prec) as s:
+                c0 = s.counters()
+                sec = _timed(torch, st, lambda: s.step(dt, 3, nsteps=nst * div))
+                c1 = s.counters()
+                E, e = s.diagnostics(central=0)
+            row = {"form": name, "dt": dt, "steps": nst * div, "time_s": sec,
+                   "particle_steps_per_s": (c1["particle_steps"] - c0["particle_steps"]) / sec,
+                   "pair_interactions_per_s": (c1["pair_interactions"] - c0["pair_interactions"]) / sec,
+                   "ecc_err_median": _ecc_err(e, e_ref), "N": len(m), "t_end": T}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+    # equal-error comparison: the error each form reaches at dt0 and dt0/2, and the
+    # throughput of each at the finer step that reaches the FP64 error at dt0
+    target = [r for r in rows if r["form"] == "fp64" and r["dt"] == dt0][0]["ecc_err_median"]
+    summary = {"equal_error_target": target}
+    for name in ("fp64", "fp32pair"):
+        ok = [r for r in rows if r["form"] == name and r["ecc_err_median"] <= target * 1.05]
+        best = max(ok, key=lambda r: r["particle_steps_per_s"]) if ok else None
+        summary[name] = None if best is None else {k: best[k] for k in ("dt", "particle_steps_per_s",
+                                                                          "ecc_err_median")}
+    print(json.dumps({"summary": summary}), flush=True)
+
+
+def run_block(args):
+    """Block time steps on the SMBH disc at N = 262144: FP32-pair and FP64 forms
+    from the same start over args.dtmax_units x dt_max, 8th and 6th order."""
+    torch, mh, I = _setup()
+    st = torch.cuda.Stream()
+    m, x, v = I.smbh_disc(seed=3, N=args.N)
+    eps = 1e-4
+    blk = dict(dt_max=2.0 ** -5, k_max=12, eta=0.05)
+    span = args.dtmax_units * blk["dt_max"]
+    for order in args.orders:
+        out = {}
+        for prec, name in ((mh.MH_PREC_FP32PAIR, "fp32pair"), (mh.MH_PREC_FP64, "fp64")):
+            with mh.Simulation(order, m, x, v, eps, stream=st, precision=prec, block=blk) as s:
+                lv = s.levels()
+                E0 = s.energy()
+                c0 = s.counters()
+                sec = _timed(torch, st, lambda: s.step(span, 3))
+                c1 = s.counters()
+                E1, e = s.diagnostics(central=0)
+            out[name] = {"time_s": sec, "particle_steps": c1["particle_steps"] - c0["particle_steps"],
+                         "particle_steps_per_s": (c1["particle_steps"] - c0["particle_steps"]) / sec,
+                         "pair_interactions_per_s": (c1["pair_interactions"] - c0["pair_interactions"]) / sec,
+                         "block_steps": c1["steps"] - c0["steps"], "dE_rel": E1 / E0 - 1,
+                         "levels": np.bincount(lv, minlength=blk["k_max"] + 1).tolist(), "e": e}
+        diff = abs(out["fp32pair"]["dE_rel"] - out["fp64"]["dE_rel"])
+        ecc_diff = _ecc_err(out["fp32pair"].pop("e"), out["fp64"].pop("e"))
+        print(json.dumps({"order": order, "N": len(m), "span": span, "fp32pair": out["fp32pair"],
+                          "fp64": out["fp64"], "dE_rel_difference": diff,
+                          "ecc_median_difference_fp32_vs_fp64": ecc_diff}), flush=True)
+
+
+def run_batch(args):
+    """4096 planetary systems (3..64 bodies), 6th order, P(EC)^2, dt_s = P_min/128,
+    10^4 steps in one launch; the single-system path on a subset for comparison."""
+    torch, mh, I = _setup()
+    st = torch.cuda.Stream()
+    off, m, x, v, pmin = I.planetary_systems(seed=4, S=args.S)
+    dt = pmin / 128.0
+    eps = 1e-8
+    with mh.Batch(6, off, m, x, v, dt, eps, stream=st) as b:
+        t0 = time.perf_counter()
+        w, o = b.tune(probe_steps=16, n_iter=2)
+        tune_s = time.perf_counter() - t0
+        E0 = b.energies()
+        c0 = b.counters()
+        sec = _timed(torch, st, lambda: b.step(args.steps, 2))
+        c1 = b.counters()
+        E1 = b.energies()
+    sizes = np.diff(off)
+    pairs = float((sizes * (sizes - 1)).sum()) * 2 * args.steps
+    dE = np.abs(E1 / E0 - 1)
+    row = {"form": "batched", "systems": args.S, "bodies": int(off[-1]), "steps": args.steps, "time_s": sec,
+           "particle_steps_per_s": (c1["particle_steps"] - c0["particle_steps"]) / sec,
+           "pair_interactions_per_s": pairs / sec, "autotune": {"warps": w, "order": o, "seconds": tune_s},
+           "dE_rel_median": float(np.median(dE)), "dE_rel_max": float(dE.max())}
+    print(json.dumps(row), flush=True)
+    # the single-system path (one simulation per system) on a subset
+    k_sub, n_sub = args.subset, args.subset_steps
+    tot_ps, tot_s = 0.0, 0.0
+    for k in range(k_sub):
+        sl = slice(off[k], off[k + 1])
+        with mh.Simulation(6, m[sl], x[sl], v[sl], eps, stream=st) as s:
+            s.step(dt[k], 2, nsteps=5)
+            sec = _timed(torch, st, lambda: s.step(dt[k], 2, nsteps=n_sub))
+            tot_ps += (off[k + 1] - off[k]) * n_sub
+            tot_s += sec
+    print(json.dumps({"form": "single-system path (subset)", "systems": k_sub, "steps": n_sub,
+                      "particle_steps_per_s": tot_ps / tot_s}), flush=True)
+
+
+def run_learned(args):
+    """Learned predictor: trained on converged steps of N-star discs (seeds 100+),
+    evaluated on a fresh seed-1000 disc: passes to a 1e-13 tolerance."""
+    torch, mh, I = _setup()
+    from paper_2006_02501_gb300 import train_predictor as tp
+    st = torch.cuda.Stream()
+    eps, dt, tol = 1e-4, 2 * np.pi * 1e-3, 1e-13
+    Fs, Ts = [], []
+    rows = 0
+    seed = 100
+    t0 = time.perf_counter()
+    while rows < args.samples:
+        m, x, v = I.smbh_disc(seed=seed, N=args.N)
+        with mh.Simulation(8, m, x, v, eps, stream=st) as s:
+            steps = min(args.steps_per_disc, -(-(args.samples - rows) // len(m)))
+            F, T = tp.collect(s, dt, steps=steps, n_iter=10)
+        Fs.append(F)
+        Ts.append(T)
+        rows += F.shape[0]
+        seed += 1
+    collect_s = time.perf_counter() - t0
+    F, T = torch.cat(Fs), torch.cat(Ts)
+    t0 = time.perf_counter()
+    net = tp.fit((F, T), epochs=args.epochs, seed=0)
+    train_s = time.perf_counter() - t0
+    m, x, v = I.smbh_disc(seed=1000, N=args.N)
+    res = {}
+    for name, use in (("plain", False), ("learned", True)):
+        with mh.Simulation(8, m, x, v, eps, stream=st) as s:
+            if use:
+                s.set_predictor(net)
+            passes = [s.step_converge(dt, tol, 20) for _ in range(args.eval_steps)]
+            _, xs, _, _ = s.sync()
+        res[name] = {"mean_passes": float(np.mean(passes)), "passes": passes}
+        res[name + "_x"] = xs
+    dx = float(np.abs(res.pop("plain_x") - res.pop("learned_x")).max())
+    print(json.dumps({"N": len(m), "training_rows": int(F.shape[0]), "collect_s": collect_s, "train_s": train_s,
+                      "tol": tol, **res, "max_state_difference": dx}), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    a = sub.add_parser("ecc")
+    a.add_argument("--N", type=int, default=16384)
+    a.add_argument("--steps", type=int, default=40)
+    b = sub.add_parser("block")
+    b.add_argument("--N", type=int, default=262144)
+    b.add_argument("--dtmax-units", type=int, default=1)
+    b.add_argument("--orders", type=int, nargs="+", default=[8, 6])
+    c = sub.add_parser("batch")
+    c.add_argument("--S", type=int, default=4096)
+    c.add_argument("--steps", type=int, default=10000)
+    c.add_argument("--subset", type=int, default=16)
+    c.add_argument("--subset-steps", type=int, default=200)
+    d = sub.add_parser("learned")
+    d.add_argument("--N", type=int, default=65536)
+    d.add_argument("--samples", type=int, default=1_000_000)
+    d.add_argument("--steps-per-disc", type=int, default=8)
+    d.add_argument("--epochs", type=int, default=30)
+    d.add_argument("--eval-steps", type=int, default=12)
+    args = ap.parse_args()
+    {"ecc": run_ecc, "block": run_block, "batch": run_batch, "learned": run_learned}[args.cmd](args)
+
+
+if __name__ == "__main__":
+    main()
