@@ -155,7 +155,10 @@ def run_batch(args):
 
 def run_learned(args):
     """Learned predictor: trained on converged steps of N-star discs (seeds 100+),
-    evaluated on a fresh seed-1000 disc: passes to a 1e-13 tolerance."""
+    evaluated on a fresh seed-1000 disc: fraction of bodies converged to 1e-13
+    (relative to the 16-pass result) after n passes, plain vs learned.  A global
+    max-norm criterion is not reachable on this disc: star-star passages faster
+    than dt keep a few bodies from contracting at all."""
     torch, mh, I = _setup()
     from paper_2006_02501_gb300 import train_predictor as tp
     st = torch.cuda.Stream()
@@ -178,19 +181,31 @@ def run_learned(args):
     t0 = time.perf_counter()
     net = tp.fit((F, T), epochs=args.epochs, seed=0)
     train_s = time.perf_counter() - t0
+    # evaluation: a fresh disc, a few plain steps so the stack holds interpolated
+    # derivatives, then from one state: the fraction of bodies whose position after
+    # n passes is within tol (relative) of the 16-pass result, plain vs learned
     m, x, v = I.smbh_disc(seed=1000, N=args.N)
-    res = {}
+    with mh.Simulation(8, m, x, v, eps, stream=st) as s:
+        s.step(dt, 3, nsteps=3)
+        t, x0, v0, d0 = s.sync()
+        s.step(dt, 16)
+        _, xr, _, _ = s.sync()
+    scale = np.linalg.norm(xr, axis=1)
+    res = {"n": list(range(1, args.max_passes + 1))}
     for name, use in (("plain", False), ("learned", True)):
-        with mh.Simulation(8, m, x, v, eps, stream=st) as s:
-            if use:
-                s.set_predictor(net)
-            passes = [s.step_converge(dt, tol, 20) for _ in range(args.eval_steps)]
-            _, xs, _, _ = s.sync()
-        res[name] = {"mean_passes": float(np.mean(passes)), "passes": passes}
-        res[name + "_x"] = xs
-    dx = float(np.abs(res.pop("plain_x") - res.pop("learned_x")).max())
+        frac = []
+        for n in res["n"]:
+            with mh.Simulation(8, m, x0, v0, eps, stream=st) as s:
+                s.set_state(x0, v0, d0, t=t)
+                if use:
+                    s.set_predictor(net)
+                s.step(dt, n)
+                _, xs, _, _ = s.sync()
+            err = np.linalg.norm(xs - xr, axis=1)
+            frac.append(float(np.mean(err <= tol * scale)))
+        res[name + "_fraction_converged"] = frac
     print(json.dumps({"N": len(m), "training_rows": int(F.shape[0]), "collect_s": collect_s, "train_s": train_s,
-                      "tol": tol, **res, "max_state_difference": dx}), flush=True)
+                      "tol": tol, **res}), flush=True)
 
 
 def main():
@@ -213,7 +228,7 @@ def main():
     d.add_argument("--samples", type=int, default=1_000_000)
     d.add_argument("--steps-per-disc", type=int, default=8)
     d.add_argument("--epochs", type=int, default=30)
-    d.add_argument("--eval-steps", type=int, default=12)
+    d.add_argument("--max-passes", type=int, default=6)
     args = ap.parse_args()
     {"ecc": run_ecc, "block": run_block, "batch": run_batch, "learned": run_learned}[args.cmd](args)
 
