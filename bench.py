@@ -55,7 +55,9 @@ PEAK_FP32 = N_SM * 128 * 2 * SM_MAX_MHZ * 1e6
 PEAK_FP64 = 1.25e12
 # DRAM traffic per launch of the dominant kernel from one ncu capture
 # (profiles/); valid only while the kernel source is the one captured.
-TRAFFIC = {"file": "paper_2006_02501_gb300/csrc/pair.cu", "sha256": None, "bytes_per_launch": None}
+TRAFFIC = {"file": "paper_2006_02501_gb300/csrc/pair.cu",
+           "sha256": "bd67eb0e518cf354cb7064cdfd8b8a520508681164ae3a4d2fb41a5d6a018059",
+           "bytes_per_launch": 8.23e6 + 25.72e6}   # profiles/k_pair_fp64_disc_N65536_order8_dram.md
 
 
 def _sha(path):
@@ -202,6 +204,17 @@ def time_steps(sim, stream, torch, steps, flush):
     return times
 
 
+def time_steps_batch(b, stream, torch, steps):
+    """Seconds of one persistent batched launch of `steps` steps (CUDA events)."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(steps, 2)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) * 1e-3
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2006_02501_gb300 as mh
@@ -285,6 +298,21 @@ def run_ours(args, rank, world, local_rank):
     pair32_ms = (d1["pair_kernel_ms"] - d0["pair_kernel_ms"]) / max(d1["pair_kernel_timed"] - d0["pair_kernel_timed"], 1)
     ach32 = FLOPS_PER_PAIR[ORDER] * N * (N - 1) / (pair32_ms * 1e-3)
 
+    # ---- batched form: 4096 planetary systems, 6th order, 10^4 steps in one launch ----
+    from paper_2006_02501_gb300 import inputs as _inp
+    off, bm, bx, bv, pmin = _inp.planetary_systems(seed=4, S=4096)
+    with mh.Batch(6, off, bm, bx, bv, pmin / 128.0, 1e-8, stream=stream) as b:
+        b.tune(probe_steps=16, n_iter=2)
+        b.step(10, 2)
+        g0 = b.counters()
+        barrier()
+        tb = time_steps_batch(b, stream, torch, 10000)
+        barrier()
+        g1 = b.counters()
+    sizes = np.diff(off)
+    batch_pairs = float((sizes * (sizes - 1)).sum()) * 2 * 10000
+    batch_ps = (g1["particle_steps"] - g0["particle_steps"]) / tb
+
     if rank != 0:
         return
     cpu = None
@@ -316,7 +344,12 @@ def run_ours(args, rank, world, local_rank):
             "steps": k32, "pair_kernel": "k_pair_fp32<3>", "launch_ms": pair32_ms,
             "achieved_tflops": ach32 / 1e12, "peak_tflops": PEAK_FP32 / 1e12,
             "frac": ach32 / PEAK_FP32,
-            "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"}},
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"},
+            "batched": {
+            "workload": "4096 planetary systems (3..64 bodies), 6th order FP64, P(EC)^2, dt_s = P_min/128, "
+                        "10^4 steps in one launch",
+            "particle_steps_per_s": world * batch_ps, "pair_interactions_per_s": world * batch_pairs / tb,
+            "seconds": tb}},
     }
     print(json.dumps(line), flush=True)
 
