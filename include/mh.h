@@ -96,6 +96,9 @@ typedef struct {
     double pair_kernel_ms;       /* with timing on: summed device time of the O(N^2)
                                     evaluation kernels (CUDA events around each launch) */
     int64_t pair_kernel_timed;   /* number of evaluation launches in pair_kernel_ms */
+    int32_t pair_bodies_per_thread;  /* precision form: i-bodies per thread of the last
+                                        evaluation, as chosen by the autotuner (1 or 2) */
+    int32_t pair_tune_ms_x1000[2];   /* the tuner's last timings of the two variants, microseconds */
 } mh_counters;
 
 /* Fill *cfg with the defaults listed above. */

@@ -180,7 +180,9 @@ class Simulation:
     def counters(self) -> dict:
         n, o, c = ctypes.c_int64(), ctypes.c_int(), _capi.Counters()
         check(_capi.lib().mh_info(self._h, ctypes.byref(n), ctypes.byref(o), ctypes.byref(c)))
-        return {f: getattr(c, f) for f, _ in c._fields_}
+        out = {f: getattr(c, f) for f, _ in c._fields_}
+        out["pair_tune_ms_x1000"] = list(out["pair_tune_ms_x1000"])
+        return out
 
 
 class MLP:

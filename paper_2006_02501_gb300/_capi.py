@@ -53,7 +53,8 @@ class Counters(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("evaluations", ctypes.c_int64),
                 ("pair_interactions", ctypes.c_double), ("particle_steps", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("pair_kernel_ms", ctypes.c_double),
-                ("pair_kernel_timed", ctypes.c_int64)]
+                ("pair_kernel_timed", ctypes.c_int64), ("pair_bodies_per_thread", ctypes.c_int32),
+                ("pair_tune_ms_x1000", ctypes.c_int32 * 2)]
 
 
 class MHError(RuntimeError):

@@ -4,7 +4,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <new>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -111,16 +113,66 @@ int timed_event_pair(mh_sim *sim, std::pair<cudaEvent_t, cudaEvent_t> *out)
     return MH_OK;
 }
 
+// Autotuner of the precision-form evaluation: i-bodies per thread (1 or 2) per
+// (P, number of evaluated bodies rounded up to a power of two, sources, device).
+// Both variants give bit-identical sums; the first evaluation of a class times
+// each once with CUDA events and keeps the faster.
+std::map<std::tuple<int, int64_t, int64_t, int>, int> g_ipt_cache;
+
+int tuned_ipt(mh_sim *sim, int P, int64_t n_i, const int *ilist, int *ipt)
+{
+    DeviceState &s = sim->s;
+    *ipt = 1;
+    if (n_i < 8192) return MH_OK;          // a single wave either way: keep one body per thread
+    int64_t bucket = 1;
+    while (bucket < n_i) bucket <<= 1;
+    const auto key = std::make_tuple(P, bucket, s.N, sim->device);
+    auto it = g_ipt_cache.find(key);
+    if (it != g_ipt_cache.end()) {
+        *ipt = it->second;
+        return MH_OK;
+    }
+    cudaEvent_t e0, e1, e2;
+    MH_CUDA(cudaEventCreate(&e0));
+    MH_CUDA(cudaEventCreate(&e1));
+    MH_CUDA(cudaEventCreate(&e2));
+    float ms[2] = {0.0f, 0.0f};
+    for (int v = 1; v <= 2; ++v) {
+        const PairPlan pl = plan_pair(P, MH_PREC_FP32PAIR, n_i, s.N, sim->cfg.split_j, sim->device, v);
+        if (int rc = ensure_part(s, (size_t)(pl.split + 1) * (P + 1) * 3 * s.Np, sim->stream)) return rc;
+        MH_CUDA(cudaEventRecord(v == 1 ? e0 : e1, sim->stream));
+        if (int rc = launch_pair(P, MH_PREC_FP32PAIR, s.N, s.Np, s.m, s.jrec, s.jrec32, sim->eps, sim->cfg.G, 0,
+                                 n_i, s.part, s.Np, pl, sim->stream, ilist))
+            return rc;
+        MH_CUDA(cudaEventRecord(v == 1 ? e1 : e2, sim->stream));
+    }
+    MH_CUDA(cudaEventSynchronize(e2));
+    MH_CUDA(cudaEventElapsedTime(&ms[0], e0, e1));
+    MH_CUDA(cudaEventElapsedTime(&ms[1], e1, e2));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    *ipt = ms[1] < ms[0] ? 2 : 1;
+    g_ipt_cache[key] = *ipt;
+    sim->ctr.pair_tune_ms_x1000[0] = (int32_t)(ms[0] * 1000.0f);
+    sim->ctr.pair_tune_ms_x1000[1] = (int32_t)(ms[1] * 1000.0f);
+    return MH_OK;
+}
+
 // One O(N^2) evaluation of a^(0..P) for all bodies into s.part; returns S via *split.
 int evaluate(mh_sim *sim, int P, int precision, int *split)
 {
     DeviceState &s = sim->s;
+    int ipt = 1;
+    if (precision == MH_PREC_FP32PAIR)
+        if (int rc = tuned_ipt(sim, P, s.N, nullptr, &ipt)) return rc;
+    sim->ctr.pair_bodies_per_thread = ipt;
     std::pair<cudaEvent_t, cudaEvent_t> ev{};
     if (sim->timing) {
         if (int rc = timed_event_pair(sim, &ev)) return rc;
         MH_CUDA(cudaEventRecord(ev.first, sim->stream));
     }
-    const PairPlan pl = plan_pair(P, precision, s.N, s.N, sim->cfg.split_j, sim->device);
+    const PairPlan pl = plan_pair(P, precision, s.N, s.N, sim->cfg.split_j, sim->device, ipt);
     const bool heavy = precision == MH_PREC_FP32PAIR && s.n_heavy > 0;
     const int slots = pl.split + (heavy ? 1 : 0);
     int rc = ensure_part(s, (size_t)slots * (P + 1) * 3 * s.Np, sim->stream);
@@ -413,8 +465,11 @@ static int block_advance(mh_sim *sim, double dt, int n_iter)
         if (int rc = launch_block_phase(s, c, T_next, n_act, 0, false, 0, sim->stream)) return rc;
         s.flip ^= 1;
         sim->ctr.kernel_launches += 1;
+        int ipt = 1;
+        if (prec == MH_PREC_FP32PAIR)
+            if (int rc = tuned_ipt(sim, s.p, n_act, s.act, &ipt)) return rc;
         for (int it = 0; it < n_iter; ++it) {
-            const PairPlan pl = plan_pair(s.p, prec, n_act, s.N, c.split_j, sim->device);
+            const PairPlan pl = plan_pair(s.p, prec, n_act, s.N, c.split_j, sim->device, ipt);
             const bool heavy = prec == MH_PREC_FP32PAIR && s.n_heavy > 0;
             const int slots = pl.split + (heavy ? 1 : 0);
             if (int rc = ensure_part(s, (size_t)slots * (s.p + 1) * 3 * s.Np, sim->stream)) return rc;

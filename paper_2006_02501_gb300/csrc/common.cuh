@@ -49,6 +49,7 @@ struct PairPlan {
     int grid;           // CTAs launched (each loops over items)
     int64_t n_itiles;
     int64_t chunk;      // j-records per chunk (multiple of tj)
+    int ipt = 1;        // FP32 form: i-bodies per thread (1 or 2)
 };
 
 // Device buffers of one simulation (every per-particle array is padded to Np).
@@ -174,7 +175,7 @@ int launch_energy(const DeviceState &s, double eps, double G, double *scratch, d
 int launch_ecc(const DeviceState &s, double G, int central, double *ecc, cudaStream_t st);
 size_t energy_scratch_doubles(int64_t N);
 
-PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hint, int device);
+PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hint, int device, int ipt = 1);
 
 // FP64 contributions of the heavy source bodies to every body i < N, written
 // to partial slot `slot` (rows (P+1)*3 of stride ld) of part.

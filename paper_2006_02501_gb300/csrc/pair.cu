@@ -158,21 +158,14 @@ struct PairArgs32 {
 
 constexpr int kThreads32 = 256;
 
+// One j-record (already in registers) against one i-body.
 template <int P, bool kGuard>
-__device__ __forceinline__ void interact32(const float4 *sh4, int jj, bool self, const float (&xh)[3],
+__device__ __forceinline__ void interact32(const float *rec, bool self, const float (&xh)[3],
                                            const float (&xl)[3], const float (&vh)[3], const float (&vl)[3],
                                            const float (&ai)[3], const float (&ji)[3], float eps2,
                                            float (&acc)[P + 1][3])
 {
     constexpr int NF = Rec32<P>::NF;
-    constexpr int RS = Rec32<P>::RS;
-    float rec[RS];
-#pragma unroll
-    for (int q4 = 0; q4 < RS / 4; ++q4) {
-        const float4 t = sh4[jj * (RS / 4) + q4];
-        rec[4 * q4 + 0] = t.x; rec[4 * q4 + 1] = t.y;
-        rec[4 * q4 + 2] = t.z; rec[4 * q4 + 3] = t.w;
-    }
     float r[P + 1][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -194,36 +187,54 @@ __device__ __forceinline__ void interact32(const float4 *sh4, int jj, bool self,
 }
 
 template <int P>
+__device__ __forceinline__ void load_rec(const float4 *sh4, int jj, float (&rec)[Rec32<P>::RS])
+{
+    constexpr int RS = Rec32<P>::RS;
+#pragma unroll
+    for (int q4 = 0; q4 < RS / 4; ++q4) {
+        const float4 t = sh4[jj * (RS / 4) + q4];
+        rec[4 * q4 + 0] = t.x; rec[4 * q4 + 1] = t.y;
+        rec[4 * q4 + 2] = t.z; rec[4 * q4 + 3] = t.w;
+    }
+}
+
+// IPT i-bodies per thread (thread t of the CTA owns positions ib + t + k kThreads32).
+template <int P, int IPT>
 __global__ void __launch_bounds__(kThreads32, 2) k_pair_fp32(PairArgs32<P> a)
 {
     constexpr int NF = Rec32<P>::NF;
     constexpr int RS = Rec32<P>::RS;
+    constexpr int NR = (P + 1) * 3;
     extern __shared__ float4 sh4[];                   // [tj][RS/4] records, then FP64 accumulators
     float *sh = reinterpret_cast<float *>(sh4);
     const int tj = a.tj;
-    // per-thread FP64 accumulators across tiles: [(P+1)*3][kThreads32]
+    // per-position FP64 accumulators across tiles: [NR][IPT * kThreads32]
     double *acc64 = reinterpret_cast<double *>(sh + (size_t)tj * RS);
+    constexpr int W = IPT * kThreads32;
     const int64_t items = a.n_itiles * a.split;
     for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
         const int64_t itile = item % a.n_itiles;
         const int jc = (int)(item / a.n_itiles);
-        const int64_t ib = a.i0 + itile * kThreads32;
-        const int64_t i = ib + threadIdx.x;
-        const bool live = i < a.i1;
-        const int64_t ipos = live ? i : a.i0;
-        const int64_t ic = a.ilist ? (int64_t)a.ilist[ipos] : ipos;
-        float xh[3], xl[3], vh[3], vl[3], ai[3], ji[3];
+        const int64_t ib = a.i0 + itile * W;
+        float xh[IPT][3], xl[IPT][3], vh[IPT][3], vl[IPT][3], ai[IPT][3], ji[IPT][3];
+        int64_t ic[IPT];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            xh[c] = a.jrec32[(0 + c) * a.ld + ic];
-            xl[c] = a.jrec32[(3 + c) * a.ld + ic];
-            vh[c] = a.jrec32[(6 + c) * a.ld + ic];
-            vl[c] = a.jrec32[(9 + c) * a.ld + ic];
-            ai[c] = P >= 2 ? a.jrec32[(12 + c) * a.ld + ic] : 0.0f;
-            ji[c] = P >= 3 ? a.jrec32[(15 + c) * a.ld + ic] : 0.0f;
+        for (int k = 0; k < IPT; ++k) {
+            const int64_t i = ib + threadIdx.x + k * kThreads32;
+            const int64_t ipos = i < a.i1 ? i : a.i0;
+            ic[k] = a.ilist ? (int64_t)a.ilist[ipos] : ipos;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                xh[k][c] = a.jrec32[(0 + c) * a.ld + ic[k]];
+                xl[k][c] = a.jrec32[(3 + c) * a.ld + ic[k]];
+                vh[k][c] = a.jrec32[(6 + c) * a.ld + ic[k]];
+                vl[k][c] = a.jrec32[(9 + c) * a.ld + ic[k]];
+                ai[k][c] = P >= 2 ? a.jrec32[(12 + c) * a.ld + ic[k]] : 0.0f;
+                ji[k][c] = P >= 3 ? a.jrec32[(15 + c) * a.ld + ic[k]] : 0.0f;
+            }
+#pragma unroll
+            for (int q = 0; q < NR; ++q) acc64[q * W + threadIdx.x + k * kThreads32] = 0.0;
         }
-#pragma unroll
-        for (int q = 0; q < (P + 1) * 3; ++q) acc64[q * kThreads32 + threadIdx.x] = 0.0;
 
         const int64_t jb = (int64_t)jc * a.chunk;
         const int64_t je = min(jb + a.chunk, a.n_j);
@@ -235,30 +246,50 @@ __global__ void __launch_bounds__(kThreads32, 2) k_pair_fp32(PairArgs32<P> a)
                 sh[col * RS + row] = j < a.n_j ? a.jrec32[row * a.ld + j] : (row < 3 ? (float)kFarAway : 0.0f);
             }
             __syncthreads();
-            float acc[P + 1][3];
+            float acc[IPT][P + 1][3];
 #pragma unroll
-            for (int k = 0; k <= P; ++k)
+            for (int k = 0; k < IPT; ++k)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) acc[k][c] = 0.0f;
-            if (a.ilist || (j0 < ib + kThreads32 && ib < j0 + tj)) {
-                // the tile may hold this thread's own body: guard the i == j pair
+                for (int n = 0; n <= P; ++n)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) acc[k][n][c] = 0.0f;
+            if (a.ilist || (j0 < ib + W && ib < j0 + tj)) {
+                // the tile may hold this thread's own bodies: guard the i == j pairs
 #pragma unroll 2
-                for (int jj = 0; jj < tj; ++jj)
-                    interact32<P, true>(sh4, jj, j0 + jj == ic, xh, xl, vh, vl, ai, ji, a.eps2, acc);
+                for (int jj = 0; jj < tj; ++jj) {
+                    float rec[RS];
+                    load_rec<P>(sh4, jj, rec);
+#pragma unroll
+                    for (int k = 0; k < IPT; ++k)
+                        interact32<P, true>(rec, j0 + jj == ic[k], xh[k], xl[k], vh[k], vl[k], ai[k], ji[k],
+                                            a.eps2, acc[k]);
+                }
             } else {
 #pragma unroll 2
-                for (int jj = 0; jj < tj; ++jj)
-                    interact32<P, false>(sh4, jj, false, xh, xl, vh, vl, ai, ji, a.eps2, acc);
+                for (int jj = 0; jj < tj; ++jj) {
+                    float rec[RS];
+                    load_rec<P>(sh4, jj, rec);
+#pragma unroll
+                    for (int k = 0; k < IPT; ++k)
+                        interact32<P, false>(rec, false, xh[k], xl[k], vh[k], vl[k], ai[k], ji[k], a.eps2, acc[k]);
+                }
             }
 #pragma unroll
-            for (int k = 0; k <= P; ++k)
+            for (int k = 0; k < IPT; ++k)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) acc64[(3 * k + c) * kThreads32 + threadIdx.x] += (double)acc[k][c];
+                for (int n = 0; n <= P; ++n)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        acc64[(3 * n + c) * W + threadIdx.x + k * kThreads32] += (double)acc[k][n][c];
         }
-        if (live) {
-            double *out = a.part + (int64_t)jc * (P + 1) * 3 * a.part_ld + (i - a.i0);
 #pragma unroll
-            for (int q = 0; q < (P + 1) * 3; ++q) out[q * a.part_ld] = acc64[q * kThreads32 + threadIdx.x];
+        for (int k = 0; k < IPT; ++k) {
+            const int64_t i = ib + threadIdx.x + k * kThreads32;
+            if (i < a.i1) {
+                double *out = a.part + (int64_t)jc * NR * a.part_ld + (i - a.i0);
+#pragma unroll
+                for (int q = 0; q < NR; ++q) out[q * a.part_ld] = acc64[q * W + threadIdx.x + k * kThreads32];
+            }
         }
     }
 }
@@ -315,6 +346,22 @@ int launch_fp64(const double *jrec, const double *m, int64_t ld, int64_t n_j, do
     return MH_OK;
 }
 
+template <int P, int IPT>
+int launch_fp32_ipt(const PairArgs32<P> &a, const PairPlan &pl, cudaStream_t st)
+{
+    const size_t smem = sizeof(float) * Rec32<P>::RS * pl.tj + sizeof(double) * (P + 1) * 3 * IPT * kThreads32;
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        MH_CUDA(cudaFuncSetAttribute(k_pair_fp32<P, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr_set[dev] = true;
+    }
+    k_pair_fp32<P, IPT><<<pl.grid, pl.threads, smem, st>>>(a);
+    MH_LAUNCHED("k_pair_fp32");
+    return MH_OK;
+}
+
 template <int P>
 int launch_fp32(const float *jrec32, int64_t ld, int64_t n_j, double eps, int64_t i0,
                 int64_t i1, double *part, int64_t part_ld, const PairPlan &pl, const int *ilist,
@@ -322,10 +369,7 @@ int launch_fp32(const float *jrec32, int64_t ld, int64_t n_j, double eps, int64_
 {
     PairArgs32<P> a{jrec32, ld, n_j, i0, i1, (float)(eps * eps), part, part_ld,
                     pl.n_itiles, pl.chunk, pl.split, pl.tj, ilist};
-    const size_t smem = sizeof(float) * Rec32<P>::RS * pl.tj + sizeof(double) * (P + 1) * 3 * kThreads32;
-    k_pair_fp32<P><<<pl.grid, pl.threads, smem, st>>>(a);
-    MH_LAUNCHED("k_pair_fp32");
-    return MH_OK;
+    return pl.ipt == 2 ? launch_fp32_ipt<P, 2>(a, pl, st) : launch_fp32_ipt<P, 1>(a, pl, st);
 }
 
 }  // namespace
@@ -346,7 +390,7 @@ int launch_pair_heavy(int P, int64_t N, int64_t ld, const double *m, const doubl
     return MH_OK;
 }
 
-PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hint, int device)
+PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hint, int device, int ipt)
 {
     static int n_sm_cache[64] = {0};
     int n_sm = device >= 0 && device < 64 ? n_sm_cache[device] : 0;
@@ -357,7 +401,8 @@ PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hin
     }
     PairPlan pl{};
     pl.threads = precision == MH_PREC_FP64 ? 128 : kThreads32;
-    pl.i_per_cta = pl.threads;
+    pl.ipt = precision == MH_PREC_FP64 ? 1 : (ipt == 2 ? 2 : 1);
+    pl.i_per_cta = pl.threads * pl.ipt;
     pl.tj = precision == MH_PREC_FP64 ? 64 : 128;
     const int occ = precision == MH_PREC_FP64 ? 4 : 2;     // resident CTAs per SM
     const int slots = n_sm * occ;
