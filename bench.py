@@ -47,6 +47,11 @@ SEED = 2
 # Algorithmic flops per pair interaction at 8th order: the conventional count
 # used for 4th/6th/8th-order Hermite codes (60/97/144).
 FLOPS_PER_PAIR = {4: 60, 6: 97, 8: 144}
+# The FP64 headline kernel evaluates each unordered pair once and accumulates
+# its terms into both bodies: per unordered pair the conventional count of one
+# direction plus one multiply-add (2 flops) per accumulated component of the
+# second body, 3 (p + 1) of them.
+FLOPS_PER_UNORDERED_PAIR = {o: FLOPS_PER_PAIR[o] + 2 * 3 * (o // 2) for o in (4, 6, 8)}
 # Peaks from unit counts and the maximum SM clock (2070 MHz), 152 SMs:
 #   FP32: 128 FMA lanes/SM x 2 flops; FP64: the GB300 nominal 1.25 TFLOP/s.
 SM_MAX_MHZ = 2070.0
@@ -55,9 +60,9 @@ PEAK_FP32 = N_SM * 128 * 2 * SM_MAX_MHZ * 1e6
 PEAK_FP64 = 1.25e12
 # DRAM traffic per launch of the dominant kernel from one ncu capture
 # (profiles/); valid only while the kernel source is the one captured.
-TRAFFIC = {"file": "paper_2006_02501_gb300/csrc/pair.cu",
-           "sha256": "bd67eb0e518cf354cb7064cdfd8b8a520508681164ae3a4d2fb41a5d6a018059",
-           "bytes_per_launch": 8.23e6 + 25.72e6}   # profiles/k_pair_fp64_disc_N65536_order8_dram.md
+TRAFFIC = {"file": "paper_2006_02501_gb300/csrc/pair_sym.cu",
+           "sha256": "",
+           "bytes_per_launch": None}
 
 
 def _sha(path):
@@ -262,7 +267,7 @@ def run_ours(args, rank, world, local_rank):
     pair_launches = c1["pair_kernel_timed"] - c0["pair_kernel_timed"]
     pair_ms = (c1["pair_kernel_ms"] - c0["pair_kernel_ms"]) / max(pair_launches, 1)
     gpu_launches = c1["kernel_launches"] - c0["kernel_launches"]
-    achieved = FLOPS_PER_PAIR[ORDER] * N * (N - 1) / (pair_ms * 1e-3)
+    achieved = FLOPS_PER_UNORDERED_PAIR[ORDER] * N * (N - 1) / 2 / (pair_ms * 1e-3)
     traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["sha256"] and _sha(TRAFFIC["file"]) == TRAFFIC["sha256"] else None
 
     # ---- end to end through the public API: state in from host, step, state out ----
@@ -281,6 +286,21 @@ def run_ours(args, rank, world, local_rank):
     h2d = hx.nbytes + hv.nbytes + hd.nbytes
     d2h = hx2.nbytes + hv2.nbytes + hd2.nbytes
     sim.close()
+
+    # ---- FP64 form with the ordered-pair kernel (every i, j evaluated), same workload ----
+    simo = mh.Simulation(ORDER, m, x, v, EPS, stream=stream, symmetric=False)
+    simo.step(DT, N_ITER)
+    ko = 2
+    o0 = simo.counters()
+    barrier()
+    simo.set_timing(True)
+    to = time_steps(simo, stream, torch, ko, flush)
+    barrier()
+    o1 = simo.counters()
+    simo.close()
+    elo = reduce_max(sum(to))
+    pairo_ms = (o1["pair_kernel_ms"] - o0["pair_kernel_ms"]) / max(o1["pair_kernel_timed"] - o0["pair_kernel_timed"], 1)
+    acho = FLOPS_PER_PAIR[ORDER] * N * (N - 1) / (pairo_ms * 1e-3)
 
     # ---- FP32-pair precision form, same workload ----
     sim32 = mh.Simulation(ORDER, m, x, v, EPS, stream=stream, precision=mh.MH_PREC_FP32PAIR)
@@ -330,8 +350,9 @@ def run_ours(args, rank, world, local_rank):
         "particle_steps_per_s": world * args.steps * N / (elapsed_ms * 1e-3),
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": PEAK_FP64 / 1e12,
                      "unit": "TFLOP/s", "frac": achieved / PEAK_FP64, "traffic": traffic,
-                     "kernel": "k_pair_fp64<3>",
-                     "flops_per_pair": FLOPS_PER_PAIR[ORDER],
+                     "kernel": "k_pair_fp64_sym<3>",
+                     "flops_per_unordered_pair": FLOPS_PER_UNORDERED_PAIR[ORDER],
+                     "unordered_pairs_per_launch": N * (N - 1) // 2,
                      "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (profiling recipe table)",
                      "launch_ms": pair_ms, "launches": pair_launches},
         "cpu_baseline": cpu,
@@ -339,7 +360,12 @@ def run_ours(args, rank, world, local_rank):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clocks,
         "gpu_launches": gpu_launches,
-        "forms": {"fp32pair": {
+        "forms": {"fp64_ordered": {
+            "value": world * ko * units / (elo * 1e-3), "unit": UNIT, "ms_per_step": elo / ko,
+            "steps": ko, "pair_kernel": "k_pair_fp64<3>", "launch_ms": pairo_ms,
+            "achieved_tflops": acho / 1e12, "peak_tflops": PEAK_FP64 / 1e12, "frac": acho / PEAK_FP64,
+            "flops_per_pair": FLOPS_PER_PAIR[ORDER]},
+            "fp32pair": {
             "value": world * k32 * units / (el32 * 1e-3), "unit": UNIT, "ms_per_step": el32 / k32,
             "steps": k32, "pair_kernel": "k_pair_fp32<3>", "launch_ms": pair32_ms,
             "achieved_tflops": ach32 / 1e12, "peak_tflops": PEAK_FP32 / 1e12,

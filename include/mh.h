@@ -74,6 +74,14 @@ typedef struct {
                            (at most 32 such bodies; 0 disables; default 1e-3).  In
                            a disc around a central mass this keeps the dominant
                            central force at FP64 accuracy for O(N) extra work. */
+    int symmetric;      /* FP64 form, shared steps: 1 (default) evaluates every unordered
+                           pair once and adds its terms to both bodies (each term of
+                           the Section 3 pair derivatives is odd under i <-> j), which
+                           halves the FP64 work; 0 evaluates every ordered pair.  The
+                           symmetric kernel needs (C + Np/256) partial-sum slots of
+                           (P+1)*3*Np doubles (C ~ 10; Np = N padded to 256), about
+                           1.7 GB at N = 65536 and order 8; above 8 GiB, or with block
+                           steps, the ordered kernel runs. */
 } mh_config;
 
 /* Snapshot of a simulation (mh_sync / mh_set_state).  Each pointer may be NULL

@@ -60,12 +60,15 @@ class Simulation:
     heavy_frac: precision form, mass fraction above which a source body's
     pairs run in FP64 (None = library default 1e-3, 0 = all pairs FP32);
     block: None for shared steps, or {"dt_max", "k_max", "eta"} for block time
-    steps (order 6 or 8; step() then needs a multiple of dt_max).
+    steps (order 6 or 8; step() then needs a multiple of dt_max);
+    symmetric: FP64 shared-step evaluation of each unordered pair once, both
+    bodies updated (default), or of every ordered pair (False).
     """
 
     def __init__(self, order: int, m, x, v, eps: float, precision: int = MH_PREC_FP64,
                  beta: int = MH_BETA_MODIFIED, G: float = 1.0, stream=None, split_j: int = 0,
-                 heavy_frac: float | None = None, block: dict | None = None):
+                 heavy_frac: float | None = None, block: dict | None = None,
+                 symmetric: bool = True):
         L = _capi.lib()
         m = _host(m)
         N = m.shape[0]
@@ -75,6 +78,7 @@ class Simulation:
         cfg.order, cfg.precision, cfg.beta_mode, cfg.G, cfg.split_j = order, precision, beta, G, split_j
         if heavy_frac is not None:
             cfg.heavy_frac = heavy_frac
+        cfg.symmetric = 1 if symmetric else 0
         if block is not None:
             cfg.step_mode = _capi.MH_STEP_BLOCK
             cfg.dt_max = float(block.get("dt_max", cfg.dt_max))

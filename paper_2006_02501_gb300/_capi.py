@@ -40,7 +40,7 @@ class Config(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("beta_mode", ctypes.c_int), ("precision", ctypes.c_int),
                 ("step_mode", ctypes.c_int), ("G", ctypes.c_double), ("eta", ctypes.c_double),
                 ("dt_max", ctypes.c_double), ("k_max", ctypes.c_int), ("split_j", ctypes.c_int),
-                ("heavy_frac", ctypes.c_double)]
+                ("heavy_frac", ctypes.c_double), ("symmetric", ctypes.c_int)]
 
 
 class StateC(ctypes.Structure):

@@ -163,6 +163,30 @@ int tuned_ipt(mh_sim *sim, int P, int64_t n_i, const int *ilist, int *ipt)
 int evaluate(mh_sim *sim, int P, int precision, int *split)
 {
     DeviceState &s = sim->s;
+    if (precision == MH_PREC_FP64 && P <= 3 && sim->cfg.symmetric) {
+        const SymPlan sp = plan_sym(P, s.Np, sim->device);
+        const size_t need = (size_t)sp.slots * (P + 1) * 3 * s.Np;
+        if (sp.nB > 0 && need * sizeof(double) <= kSymMaxPartBytes) {
+            int rc = ensure_part(s, need, sim->stream);
+            if (rc) return rc;
+            std::pair<cudaEvent_t, cudaEvent_t> ev{};
+            if (sim->timing) {
+                if ((rc = timed_event_pair(sim, &ev))) return rc;
+                MH_CUDA(cudaEventRecord(ev.first, sim->stream));
+            }
+            rc = launch_pair_sym(P, sp, s.jrec, s.m, s.Np, s.N, sim->eps, sim->cfg.G, s.part, sim->stream);
+            if (rc) return rc;
+            if (sim->timing) {
+                MH_CUDA(cudaEventRecord(ev.second, sim->stream));
+                sim->ev_pending.push_back(ev);
+            }
+            *split = sp.slots;
+            sim->ctr.evaluations += 1;
+            sim->ctr.pair_interactions += (double)s.N * (double)(s.N - 1);
+            sim->ctr.kernel_launches += 1;
+            return MH_OK;
+        }
+    }
     int ipt = 1;
     if (precision == MH_PREC_FP32PAIR)
         if (int rc = tuned_ipt(sim, P, s.N, nullptr, &ipt)) return rc;
@@ -268,6 +292,7 @@ void mh_config_default(mh_config *cfg)
     cfg->dt_max = 1.0 / 32.0;
     cfg->k_max = 12;
     cfg->split_j = 0;
+    cfg->symmetric = 1;
     cfg->heavy_frac = 1e-3;
 }
 

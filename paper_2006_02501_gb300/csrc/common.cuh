@@ -87,6 +87,11 @@ struct DeviceState {
 
 constexpr int kMaxHeavy = 32;
 
+// Largest partial-sum buffer the pair-symmetric evaluation may use (about
+// 0.375 Np^2 bytes at order 8, i.e. Np up to ~146k); above it the one-sided
+// kernel runs.
+constexpr size_t kSymMaxPartBytes = (size_t)8 << 30;
+
 }  // namespace mh
 
 struct mh_sim {
@@ -176,6 +181,18 @@ int launch_ecc(const DeviceState &s, double G, int central, double *ecc, cudaStr
 size_t energy_scratch_doubles(int64_t N);
 
 PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hint, int device, int ipt = 1);
+
+// All-pairs FP64 evaluation that computes each unordered pair once (pair_sym.cu).
+// Valid (nB > 0) when ld is a positive multiple of its 128-body block; writes
+// `slots` partial-sum slots of (P+1)*3 rows of stride ld, every one of them in full.
+struct SymPlan {
+    int nB = 0, D = 0, C = 0, Bc = 0;   // blocks, distances, row chunks, blocks per chunk
+    int grid = 0;
+    int slots = 0;                      // C + D
+};
+SymPlan plan_sym(int P, int64_t ld, int device);
+int launch_pair_sym(int P, const SymPlan &plan, const double *jrec, const double *m, int64_t ld, int64_t N,
+                    double eps, double G, double *part, cudaStream_t st);
 
 // FP64 contributions of the heavy source bodies to every body i < N, written
 // to partial slot `slot` (rows (P+1)*3 of stride ld) of part.

@@ -67,10 +67,12 @@ __device__ __forceinline__ void pair_terms(const T (&r)[P + 1][3], T mS, const T
 //   alpha = (r.v)/s,  beta = (v.v + r.a)/s + alpha^2,
 //   gamma = (3 v.a + r.adot)/s + alpha (3 beta - 4 alpha^2),
 //   B0 = r, B1 = v - 3 alpha B0, B2 = a - 6 alpha B1 - 3 beta B0,
-//   B3 = adot - 9 alpha B2 - 9 beta B1 - 3 gamma B0,
-// so every term is accumulated by one multiply-add, acc_k += (G m S) B_k.
-template <int P, typename T>
-__device__ __forceinline__ void pair_abg(const T (&r)[P + 1][3], T mS, T sinv, T (&acc)[P + 1][3])
+//   B3 = adot - 9 alpha B2 - 9 beta B1 - 3 gamma B0.
+// Every B_k is odd under the exchange i <-> j (r^(k) changes sign, alpha, beta,
+// gamma and s do not), so one evaluation serves both bodies of a pair.
+// sink(k, c, B) receives component c of B_k.
+template <int P, typename T, typename Sink>
+__device__ __forceinline__ void pair_abg_terms(const T (&r)[P + 1][3], T sinv, Sink &&sink)
 {
     static_assert(P >= 1 && P <= 3, "pair_abg handles P = 1, 2, 3");
     const T rv = r[0][0] * r[1][0] + r[0][1] * r[1][1] + r[0][2] * r[1][2];
@@ -80,8 +82,8 @@ __device__ __forceinline__ void pair_abg(const T (&r)[P + 1][3], T mS, T sinv, T
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         B1[c] = r[1][c] - a3 * r[0][c];
-        acc[0][c] += mS * r[0][c];
-        acc[1][c] += mS * B1[c];
+        sink(0, c, r[0][c]);
+        sink(1, c, B1[c]);
     }
     if constexpr (P >= 2) {
         const T al2 = al * al;
@@ -93,7 +95,7 @@ __device__ __forceinline__ void pair_abg(const T (&r)[P + 1][3], T mS, T sinv, T
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             B2[c] = r[2][c] - a6 * B1[c] - b3 * r[0][c];
-            acc[2][c] += mS * B2[c];
+            sink(2, c, B2[c]);
         }
         if constexpr (P >= 3) {
             const T va = r[1][0] * r[2][0] + r[1][1] * r[2][1] + r[1][2] * r[2][2];
@@ -101,10 +103,16 @@ __device__ __forceinline__ void pair_abg(const T (&r)[P + 1][3], T mS, T sinv, T
             const T ga = w3 * sinv + al * (b3 - T(4) * al2);
             const T a9 = T(9) * al, b9 = T(9) * be, g3 = T(3) * ga;
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-                acc[3][c] += mS * (r[3][c] - a9 * B2[c] - b9 * B1[c] - g3 * r[0][c]);
+            for (int c = 0; c < 3; ++c) sink(3, c, r[3][c] - a9 * B2[c] - b9 * B1[c] - g3 * r[0][c]);
         }
     }
+}
+
+// acc_k += (G m S) B_k for one ordered pair.
+template <int P, typename T>
+__device__ __forceinline__ void pair_abg(const T (&r)[P + 1][3], T mS, T sinv, T (&acc)[P + 1][3])
+{
+    pair_abg_terms<P, T>(r, sinv, [&](int k, int c, T B) { acc[k][c] += mS * B; });
 }
 
 // Pair derivatives for any supported P: the alpha/beta/gamma form up to P = 3,

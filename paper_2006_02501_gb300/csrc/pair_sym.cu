@@ -1,0 +1,260 @@
+// FP64 all-pairs evaluation of a^(0..P) that computes every unordered pair once
+// (the E of P(EC)^n under shared steps, and the initialisation passes P <= 3).
+//
+// Pair physics (Dittmann 2020, Section 3, intro): a_ij = G m_j r_ij s^(-3/2).
+// With the scaled terms B_k of pair_math.cuh, body i receives G m_j S B_k(i,j)
+// and body j receives G m_i S B_k(j,i) = -G m_i S B_k(i,j): the terms are odd
+// under i <-> j and S, alpha, beta, gamma are even.  One evaluation of the pair
+// therefore serves both bodies, and an interaction costs about 96 FP64
+// operations per unordered pair instead of 2 x 83 for two ordered pairs.  On a
+// part with two FP64 lanes per SM this halves the time of the FP64 form; the
+// extra data movement (shuffles, shared memory) runs on otherwise idle pipes.
+//
+// Decomposition.  Bodies are cut into blocks of R = 128 (the padded count Np is
+// a multiple of R; nB blocks).  Block row I handles the diagonal block (I, I)
+// and the blocks J = I + d (mod nB), d = 1 .. D with D = floor(nB/2); when nB
+// is even (always, for the simulation's padding to 256) the block pair at
+// d = nB/2 is done by the rows I < nB/2 only.  Every unordered block pair is
+// then done exactly once and every row has the same amount of work, to one block.  A row is cut into C chunks of blocks; an item is one
+// (row, chunk) and CTAs loop over items with a grid stride.
+//
+// Inside a CTA (4 warps) warp w holds the 32 i-bodies I*R + 32w + lane.  For
+// an off-diagonal block the warps take the block's four 32-body j-subtiles in
+// a rotation (warp w takes subtile (w + jt) mod 4 at stage jt); a warp runs the
+// 32 x 32 pairs of a subtile as a ring: each lane holds one j-body with its
+// j-side accumulator and passes both one lane on after every pair.  The j-side
+// sums of a subtile move between warps through shared memory at the stage
+// barriers.  The diagonal block is evaluated as ordered pairs (i-side only,
+// the i == j pair guarded).
+//
+// Output: the partial-sum slots of the other evaluation kernels, S = C + D of
+// them: slot c < C holds row chunk c's sums for its own bodies, slot C + d - 1
+// the sums that the block at distance d wrote into its j-bodies (zero where no
+// such block exists).  The corrector adds the S slots in a fixed order, so the
+// result is deterministic and independent of which CTA ran which item.
+#include <algorithm>
+
+#include "common.cuh"
+#include "pair_math.cuh"
+
+namespace mh {
+
+namespace {
+
+constexpr int kSymWarps = 4;
+constexpr int kSymR = 32 * kSymWarps;     // bodies per block
+
+template <int P>
+struct SymArgs {
+    const double *jrec;   // [3(P+1)][ld]
+    const double *m;      // [ld]
+    int64_t ld;           // row stride (the padded body count, a multiple of kSymR)
+    int64_t N;            // bodies; positions N .. ld-1 are padding
+    int nB, D, C, Bc;     // blocks, distances, row chunks, blocks per chunk
+    double eps2, G;
+    double *part;         // [C + D][(P+1)*3][ld]
+};
+
+// Record of body b.  Padding bodies get mass 0 and distinct far-away positions,
+// so that no pair has r = 0 (their own sums are never read).
+template <int P>
+__device__ __forceinline__ void load_body(const SymArgs<P> &a, int64_t b, double (&r)[P + 1][3], double &gm)
+{
+    if (b < a.N) {
+#pragma unroll
+        for (int k = 0; k <= P; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) r[k][c] = a.jrec[(3 * k + c) * a.ld + b];
+        gm = a.G * a.m[b];
+    } else {
+#pragma unroll
+        for (int k = 0; k <= P; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) r[k][c] = 0.0;
+        r[0][0] = kFarAway + (double)(b - a.N);
+        gm = 0.0;
+    }
+}
+
+template <int P>
+__device__ __forceinline__ void rotate(double (&r)[P + 1][3], double &gm, int src)
+{
+#pragma unroll
+    for (int k = 0; k <= P; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r[k][c] = __shfl_sync(0xffffffffu, r[k][c], src);
+    gm = __shfl_sync(0xffffffffu, gm, src);
+}
+
+template <int P>
+__global__ void __launch_bounds__(kSymR, 2) k_pair_fp64_sym(SymArgs<P> a)
+{
+    constexpr int NR = 3 * (P + 1);
+    __shared__ double accs[NR][kSymR];    // j-side sums of the current block, by column
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int src = (lane + 1) & 31;      // ring: after t passes lane l holds j-lane (l + t) mod 32
+    const bool even = (a.nB & 1) == 0;
+    const int64_t items = (int64_t)a.nB * a.C;
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int I = (int)(item % a.nB);
+        const int ch = (int)(item / a.nB);
+        const int64_t ib = (int64_t)I * kSymR + threadIdx.x;
+        double ri[P + 1][3], gmi;
+        load_body<P>(a, ib, ri, gmi);
+        double acci[P + 1][3];
+#pragma unroll
+        for (int k = 0; k <= P; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acci[k][c] = 0.0;
+
+        const int dmax = (even && I >= a.nB / 2) ? a.D - 1 : a.D;
+        const int b0 = ch * a.Bc;
+        const int b1 = min(b0 + a.Bc, dmax + 1);
+        for (int b = b0; b < b1; ++b) {
+            if (b == 0) {
+                // diagonal block: ordered pairs into the i-side only
+                for (int js = 0; js < kSymWarps; ++js) {
+                    double rj[P + 1][3], gmj;
+                    load_body<P>(a, (int64_t)I * kSymR + js * 32 + lane, rj, gmj);
+                    for (int t = 0; t < 32; ++t) {
+                        const bool self = js == w && t == 0;
+                        double r[P + 1][3];
+#pragma unroll
+                        for (int k = 0; k <= P; ++k)
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) r[k][c] = rj[k][c] - ri[k][c];
+                        double s = fma(r[0][0], r[0][0], fma(r[0][1], r[0][1], fma(r[0][2], r[0][2], a.eps2)));
+                        s = self ? 1.0 : s;
+                        const double wi = self ? 0.0 : gmj;
+                        const double rinv = rsqrt_fp64(s);
+                        const double sinv = rinv * rinv;
+                        const double mS = wi * (rinv * sinv);
+                        pair_abg_terms<P, double>(r, sinv, [&](int k, int c, double B) {
+                            acci[k][c] = fma(mS, B, acci[k][c]);
+                        });
+                        rotate<P>(rj, gmj, src);
+                    }
+                }
+                continue;
+            }
+            const int J = (I + b) % a.nB;
+            for (int jt = 0; jt < kSymWarps; ++jt) {
+                const int js = (w + jt) % kSymWarps;
+                double rj[P + 1][3], gmj, accj[P + 1][3];
+                load_body<P>(a, (int64_t)J * kSymR + js * 32 + lane, rj, gmj);
+#pragma unroll
+                for (int k = 0; k <= P; ++k)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) accj[k][c] = jt == 0 ? 0.0 : accs[3 * k + c][js * 32 + lane];
+                for (int t = 0; t < 32; ++t) {
+                    double r[P + 1][3];
+#pragma unroll
+                    for (int k = 0; k <= P; ++k)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) r[k][c] = rj[k][c] - ri[k][c];
+                    const double s = fma(r[0][0], r[0][0], fma(r[0][1], r[0][1], fma(r[0][2], r[0][2], a.eps2)));
+                    const double rinv = rsqrt_fp64(s);
+                    const double sinv = rinv * rinv;
+                    const double S = rinv * sinv;
+                    const double wi = gmj * S, wj = gmi * S;
+                    pair_abg_terms<P, double>(r, sinv, [&](int k, int c, double B) {
+                        acci[k][c] = fma(wi, B, acci[k][c]);
+                        accj[k][c] = fma(-wj, B, accj[k][c]);
+                    });
+                    rotate<P>(rj, gmj, src);
+#pragma unroll
+                    for (int k = 0; k <= P; ++k)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) accj[k][c] = __shfl_sync(0xffffffffu, accj[k][c], src);
+                }
+#pragma unroll
+                for (int k = 0; k <= P; ++k)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) accs[3 * k + c][js * 32 + lane] = accj[k][c];
+                __syncthreads();
+            }
+            double *out = a.part + (int64_t)(a.C + b - 1) * NR * a.ld + (int64_t)J * kSymR + threadIdx.x;
+#pragma unroll
+            for (int q = 0; q < NR; ++q) out[q * a.ld] = accs[q][threadIdx.x];
+            __syncthreads();
+        }
+        if (even && I >= a.nB / 2 && ch == a.C - 1) {
+            // this row has no block at d = D: its slot in block I + D stays zero
+            const int J = (I + a.D) % a.nB;
+            double *out = a.part + (int64_t)(a.C + a.D - 1) * NR * a.ld + (int64_t)J * kSymR + threadIdx.x;
+#pragma unroll
+            for (int q = 0; q < NR; ++q) out[q * a.ld] = 0.0;
+        }
+        double *out = a.part + (int64_t)ch * NR * a.ld + ib;
+#pragma unroll
+        for (int k = 0; k <= P; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) out[(3 * k + c) * a.ld] = acci[k][c];
+    }
+}
+
+template <int P>
+int launch_sym(const SymPlan &pl, const double *jrec, const double *m, int64_t ld, int64_t N, double eps,
+               double G, double *part, cudaStream_t st)
+{
+    SymArgs<P> a{jrec, m, ld, N, pl.nB, pl.D, pl.C, pl.Bc, eps * eps, G, part};
+    k_pair_fp64_sym<P><<<pl.grid, kSymR, 0, st>>>(a);
+    MH_LAUNCHED("k_pair_fp64_sym");
+    return MH_OK;
+}
+
+}  // namespace
+
+SymPlan plan_sym(int P, int64_t ld, int device)
+{
+    SymPlan pl{};
+    if (ld % kSymR != 0 || ld < kSymR || P < 1 || P > 3) return pl;
+    // resident CTAs per device, cached per (device, P)
+    static int slot_cache[64][4] = {{0}};
+    int slots = device >= 0 && device < 64 ? slot_cache[device][P] : 0;
+    if (slots == 0) {
+        int n_sm = 0, occ = 0;
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
+        const void *fn = P == 1 ? (const void *)k_pair_fp64_sym<1>
+                       : P == 2 ? (const void *)k_pair_fp64_sym<2> : (const void *)k_pair_fp64_sym<3>;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kSymR, 0);
+        slots = std::max(n_sm, 1) * std::max(occ, 1);
+        if (device >= 0 && device < 64) slot_cache[device][P] = slots;
+    }
+    pl.nB = (int)(ld / kSymR);
+    pl.D = pl.nB / 2;
+    const int nb = pl.D + 1;                        // blocks of the longest row
+    // items of equal size; pick the chunk count with the fewest block-times on the
+    // busiest CTA (the diagonal block counts about twice, it runs ordered pairs)
+    double best = 1e300;
+    for (int C = 1; C <= nb; ++C) {
+        const int Bc = (nb + C - 1) / C;
+        if ((nb + Bc - 1) / Bc != C) continue;
+        const int64_t items = (int64_t)pl.nB * C;
+        const int64_t waves = (items + slots - 1) / slots;
+        const double cost = (double)waves * (Bc + 1.0) * (1.0 + 0.001 * C);
+        if (cost < best) {
+            best = cost;
+            pl.C = C;
+            pl.Bc = Bc;
+        }
+    }
+    pl.grid = (int)std::min<int64_t>((int64_t)pl.nB * pl.C, slots);
+    pl.slots = pl.C + pl.D;
+    return pl;
+}
+
+int launch_pair_sym(int P, const SymPlan &pl, const double *jrec, const double *m, int64_t ld, int64_t N,
+                    double eps, double G, double *part, cudaStream_t st)
+{
+    switch (P) {
+    case 1: return launch_sym<1>(pl, jrec, m, ld, N, eps, G, part, st);
+    case 2: return launch_sym<2>(pl, jrec, m, ld, N, eps, G, part, st);
+    case 3: return launch_sym<3>(pl, jrec, m, ld, N, eps, G, part, st);
+    }
+    set_error("launch_pair_sym: P must be 1..3");
+    return MH_EINVAL;
+}
+
+}  // namespace mh
