@@ -60,9 +60,11 @@ PEAK_FP32 = N_SM * 128 * 2 * SM_MAX_MHZ * 1e6
 PEAK_FP64 = 1.25e12
 # DRAM traffic per launch of the dominant kernel from one ncu capture
 # (profiles/); valid only while the kernel source is the one captured.
-TRAFFIC = {"file": "paper_2006_02501_gb300/csrc/pair_sym.cu",
-           "sha256": "",
-           "bytes_per_launch": None}
+TRAFFIC = {"files": ["paper_2006_02501_gb300/csrc/pair_sym.cu", "paper_2006_02501_gb300/csrc/pair_math.cuh"],
+           "sha256": ["824659c626af56f9fb75dc7df94d4e0cf91e28631505290704a05d7e4d65b5e2",
+                      "6fb5de969d2e5ff8a196395d0212ae24b655b7d4cf57b83ec55fbaef9aaaecc7"],
+           # profiles/k_pair_fp64_sym_disc_N65536_order8_dram.md: 54.72 MB read + 1.61 GB written
+           "bytes_per_launch": 54.72e6 + 1.61e9}
 
 
 def _sha(path):
@@ -268,7 +270,8 @@ def run_ours(args, rank, world, local_rank):
     pair_ms = (c1["pair_kernel_ms"] - c0["pair_kernel_ms"]) / max(pair_launches, 1)
     gpu_launches = c1["kernel_launches"] - c0["kernel_launches"]
     achieved = FLOPS_PER_UNORDERED_PAIR[ORDER] * N * (N - 1) / 2 / (pair_ms * 1e-3)
-    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["sha256"] and _sha(TRAFFIC["file"]) == TRAFFIC["sha256"] else None
+    same_src = all(_sha(f) == h for f, h in zip(TRAFFIC["files"], TRAFFIC["sha256"]))
+    traffic = TRAFFIC["bytes_per_launch"] if same_src else None
 
     # ---- end to end through the public API: state in from host, step, state out ----
     _, hx, hv, hd = sim.sync()
@@ -314,6 +317,8 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     d1 = sim32.counters()
     sim32.close()
+    variant32 = d1["pair_variant"]
+    kernel32 = {1: "k_pair_fp32<3,1>", 2: "k_pair_fp32<3,2>", 3: "k_pair_fp32x2<3>"}.get(variant32, "?")
     el32 = reduce_max(sum(t32))
     pair32_ms = (d1["pair_kernel_ms"] - d0["pair_kernel_ms"]) / max(d1["pair_kernel_timed"] - d0["pair_kernel_timed"], 1)
     ach32 = FLOPS_PER_PAIR[ORDER] * N * (N - 1) / (pair32_ms * 1e-3)
@@ -367,7 +372,10 @@ def run_ours(args, rank, world, local_rank):
             "flops_per_pair": FLOPS_PER_PAIR[ORDER]},
             "fp32pair": {
             "value": world * k32 * units / (el32 * 1e-3), "unit": UNIT, "ms_per_step": el32 / k32,
-            "steps": k32, "pair_kernel": "k_pair_fp32<3>", "launch_ms": pair32_ms,
+            "steps": k32, "pair_kernel": kernel32, "launch_ms": pair32_ms,
+            "autotuner_us": {"one_per_thread": d1["pair_tune_ms_x1000"][0],
+                             "two_per_thread": d1["pair_tune_ms_x1000"][1],
+                             "two_packed_fp32x2": d1["pair_tune_ms_x1000"][2]},
             "achieved_tflops": ach32 / 1e12, "peak_tflops": PEAK_FP32 / 1e12,
             "frac": ach32 / PEAK_FP32,
             "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"},

@@ -82,6 +82,11 @@ typedef struct {
                            (P+1)*3*Np doubles (C ~ 10; Np = N padded to 256), about
                            1.7 GB at N = 65536 and order 8; above 8 GiB, or with block
                            steps, the ordered kernel runs. */
+    int fp32_variant;   /* precision form, evaluation kernel: 0 (default) = chosen per size
+                           class by timing each once (autotuner), or fixed: 1 = one i-body
+                           per thread, 2 = two, 3 = two in packed FP32x2 lanes.  The
+                           autotuner only runs for 8192 or more evaluated bodies; below,
+                           0 means 1. */
 } mh_config;
 
 /* Snapshot of a simulation (mh_sync / mh_set_state).  Each pointer may be NULL
@@ -104,9 +109,10 @@ typedef struct {
     double pair_kernel_ms;       /* with timing on: summed device time of the O(N^2)
                                     evaluation kernels (CUDA events around each launch) */
     int64_t pair_kernel_timed;   /* number of evaluation launches in pair_kernel_ms */
-    int32_t pair_bodies_per_thread;  /* precision form: i-bodies per thread of the last
-                                        evaluation, as chosen by the autotuner (1 or 2) */
-    int32_t pair_tune_ms_x1000[2];   /* the tuner's last timings of the two variants, microseconds */
+    int32_t pair_variant;        /* precision form: evaluation kernel of the last evaluation, as
+                                    chosen by the autotuner: 1 = one i-body per thread, 2 = two,
+                                    3 = two in the lanes of packed FP32x2 instructions */
+    int32_t pair_tune_ms_x1000[3];   /* the tuner's last timings of the three variants, microseconds */
 } mh_counters;
 
 /* Fill *cfg with the defaults listed above. */

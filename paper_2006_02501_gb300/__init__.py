@@ -62,13 +62,15 @@ class Simulation:
     block: None for shared steps, or {"dt_max", "k_max", "eta"} for block time
     steps (order 6 or 8; step() then needs a multiple of dt_max);
     symmetric: FP64 shared-step evaluation of each unordered pair once, both
-    bodies updated (default), or of every ordered pair (False).
+    bodies updated (default), or of every ordered pair (False);
+    fp32_variant: precision form evaluation kernel, 0 = autotuned, 1/2/3 fixed
+    (one i-body per thread, two, two in packed FP32x2 lanes).
     """
 
     def __init__(self, order: int, m, x, v, eps: float, precision: int = MH_PREC_FP64,
                  beta: int = MH_BETA_MODIFIED, G: float = 1.0, stream=None, split_j: int = 0,
                  heavy_frac: float | None = None, block: dict | None = None,
-                 symmetric: bool = True):
+                 symmetric: bool = True, fp32_variant: int = 0):
         L = _capi.lib()
         m = _host(m)
         N = m.shape[0]
@@ -79,6 +81,7 @@ class Simulation:
         if heavy_frac is not None:
             cfg.heavy_frac = heavy_frac
         cfg.symmetric = 1 if symmetric else 0
+        cfg.fp32_variant = int(fp32_variant)
         if block is not None:
             cfg.step_mode = _capi.MH_STEP_BLOCK
             cfg.dt_max = float(block.get("dt_max", cfg.dt_max))

@@ -40,7 +40,8 @@ class Config(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("beta_mode", ctypes.c_int), ("precision", ctypes.c_int),
                 ("step_mode", ctypes.c_int), ("G", ctypes.c_double), ("eta", ctypes.c_double),
                 ("dt_max", ctypes.c_double), ("k_max", ctypes.c_int), ("split_j", ctypes.c_int),
-                ("heavy_frac", ctypes.c_double), ("symmetric", ctypes.c_int)]
+                ("heavy_frac", ctypes.c_double), ("symmetric", ctypes.c_int),
+                ("fp32_variant", ctypes.c_int)]
 
 
 class StateC(ctypes.Structure):
@@ -53,8 +54,8 @@ class Counters(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("evaluations", ctypes.c_int64),
                 ("pair_interactions", ctypes.c_double), ("particle_steps", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("pair_kernel_ms", ctypes.c_double),
-                ("pair_kernel_timed", ctypes.c_int64), ("pair_bodies_per_thread", ctypes.c_int32),
-                ("pair_tune_ms_x1000", ctypes.c_int32 * 2)]
+                ("pair_kernel_timed", ctypes.c_int64), ("pair_variant", ctypes.c_int32),
+                ("pair_tune_ms_x1000", ctypes.c_int32 * 3)]
 
 
 class MHError(RuntimeError):

@@ -113,49 +113,56 @@ int timed_event_pair(mh_sim *sim, std::pair<cudaEvent_t, cudaEvent_t> *out)
     return MH_OK;
 }
 
-// Autotuner of the precision-form evaluation: i-bodies per thread (1 or 2) per
-// (P, number of evaluated bodies rounded up to a power of two, sources, device).
-// Both variants give bit-identical sums; the first evaluation of a class times
-// each once with CUDA events and keeps the faster.
-std::map<std::tuple<int, int64_t, int64_t, int>, int> g_ipt_cache;
+// Autotuner of the precision-form evaluation: kernel variant (1 = one i-body
+// per thread, 2 = two, 3 = two in packed FP32x2 lanes) per (P, number of
+// evaluated bodies rounded up to a power of two, sources, device).  Variants 1
+// and 2 give bit-identical sums, variant 3 differs by the rounding of its
+// explicit multiply-adds.  The first evaluation of a class times each variant
+// once with CUDA events and keeps the fastest.
+std::map<std::tuple<int, int64_t, int64_t, int>, int> g_variant_cache;
 
-int tuned_ipt(mh_sim *sim, int P, int64_t n_i, const int *ilist, int *ipt)
+int tuned_variant(mh_sim *sim, int P, int64_t n_i, const int *ilist, int *variant)
 {
     DeviceState &s = sim->s;
-    *ipt = 1;
+    if (sim->cfg.fp32_variant >= 1 && sim->cfg.fp32_variant <= 3) {
+        *variant = sim->cfg.fp32_variant;
+        return MH_OK;
+    }
+    *variant = 1;
     if (n_i < 8192) return MH_OK;          // a single wave either way: keep one body per thread
     int64_t bucket = 1;
     while (bucket < n_i) bucket <<= 1;
     const auto key = std::make_tuple(P, bucket, s.N, sim->device);
-    auto it = g_ipt_cache.find(key);
-    if (it != g_ipt_cache.end()) {
-        *ipt = it->second;
+    auto it = g_variant_cache.find(key);
+    if (it != g_variant_cache.end()) {
+        *variant = it->second;
         return MH_OK;
     }
-    cudaEvent_t e0, e1, e2;
-    MH_CUDA(cudaEventCreate(&e0));
-    MH_CUDA(cudaEventCreate(&e1));
-    MH_CUDA(cudaEventCreate(&e2));
-    float ms[2] = {0.0f, 0.0f};
-    for (int v = 1; v <= 2; ++v) {
+    constexpr int kVariants = 3;
+    cudaEvent_t ev[kVariants + 1];
+    for (auto &e : ev) MH_CUDA(cudaEventCreate(&e));
+    for (int v = 1; v <= kVariants; ++v) {
         const PairPlan pl = plan_pair(P, MH_PREC_FP32PAIR, n_i, s.N, sim->cfg.split_j, sim->device, v);
         if (int rc = ensure_part(s, (size_t)(pl.split + 1) * (P + 1) * 3 * s.Np, sim->stream)) return rc;
-        MH_CUDA(cudaEventRecord(v == 1 ? e0 : e1, sim->stream));
+        MH_CUDA(cudaEventRecord(ev[v - 1], sim->stream));
         if (int rc = launch_pair(P, MH_PREC_FP32PAIR, s.N, s.Np, s.m, s.jrec, s.jrec32, sim->eps, sim->cfg.G, 0,
                                  n_i, s.part, s.Np, pl, sim->stream, ilist))
             return rc;
-        MH_CUDA(cudaEventRecord(v == 1 ? e1 : e2, sim->stream));
     }
-    MH_CUDA(cudaEventSynchronize(e2));
-    MH_CUDA(cudaEventElapsedTime(&ms[0], e0, e1));
-    MH_CUDA(cudaEventElapsedTime(&ms[1], e1, e2));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaEventDestroy(e2);
-    *ipt = ms[1] < ms[0] ? 2 : 1;
-    g_ipt_cache[key] = *ipt;
-    sim->ctr.pair_tune_ms_x1000[0] = (int32_t)(ms[0] * 1000.0f);
-    sim->ctr.pair_tune_ms_x1000[1] = (int32_t)(ms[1] * 1000.0f);
+    MH_CUDA(cudaEventRecord(ev[kVariants], sim->stream));
+    MH_CUDA(cudaEventSynchronize(ev[kVariants]));
+    float best = 0.0f;
+    for (int v = 1; v <= kVariants; ++v) {
+        float ms = 0.0f;
+        MH_CUDA(cudaEventElapsedTime(&ms, ev[v - 1], ev[v]));
+        sim->ctr.pair_tune_ms_x1000[v - 1] = (int32_t)(ms * 1000.0f);
+        if (v == 1 || ms < best) {
+            best = ms;
+            *variant = v;
+        }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    g_variant_cache[key] = *variant;
     return MH_OK;
 }
 
@@ -189,8 +196,8 @@ int evaluate(mh_sim *sim, int P, int precision, int *split)
     }
     int ipt = 1;
     if (precision == MH_PREC_FP32PAIR)
-        if (int rc = tuned_ipt(sim, P, s.N, nullptr, &ipt)) return rc;
-    sim->ctr.pair_bodies_per_thread = ipt;
+        if (int rc = tuned_variant(sim, P, s.N, nullptr, &ipt)) return rc;
+    sim->ctr.pair_variant = ipt;
     std::pair<cudaEvent_t, cudaEvent_t> ev{};
     if (sim->timing) {
         if (int rc = timed_event_pair(sim, &ev)) return rc;
@@ -293,6 +300,7 @@ void mh_config_default(mh_config *cfg)
     cfg->k_max = 12;
     cfg->split_j = 0;
     cfg->symmetric = 1;
+    cfg->fp32_variant = 0;
     cfg->heavy_frac = 1e-3;
 }
 
@@ -321,6 +329,7 @@ int mh::create_shell(mh_sim **out, int64_t N, int order, const double *m, const 
     if (c.precision != MH_PREC_FP64 && c.precision != MH_PREC_FP32PAIR) { set_error("mh_create: bad precision"); return MH_EINVAL; }
     if (c.beta_mode != MH_BETA_MODIFIED && c.beta_mode != MH_BETA_STANDARD) { set_error("mh_create: bad beta_mode"); return MH_EINVAL; }
     if (c.step_mode != MH_STEP_SHARED && c.step_mode != MH_STEP_BLOCK) { set_error("mh_create: bad step_mode"); return MH_EINVAL; }
+    if (c.fp32_variant < 0 || c.fp32_variant > 3) { set_error("mh_create: fp32_variant must be 0..3"); return MH_EINVAL; }
     if (c.step_mode == MH_STEP_BLOCK) {
         if (p < 2) { set_error("mh_create: block steps need order 6 or 8"); return MH_EINVAL; }
         if (!(c.dt_max > 0.0) || !std::isfinite(c.dt_max) || c.k_max < 0 || c.k_max > 30 || !(c.eta > 0.0)) {
@@ -492,7 +501,8 @@ static int block_advance(mh_sim *sim, double dt, int n_iter)
         sim->ctr.kernel_launches += 1;
         int ipt = 1;
         if (prec == MH_PREC_FP32PAIR)
-            if (int rc = tuned_ipt(sim, s.p, n_act, s.act, &ipt)) return rc;
+            if (int rc = tuned_variant(sim, s.p, n_act, s.act, &ipt)) return rc;
+        sim->ctr.pair_variant = ipt;
         for (int it = 0; it < n_iter; ++it) {
             const PairPlan pl = plan_pair(s.p, prec, n_act, s.N, c.split_j, sim->device, ipt);
             const bool heavy = prec == MH_PREC_FP32PAIR && s.n_heavy > 0;

@@ -50,6 +50,7 @@ struct PairPlan {
     int64_t n_itiles;
     int64_t chunk;      // j-records per chunk (multiple of tj)
     int ipt = 1;        // FP32 form: i-bodies per thread (1 or 2)
+    bool packed = false;  // FP32 form: the two i-bodies of a thread share paired FP32 instructions
 };
 
 // Device buffers of one simulation (every per-particle array is padded to Np).
@@ -180,7 +181,8 @@ int launch_energy(const DeviceState &s, double eps, double G, double *scratch, d
 int launch_ecc(const DeviceState &s, double G, int central, double *ecc, cudaStream_t st);
 size_t energy_scratch_doubles(int64_t N);
 
-PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hint, int device, int ipt = 1);
+// FP32 form variant: 1 = one i-body per thread, 2 = two, 3 = two in packed FP32x2 lanes.
+PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hint, int device, int variant = 1);
 
 // All-pairs FP64 evaluation that computes each unordered pair once (pair_sym.cu).
 // Valid (nB > 0) when ld is a positive multiple of its 128-body block; writes

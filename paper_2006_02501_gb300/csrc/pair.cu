@@ -180,7 +180,7 @@ __device__ __forceinline__ void interact32(const float *rec, bool self, const fl
         s = self ? 1.0f : s;
         gm = self ? 0.0f : gm;
     }
-    const float rinv = rsqrtf(s);
+    const float rinv = rsqrt_mufu(s);
     const float sinv = rinv * rinv;
     const float mS = gm * rinv * sinv;
     pair_abg<P, float>(r, mS, sinv, acc);
@@ -294,6 +294,187 @@ __global__ void __launch_bounds__(kThreads32, 2) k_pair_fp32(PairArgs32<P> a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32-pair form, packed: two i-bodies per thread in the two lanes of
+// Blackwell's paired FP32 instructions (FFMA2/FMUL2/FADD2), so that one issue
+// slot advances both pairs.  Same arithmetic as interact32 per lane, with the
+// multiply-adds written out explicitly; results differ from the scalar kernels
+// only by the rounding of those contractions.  The shared-memory tile stores
+// every j value twice ({v, v}), so a 16-byte load yields two packed operands.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// B_k of pair_abg_terms for two pairs at once; acc_k += mS B_k.
+template <int P>
+__device__ __forceinline__ void pair_abg_x2(const float2 (&r)[P + 1][3], float2 mS, float2 sinv,
+                                            float2 (&acc)[P + 1][3])
+{
+    const float2 rv = fma2(r[0][2], r[1][2], fma2(r[0][1], r[1][1], mul2(r[0][0], r[1][0])));
+    const float2 al = mul2(rv, sinv);
+    const float2 na3 = mul2(f2(-3.0f), al);
+    float2 B1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        B1[c] = fma2(na3, r[0][c], r[1][c]);
+        acc[0][c] = fma2(mS, r[0][c], acc[0][c]);
+        acc[1][c] = fma2(mS, B1[c], acc[1][c]);
+    }
+    if constexpr (P >= 2) {
+        const float2 al2 = mul2(al, al);
+        float2 w2 = mul2(r[1][0], r[1][0]);
+        w2 = fma2(r[1][1], r[1][1], w2);
+        w2 = fma2(r[1][2], r[1][2], w2);
+        w2 = fma2(r[0][0], r[2][0], w2);
+        w2 = fma2(r[0][1], r[2][1], w2);
+        w2 = fma2(r[0][2], r[2][2], w2);
+        const float2 be = fma2(w2, sinv, al2);
+        const float2 na6 = mul2(f2(-6.0f), al), nb3 = mul2(f2(-3.0f), be);
+        float2 B2[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            B2[c] = fma2(nb3, r[0][c], fma2(na6, B1[c], r[2][c]));
+            acc[2][c] = fma2(mS, B2[c], acc[2][c]);
+        }
+        if constexpr (P >= 3) {
+            const float2 va = fma2(r[1][2], r[2][2], fma2(r[1][1], r[2][1], mul2(r[1][0], r[2][0])));
+            const float2 rj = fma2(r[0][2], r[3][2], fma2(r[0][1], r[3][1], mul2(r[0][0], r[3][0])));
+            const float2 w3 = fma2(f2(3.0f), va, rj);
+            // gamma = w3/s + alpha (3 beta - 4 alpha^2), with 3 beta - 4 alpha^2 = -(nb3 + 4 alpha^2)
+            const float2 u = fma2(f2(4.0f), al2, nb3);
+            const float2 ga = fma2(w3, sinv, mul2(mul2(f2(-1.0f), al), u));
+            const float2 na9 = mul2(f2(-9.0f), al), nb9 = mul2(f2(-9.0f), be), ng3 = mul2(f2(-3.0f), ga);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float2 B3 = fma2(ng3, r[0][c], fma2(nb9, B1[c], fma2(na9, B2[c], r[3][c])));
+                acc[3][c] = fma2(mS, B3, acc[3][c]);
+            }
+        }
+    }
+}
+
+// One j-record (packed duplicates in shared memory) against this thread's two
+// i-bodies, whose x, v hi/lo and a, a-dot are held negated (ni*).
+template <int P, bool kGuard>
+__device__ __forceinline__ void interact32x2(const float2 *rec, bool self0, bool self1,
+                                             const float2 (&nxh)[3], const float2 (&nxl)[3],
+                                             const float2 (&nvh)[3], const float2 (&nvl)[3],
+                                             const float2 (&nai)[3], const float2 (&nji)[3], float2 eps2,
+                                             float2 (&acc)[P + 1][3])
+{
+    constexpr int NF = Rec32<P>::NF;
+    float2 r[P + 1][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        r[0][c] = add2(add2(rec[c], nxh[c]), add2(rec[3 + c], nxl[c]));
+        r[1][c] = add2(add2(rec[6 + c], nvh[c]), add2(rec[9 + c], nvl[c]));
+        if constexpr (P >= 2) r[2][c] = add2(rec[12 + c], nai[c]);
+        if constexpr (P >= 3) r[3][c] = add2(rec[15 + c], nji[c]);
+    }
+    float2 s = fma2(r[0][0], r[0][0], fma2(r[0][1], r[0][1], fma2(r[0][2], r[0][2], eps2)));
+    float2 gm = rec[NF - 1];
+    if (kGuard) {
+        s.x = self0 ? 1.0f : s.x;
+        s.y = self1 ? 1.0f : s.y;
+        gm.x = self0 ? 0.0f : gm.x;
+        gm.y = self1 ? 0.0f : gm.y;
+    }
+    const float2 rinv = make_float2(rsqrt_mufu(s.x), rsqrt_mufu(s.y));
+    const float2 sinv = mul2(rinv, rinv);
+    const float2 mS = mul2(mul2(gm, rinv), sinv);
+    pair_abg_x2<P>(r, mS, sinv, acc);
+}
+
+// Thread t of the CTA owns positions ib + t and ib + t + kThreads32 (the layout
+// of k_pair_fp32<P, 2>, so both write the same partial-sum slots).
+template <int P>
+__global__ void __launch_bounds__(kThreads32, 2) k_pair_fp32x2(PairArgs32<P> a)
+{
+    constexpr int NF = Rec32<P>::NF;
+    constexpr int RS = Rec32<P>::RS;
+    constexpr int NR = (P + 1) * 3;
+    constexpr int W = 2 * kThreads32;
+    extern __shared__ float4 sh4[];                   // [tj][RS] packed records, then FP64 accumulators
+    float2 *sh2 = reinterpret_cast<float2 *>(sh4);
+    const int tj = a.tj;
+    double *acc64 = reinterpret_cast<double *>(sh2 + (size_t)tj * RS);   // [NR][W]
+    const float2 eps2 = f2(a.eps2);
+    const int64_t items = a.n_itiles * a.split;
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int64_t itile = item % a.n_itiles;
+        const int jc = (int)(item / a.n_itiles);
+        const int64_t ib = a.i0 + itile * W;
+        int64_t ic[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int64_t i = ib + threadIdx.x + k * kThreads32;
+            const int64_t ipos = i < a.i1 ? i : a.i0;
+            ic[k] = a.ilist ? (int64_t)a.ilist[ipos] : ipos;
+#pragma unroll
+            for (int q = 0; q < NR; ++q) acc64[q * W + threadIdx.x + k * kThreads32] = 0.0;
+        }
+        auto ld2n = [&](int row) {
+            return make_float2(-a.jrec32[row * a.ld + ic[0]], -a.jrec32[row * a.ld + ic[1]]);
+        };
+        float2 nxh[3], nxl[3], nvh[3], nvl[3], nai[3], nji[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            nxh[c] = ld2n(0 + c);
+            nxl[c] = ld2n(3 + c);
+            nvh[c] = ld2n(6 + c);
+            nvl[c] = ld2n(9 + c);
+            nai[c] = P >= 2 ? ld2n(12 + c) : f2(0.0f);
+            nji[c] = P >= 3 ? ld2n(15 + c) : f2(0.0f);
+        }
+
+        const int64_t jb = (int64_t)jc * a.chunk;
+        const int64_t je = min(jb + a.chunk, a.n_j);
+        for (int64_t j0 = jb; j0 < je; j0 += tj) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < NF * tj; e += kThreads32) {
+                const int row = e / tj, col = e - row * tj;
+                const int64_t j = j0 + col;
+                sh2[col * RS + row] = f2(j < a.n_j ? a.jrec32[row * a.ld + j] : (row < 3 ? (float)kFarAway : 0.0f));
+            }
+            __syncthreads();
+            float2 acc[P + 1][3];
+#pragma unroll
+            for (int n = 0; n <= P; ++n)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) acc[n][c] = f2(0.0f);
+            if (a.ilist || (j0 < ib + W && ib < j0 + tj)) {
+#pragma unroll 2
+                for (int jj = 0; jj < tj; ++jj)
+                    interact32x2<P, true>(sh2 + jj * RS, j0 + jj == ic[0], j0 + jj == ic[1], nxh, nxl, nvh, nvl,
+                                          nai, nji, eps2, acc);
+            } else {
+#pragma unroll 2
+                for (int jj = 0; jj < tj; ++jj)
+                    interact32x2<P, false>(sh2 + jj * RS, false, false, nxh, nxl, nvh, nvl, nai, nji, eps2, acc);
+            }
+#pragma unroll
+            for (int n = 0; n <= P; ++n)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    acc64[(3 * n + c) * W + threadIdx.x] += (double)acc[n][c].x;
+                    acc64[(3 * n + c) * W + threadIdx.x + kThreads32] += (double)acc[n][c].y;
+                }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int64_t i = ib + threadIdx.x + k * kThreads32;
+            if (i < a.i1) {
+                double *out = a.part + (int64_t)jc * NR * a.part_ld + (i - a.i0);
+#pragma unroll
+                for (int q = 0; q < NR; ++q) out[q * a.part_ld] = acc64[q * W + threadIdx.x + k * kThreads32];
+            }
+        }
+    }
+}
+
 // FP64 contributions of a short list of heavy source bodies (precision form):
 // one thread per body i, the heavy records read through the read-only cache.
 template <int P>
@@ -363,12 +544,29 @@ int launch_fp32_ipt(const PairArgs32<P> &a, const PairPlan &pl, cudaStream_t st)
 }
 
 template <int P>
+int launch_fp32_packed(const PairArgs32<P> &a, const PairPlan &pl, cudaStream_t st)
+{
+    const size_t smem = sizeof(float2) * Rec32<P>::RS * pl.tj + sizeof(double) * (P + 1) * 3 * 2 * kThreads32;
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        MH_CUDA(cudaFuncSetAttribute(k_pair_fp32x2<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr_set[dev] = true;
+    }
+    k_pair_fp32x2<P><<<pl.grid, pl.threads, smem, st>>>(a);
+    MH_LAUNCHED("k_pair_fp32x2");
+    return MH_OK;
+}
+
+template <int P>
 int launch_fp32(const float *jrec32, int64_t ld, int64_t n_j, double eps, int64_t i0,
                 int64_t i1, double *part, int64_t part_ld, const PairPlan &pl, const int *ilist,
                 cudaStream_t st)
 {
     PairArgs32<P> a{jrec32, ld, n_j, i0, i1, (float)(eps * eps), part, part_ld,
                     pl.n_itiles, pl.chunk, pl.split, pl.tj, ilist};
+    if (pl.packed) return launch_fp32_packed<P>(a, pl, st);
     return pl.ipt == 2 ? launch_fp32_ipt<P, 2>(a, pl, st) : launch_fp32_ipt<P, 1>(a, pl, st);
 }
 
@@ -390,8 +588,9 @@ int launch_pair_heavy(int P, int64_t N, int64_t ld, const double *m, const doubl
     return MH_OK;
 }
 
-PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hint, int device, int ipt)
+PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hint, int device, int variant)
 {
+    const int ipt = variant;
     static int n_sm_cache[64] = {0};
     int n_sm = device >= 0 && device < 64 ? n_sm_cache[device] : 0;
     if (n_sm == 0) {
@@ -401,7 +600,8 @@ PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hin
     }
     PairPlan pl{};
     pl.threads = precision == MH_PREC_FP64 ? 128 : kThreads32;
-    pl.ipt = precision == MH_PREC_FP64 ? 1 : (ipt == 2 ? 2 : 1);
+    pl.ipt = precision == MH_PREC_FP64 ? 1 : (ipt >= 2 ? 2 : 1);
+    pl.packed = precision != MH_PREC_FP64 && ipt == 3;
     pl.i_per_cta = pl.threads * pl.ipt;
     pl.tj = precision == MH_PREC_FP64 ? 64 : 128;
     const int occ = precision == MH_PREC_FP64 ? 4 : 2;     // resident CTAs per SM

@@ -129,11 +129,37 @@ __device__ __forceinline__ void pair_derivs(const T (&r)[P + 1][3], T mS, T sinv
     }
 }
 
-// 1/sqrt(s) in FP64: FP32 estimate (MUFU), then one third-order Householder
-// step y <- y (1 + e/2 + 3e^2/8), e = 1 - s y^2 (error ~ e0^3).
+// Single-precision 1/sqrt(x) of the special-function unit (one instruction;
+// x below 2^-126 is flushed to zero).
+__device__ __forceinline__ float rsqrt_mufu(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// 1/sqrt(s) in FP64: an FP32 estimate, then one third-order Householder step
+// y <- y (1 + e/2 + 3e^2/8), e = 1 - s y^2 (error ~ e0^3, e0 ~ 2^-22).
+// The estimate is taken of m in s = 4^k m, m in [1, 4), and scaled by 2^-k, so
+// that every positive normal double is in range.  m crosses to single precision
+// and the estimate back to double by integer operations on the bit patterns
+// (exponent rebiased by 1023 - 127, mantissa truncated to 23 bits going in,
+// exact coming back), which keeps both conversions off the FP64 pipe.
+// s = 0 (or subnormal) gives +inf, which turns the pair into NaN as the
+// softening-free singularity should; an infinite or NaN s gives a non-finite result.
 __device__ __forceinline__ double rsqrt_fp64(double s)
 {
-    double y = (double)rsqrtf((float)s);
+    constexpr int kRebias = (1023 - 127) << 20;          // exponent shift in the high word
+    const long long b = __double_as_longlong(s);
+    const int hi = (int)(b >> 32);
+    const unsigned lo = (unsigned)b;
+    const int de = (hi >> 20) & 0x7ff;                   // biased exponent of s
+    const int k = (de - 1023) >> 1;                      // floor(exponent / 2)
+    const int mhi = (hi & 0x000fffff) | ((de - 2 * k) << 20);   // m: exponent 1023 or 1024
+    const int fb = ((mhi - kRebias) << 3) | (int)(lo >> 29);
+    const int yb = __float_as_int(rsqrt_mufu(__int_as_float(fb)));   // 1/sqrt(m) in (0.5, 1]
+    const int yhi = de == 0 ? 0x7ff00000 : (yb >> 3) + kRebias - (k << 20);
+    const double y = __hiloint2double(yhi, de == 0 ? 0 : (yb & 7) << 29);
     const double e = fma(-s, y * y, 1.0);
     const double t = fma(0.375, e, 0.5);
     return fma(y * e, t, y);

@@ -64,17 +64,26 @@ def test_block_step_parity_fp64(mh, orc, order):
     assert scaled_stack_err(dg[:, :4], B.derivs[:, :4], blk["dt_max"] * 2.0 ** -lv.max()) < 1e-9
 
 
-def test_block_step_fp32_precision_form(mh, orc):
-    """Precision form with block steps: accelerations within 2e-6 of the oracle
-    after two dt_max of block steps from the same start."""
+@pytest.fixture(scope="module")
+def fp32_block_case(orc):
     m, x, v = I.smbh_disc(seed=33, N=900)
     blk = dict(dt_max=2.0 ** -5, k_max=10, eta=0.05)
     eps = 1e-4
     B = orc.BlockState(8, m, x, v, eps, blk["dt_max"], blk["k_max"], blk["eta"])
-    with mh.Simulation(8, m, x, v, eps, block=blk, precision=mh.MH_PREC_FP32PAIR) as sim:
-        sim.set_state(x, v, B.derivs, level=B.level)
+    start = (B.derivs.copy(), B.level.copy())
+    B.advance(2 * blk["dt_max"], 3)
+    return m, x, v, blk, eps, start, B
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_block_step_fp32_precision_form(mh, orc, fp32_block_case, variant):
+    """Precision form with block steps: accelerations within 2e-6 of the oracle
+    after two dt_max of block steps from the same start, for each evaluation
+    kernel (one i-body per thread, two, two in packed FP32x2 lanes)."""
+    m, x, v, blk, eps, (d_start, lv_start), B = fp32_block_case
+    with mh.Simulation(8, m, x, v, eps, block=blk, precision=mh.MH_PREC_FP32PAIR, fp32_variant=variant) as sim:
+        sim.set_state(x, v, d_start, level=lv_start)
         E0 = sim.energy()
-        B.advance(2 * blk["dt_max"], 3)
         sim.step(2 * blk["dt_max"], 3)
         t, xg, vg, dg = sim.sync()
         E1 = sim.energy()

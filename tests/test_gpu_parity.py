@@ -230,23 +230,52 @@ def test_nonfinite_state_reported(mh):
     assert ei.value.code == -4
 
 
-def test_fp32_pair_form_accuracy(mh, orc):
-    """Precision form: the relative energy error after the run within 1e-9 of
-    the oracle's, and accelerations within 2e-6 of the oracle's.  Stars of
-    1e-9 each keep star-star encounters negligible, so the energy error is the
-    deterministic truncation error of the inner orbits (about 31 steps per
-    orbit at r = 0.1) rather than a chaotic quantity."""
+@pytest.fixture(scope="module")
+def fp32_disc_case(orc):
     m, x, v = I.smbh_disc(seed=12, N=1023, m_total=1023e-9)
     dt, eps, nst = 2 * np.pi * 1e-3, 1e-4, 50
-    with mh.Simulation(8, m, x, v, eps, precision=mh.MH_PREC_FP32PAIR) as s32:
+    ref = orc.State(8, m, x, v, eps)
+    ref.step(dt, 3, nst)
+    return m, x, v, dt, eps, nst, ref
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_fp32_pair_form_accuracy(mh, orc, fp32_disc_case, variant):
+    """Precision form: the relative energy error after the run within 1e-9 of
+    the oracle's, and accelerations within 2e-6 of the oracle's, for each
+    evaluation kernel.  Stars of 1e-9 each keep star-star encounters
+    negligible, so the energy error is the deterministic truncation error of
+    the inner orbits (about 31 steps per orbit at r = 0.1) rather than a
+    chaotic quantity."""
+    m, x, v, dt, eps, nst, ref = fp32_disc_case
+    with mh.Simulation(8, m, x, v, eps, precision=mh.MH_PREC_FP32PAIR, fp32_variant=variant) as s32:
         E0 = s32.energy()
         s32.step(dt, 3, nsteps=nst)
         _, x32, v32, d32 = s32.sync()
         E32 = s32.energy()
-    ref = orc.State(8, m, x, v, eps)
-    ref.step(dt, 3, nst)
     dE_ref = ref.energy() / orc.energy(m, x, v, eps) - 1
     dE_32 = E32 / E0 - 1
     assert abs(dE_ref) > 1e-8                     # the quantity compared is well resolved
     assert abs(dE_32 - dE_ref) < 1e-9
     assert rel_rows(d32[:, 0], ref.derivs[:, 0]) < 2e-6
+
+
+def test_fp32_variants_full_size(mh):
+    """SMBH disc, 65536 stars + SMBH, one 8th-order P(EC)^3 step in the precision
+    form with each evaluation kernel: one and two i-bodies per thread agree
+    bit for bit; every variant's accelerations lie within 2e-6 of the FP64
+    form's (itself held to the oracle at 1e-12)."""
+    m, x, v = I.smbh_disc(seed=2, N=65536)
+    dt, eps = 2 * np.pi * 1e-3, 1e-4
+    with mh.Simulation(8, m, x, v, eps) as s64:
+        s64.step(dt, 3)
+        _, _, _, d64 = s64.sync()
+    got = {}
+    for variant in (1, 2, 3):
+        with mh.Simulation(8, m, x, v, eps, precision=mh.MH_PREC_FP32PAIR, fp32_variant=variant) as s32:
+            s32.step(dt, 3)
+            _, _, _, d32 = s32.sync()
+            assert s32.counters()["pair_variant"] == variant
+        got[variant] = d32
+        assert rel_rows(d32[:, 0], d64[:, 0]) < 2e-6, variant
+    np.testing.assert_array_equal(got[1][:, :4], got[2][:, :4])
