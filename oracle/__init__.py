@@ -63,7 +63,9 @@ def _lib_handle():
             lib.orc_energy.argtypes = [i, _D, _D, _D, d, d]
             lib.orc_energy.restype = d
             lib.orc_ecc.argtypes = [i, _D, _D, _D, d, i, _D]
-            lib.orc_timestep_H.argtypes = [i, _D, _D, d, d]
+            lib.orc_timestep_H.argtypes = [i, _D, _D, d, d, d]
+            lib.orc_run_timesym.argtypes = [i, i, i, i, i, d, i, _D, d, d, _D, _D, _D, _D, _D]
+            lib.orc_run_timesym.restype = d
             lib.orc_timestep_H.restype = d
             LL = ctypes.POINTER(ctypes.c_longlong)
             IP = ctypes.POINTER(ctypes.c_int)
@@ -199,6 +201,24 @@ class State:
                               _p(self.derivs))
         self.t += dt * nsteps
 
+    def step_timesym(self, eta: float, n_iter: int, nsteps: int = 1, backward: bool = False) -> np.ndarray:
+        """nsteps time-symmetric variable steps (Section 3.3): dt = (H- + H+)/2 with
+        H of Eq. 24, H+ re-evaluated in every pass of P(EC)^n.  H- of the first
+        step is Eq. 24 at the current positions unless a previous call left the
+        next step's H- (self.H).  Returns the step sizes taken."""
+        if getattr(self, "H", None) is None or getattr(self, "H_eta", None) != eta:
+            self.H = timestep_H(self.m, self.x, self.eps, eta, self.G)
+            self.H_eta = eta
+        Hc = ctypes.c_double(self.H)
+        dts = np.zeros(nsteps)
+        adv = _lib_handle().orc_run_timesym(self.N, self.p, 0 if self.modified else 1, n_iter,
+                                            -1 if backward else 1, eta, nsteps, _p(self.m), self.eps,
+                                            self.G, _p(self.x), _p(self.v), _p(self.derivs),
+                                            ctypes.byref(Hc), _p(dts))
+        self.H = Hc.value
+        self.t += adv
+        return dts
+
     def energy(self) -> float:
         return energy(self.m, self.x, self.v, self.eps, self.G)
 
@@ -224,9 +244,10 @@ def ecc(m, x, v, G: float = 1.0, central: int = 0) -> np.ndarray:
     return e
 
 
-def timestep_H(m, x, eps: float, eta: float) -> float:
+def timestep_H(m, x, eps: float, eta: float, G: float = 1.0) -> float:
+    """Eq. 24: eta times the shortest two-body time scale sqrt(s^1.5 / (G (m_i + m_j)))."""
     m, x = _f64(m), _f64(x)
-    return _lib_handle().orc_timestep_H(m.shape[0], _p(m), _p(x), eps, eta)
+    return _lib_handle().orc_timestep_H(m.shape[0], _p(m), _p(x), eps, eta, G)
 
 
 # --------------------------------------------------------------------------- #

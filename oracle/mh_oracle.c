@@ -351,17 +351,28 @@ static void correct_one(int p, double dt, const double *cv, const double *cx,
 /* One shared P(EC)^n step (Section 2.1 end, Section 3)                       */
 /* ------------------------------------------------------------------------- */
 
-/* Advance x, v, derivs (N x 2p x 3, a^(0..2p-1)) by dt in place.
+double orc_timestep_H(int N, const double *m, const double *x, double eps, double eta, double G);
+
+/* Advance x, v, derivs (N x 2p x 3, a^(0..2p-1)) by one step in place.
  * P: Taylor predictor.  Then n_iter times: E (direct summation of a^(0..p) at
  * the current estimate of t+dt) and C (corrector).  No evaluation follows the
  * last correction; the next step starts from the derivatives of the n-th E.
- * Finally a^(p+1..2p-1) at t+dt by interpolation (R3).                      */
-void orc_step(int N, int p, int beta_mode, int n_iter, double dt, const double *m,
-              double eps, double G, double *x, double *v, double *derivs)
+ * Finally a^(p+1..2p-1) at t+dt by interpolation (R3).
+ *
+ * Constant step (eta <= 0): dt as given.
+ * Time-symmetric variable step (eta > 0, Section 3.3): dt = dir (H- + H+)/2,
+ * with dir = +1 or -1 the sign of the dt argument, H- = *H (Eq. 24 at the
+ * start of the step) and H+ = Eq. 24 at the positions of the latest
+ * evaluation, so that dt is re-chosen in every pass of the iteration; the
+ * prediction uses dt = dir H-.  On return *H holds H+ of the last evaluation,
+ * the next step's H- (R15).  Returns the dt of the final correction.          */
+static double step_impl(int N, int p, int beta_mode, int n_iter, double dt, double eta, double *H,
+                        const double *m, double eps, double G, double *x, double *v, double *derivs)
 {
     const int K = 2 * p;
     const int P = p;                          /* pair derivatives evaluated */
     const int na = (p > 1 ? p - 1 : 1);
+    const double dir = dt < 0 ? -1.0 : 1.0;
     double cv[ORC_MAXSYS], cx[ORC_MAXSYS];
     orc_corrector_weights(p, beta_mode, cv, cx);
 
@@ -373,6 +384,8 @@ void orc_step(int N, int p, int beta_mode, int n_iter, double dt, const double *
     double *x1 = (double *)malloc((size_t)N * 3 * sizeof(double));
     double *v1 = (double *)malloc((size_t)N * 3 * sizeof(double));
 
+    const double H_minus = eta > 0 ? *H : 0.0;
+    if (eta > 0) dt = dir * H_minus;
     orc_predict(N, p, dt, x, v, derivs, xp, vp, ap);
     memcpy(x1, xp, (size_t)N * 3 * sizeof(double));
     memcpy(v1, vp, (size_t)N * 3 * sizeof(double));
@@ -389,6 +402,12 @@ void orc_step(int N, int p, int beta_mode, int n_iter, double dt, const double *
                                                    : d1[((size_t)i * (P + 1) + q) * 3 + c];
         }
         orc_evaluate(N, P, m, tr, eps, G, 0, N, d1);
+        if (eta > 0) {
+            /* H+ at the positions just evaluated (x1 before this correction) */
+            const double H_plus = orc_timestep_H(N, m, x1, eps, eta, G);
+            dt = dir * 0.5 * (H_minus + H_plus);
+            *H = H_plus;
+        }
         for (int i = 0; i < N; ++i) {
             double d0[(ORC_MAXP + 1) * 3];
             for (int q = 0; q <= P; ++q)
@@ -410,6 +429,31 @@ void orc_step(int N, int p, int beta_mode, int n_iter, double dt, const double *
         for (int c = 0; c < 3; ++c) { x[i * 3 + c] = x1[i * 3 + c]; v[i * 3 + c] = v1[i * 3 + c]; }
     }
     free(xp); free(vp); free(ap); free(tr); free(d1); free(x1); free(v1);
+    return dt;
+}
+
+/* One shared P(EC)^n step of constant dt (Section 2.1 end, Section 3). */
+void orc_step(int N, int p, int beta_mode, int n_iter, double dt, const double *m,
+              double eps, double G, double *x, double *v, double *derivs)
+{
+    step_impl(N, p, beta_mode, n_iter, dt, 0.0, NULL, m, eps, G, x, v, derivs);
+}
+
+/* nsteps time-symmetric variable steps (Section 3.3) forward (dir > 0) or
+ * backward (dir < 0).  *H: in, Eq. 24 at the start; out, the next step's H-.
+ * dts (may be NULL): the nsteps step sizes taken.  Returns the time advanced. */
+double orc_run_timesym(int N, int p, int beta_mode, int n_iter, int dir, double eta, int nsteps,
+                       const double *m, double eps, double G, double *x, double *v, double *derivs,
+                       double *H, double *dts)
+{
+    double t = 0.0;
+    for (int s = 0; s < nsteps; ++s) {
+        const double dt = step_impl(N, p, beta_mode, n_iter, dir < 0 ? -1.0 : 1.0, eta, H, m, eps, G,
+                                    x, v, derivs);
+        if (dts) dts[s] = dt;
+        t += dt;
+    }
+    return t;
 }
 
 /* Corrector alone for N particles (exposed for tests): d0, d1 are N x (p+1) x 3. */
@@ -475,8 +519,9 @@ void orc_ecc(int N, const double *m, const double *x, const double *v, double G,
 /* Section 3.3: time-step criterion                                           */
 /* ------------------------------------------------------------------------- */
 
-/* H = eta min_{i != j} ((r_ij^2 + eps^2)^(3/2) / (m_i + m_j))^(1/2)  (Eq. 24) */
-double orc_timestep_H(int N, const double *m, const double *x, double eps, double eta)
+/* H = eta min_{i != j} ((r_ij^2 + eps^2)^(3/2) / (G (m_i + m_j)))^(1/2)  (Eq. 24,
+ * written there for G = 1: the two-body Kepler time scale of the closest pair) */
+double orc_timestep_H(int N, const double *m, const double *x, double eps, double eta, double G)
 {
     double best = INFINITY;
     for (int i = 0; i < N; ++i)
@@ -484,7 +529,7 @@ double orc_timestep_H(int N, const double *m, const double *x, double eps, doubl
             if (j == i) continue;
             double d[3] = {x[3 * j] - x[3 * i], x[3 * j + 1] - x[3 * i + 1], x[3 * j + 2] - x[3 * i + 2]};
             double s = dot3(d, d) + eps * eps;
-            double q = sqrt(s * s * s / (m[i] + m[j]));
+            double q = sqrt(s * sqrt(s) / (G * (m[i] + m[j])));   /* (s^(3/2) / G M)^(1/2) */
             if (q < best) best = q;
         }
     return eta * best;
