@@ -363,9 +363,17 @@ double orc_timestep_H(int N, const double *m, const double *x, double eps, doubl
  * Time-symmetric variable step (eta > 0, Section 3.3): dt = dir (H- + H+)/2,
  * with dir = +1 or -1 the sign of the dt argument, H- = *H (Eq. 24 at the
  * start of the step) and H+ = Eq. 24 at the positions of the latest
- * evaluation, so that dt is re-chosen in every pass of the iteration; the
- * prediction uses dt = dir H-.  On return *H holds H+ of the last evaluation,
- * the next step's H- (R15).  Returns the dt of the final correction.          */
+ * evaluation, so that dt is re-chosen as the iteration proceeds (R15):
+ *   the prediction uses dt = dir H-;
+ *   every pass corrects with the dt its evaluation was made at, so the
+ *   derivatives and the end time of each correction agree;
+ *   after every pass but the last, dt <- dir (H- + H+)/2 and the corrected
+ *   end state (x, v and the a-derivatives the next evaluation takes, R2) is
+ *   moved to the new end time by its Taylor series with the derivatives just
+ *   evaluated, over the small change of dt.
+ * At convergence dt = dir (H(start) + H(end))/2, symmetric in time.  On return
+ * *H holds H+ of the last evaluation, the next step's H-.  Returns the dt of
+ * the final correction.                                                        */
 static double step_impl(int N, int p, int beta_mode, int n_iter, double dt, double eta, double *H,
                         const double *m, double eps, double G, double *x, double *v, double *derivs)
 {
@@ -402,10 +410,10 @@ static double step_impl(int N, int p, int beta_mode, int n_iter, double dt, doub
                                                    : d1[((size_t)i * (P + 1) + q) * 3 + c];
         }
         orc_evaluate(N, P, m, tr, eps, G, 0, N, d1);
+        double H_plus = 0.0;
         if (eta > 0) {
             /* H+ at the positions just evaluated (x1 before this correction) */
-            const double H_plus = orc_timestep_H(N, m, x1, eps, eta, G);
-            dt = dir * 0.5 * (H_minus + H_plus);
+            H_plus = orc_timestep_H(N, m, x1, eps, eta, G);
             *H = H_plus;
         }
         for (int i = 0; i < N; ++i) {
@@ -414,6 +422,32 @@ static double step_impl(int N, int p, int beta_mode, int n_iter, double dt, doub
                 for (int c = 0; c < 3; ++c) d0[q * 3 + c] = derivs[((size_t)i * K + q) * 3 + c];
             correct_one(p, dt, cv, cx, x + 3 * i, v + 3 * i, d0,
                         d1 + (size_t)i * (P + 1) * 3, x1 + 3 * i, v1 + 3 * i);
+        }
+        if (eta > 0 && it < n_iter - 1) {
+            const double dt_new = dir * 0.5 * (H_minus + H_plus);
+            const double delta = dt_new - dt;
+            /* move the end state by delta: x, v and a^(0..P) by their Taylor
+             * series with a^(0..P) at the old end time */
+            for (int i = 0; i < N; ++i) {
+                double *e = d1 + (size_t)i * (P + 1) * 3;
+                for (int c = 0; c < 3; ++c) {
+                    double a[ORC_MAXP + 1];
+                    for (int q = 0; q <= P; ++q) a[q] = e[q * 3 + c];
+                    double sx = x1[i * 3 + c] + v1[i * 3 + c] * delta, sv = v1[i * 3 + c];
+                    for (int q = 0; q <= P; ++q) {
+                        sx += a[q] * pow(delta, q + 2) / fact(q + 2);
+                        sv += a[q] * pow(delta, q + 1) / fact(q + 1);
+                    }
+                    x1[i * 3 + c] = sx;
+                    v1[i * 3 + c] = sv;
+                    for (int q = 0; q <= P; ++q) {
+                        double sq = 0.0;
+                        for (int j = q; j <= P; ++j) sq += a[j] * pow(delta, j - q) / fact(j - q);
+                        e[q * 3 + c] = sq;
+                    }
+                }
+            }
+            dt = dt_new;
         }
     }
 
