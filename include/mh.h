@@ -53,7 +53,7 @@ typedef enum {
 
 enum { MH_BETA_MODIFIED = 0, MH_BETA_STANDARD = 1 };
 enum { MH_PREC_FP64 = 0, MH_PREC_FP32PAIR = 1 };
-enum { MH_STEP_SHARED = 0, MH_STEP_BLOCK = 1 };
+enum { MH_STEP_SHARED = 0, MH_STEP_BLOCK = 1, MH_STEP_TIMESYM = 2 };
 
 /* Integrator configuration.  Fill with mh_config_default() first. */
 typedef struct {
@@ -63,9 +63,11 @@ typedef struct {
                            MH_PREC_FP32PAIR: pair arithmetic in FP32, state, pre-cast
                            differences (hi/lo split), accumulation across j-tiles,
                            corrector and diagnostics in FP64. */
-    int step_mode;      /* MH_STEP_SHARED or MH_STEP_BLOCK */
+    int step_mode;      /* MH_STEP_SHARED, MH_STEP_BLOCK, or MH_STEP_TIMESYM (time-symmetric
+                           variable shared step of Section 3.3, advanced by mh_step_timesym) */
     double G;           /* gravitational constant (default 1) */
-    double eta;         /* block steps: accuracy parameter of the per-particle criterion */
+    double eta;         /* block steps: accuracy parameter of the per-particle criterion;
+                           time-symmetric steps: eta of Eq. 24 */
     double dt_max;      /* block steps: largest step (levels are dt_max * 2^-k, default 1/32) */
     int k_max;          /* block steps: deepest level, 0 <= k_max <= 30 (default 12) */
     int split_j;        /* pair kernel: j-range split factor, 0 = automatic */
@@ -74,11 +76,13 @@ typedef struct {
                            (at most 32 such bodies; 0 disables; default 1e-3).  In
                            a disc around a central mass this keeps the dominant
                            central force at FP64 accuracy for O(N) extra work. */
-    int symmetric;      /* FP64 form, shared steps: 1 (default) evaluates every unordered
-                           pair once and adds its terms to both bodies (each term of
-                           the Section 3 pair derivatives is odd under i <-> j), which
-                           halves the FP64 work; 0 evaluates every ordered pair.  The
-                           symmetric kernel needs (C + Np/256) partial-sum slots of
+    int symmetric;      /* FP64 form, shared and time-symmetric steps: 2 evaluates every
+                           unordered pair once and adds its terms to both bodies (each
+                           term of the Section 3 pair derivatives is odd under i <-> j),
+                           which halves the FP64 work; 0 evaluates every ordered pair;
+                           1 (default) chooses 2 from N padded to 256 >= 2048 bodies up
+                           (below, the ordered kernel spreads the pairs over more SMs).
+                           The symmetric kernel needs (C + Np/256) partial-sum slots of
                            (P+1)*3*Np doubles (C ~ 10; Np = N padded to 256), about
                            1.7 GB at N = 65536 and order 8; above 8 GiB, or with block
                            steps, the ordered kernel runs. */
@@ -146,6 +150,18 @@ void mh_destroy(mh_sim *sim);
  * return the whole system is at t + dt.  One 16-byte device-to-host read per
  * block step sizes the evaluation of the active list. */
 int mh_step(mh_sim *sim, double dt, int n_iter);
+
+/* Time-symmetric variable shared steps (Section 3.3; step_mode MH_STEP_TIMESYM,
+ * FP64 form, N >= 2).  Each step has dt = (H- + H+)/2 (negated when backward != 0)
+ * with H = eta min_{i != j} ((r_ij^2 + eps^2)^(3/2) / (G (m_i + m_j)))^(1/2)
+ * (Eq. 24, there with G = 1): H- at the start of the step, H+ at the positions of
+ * each evaluation of P(EC)^n_iter, so that dt is re-chosen in every pass and the
+ * converged step is symmetric in time.  The prediction uses dt = H-; the next
+ * step's H- is H+ of this step's last evaluation (at creation and after
+ * mh_set_state, Eq. 24 at the given positions).  Advances nsteps steps; dt and
+ * the time stay on the device (mh_sync reports t).  Needs the pair-symmetric
+ * FP64 evaluation (its partial sums within 8 GiB); 1 <= n_iter <= 64. */
+int mh_step_timesym(mh_sim *sim, int64_t nsteps, int n_iter, int backward);
 
 /* Copy the current state to host buffers (waits for queued work). */
 int mh_sync(mh_sim *sim, mh_state *out);

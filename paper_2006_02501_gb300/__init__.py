@@ -61,16 +61,19 @@ class Simulation:
     pairs run in FP64 (None = library default 1e-3, 0 = all pairs FP32);
     block: None for shared steps, or {"dt_max", "k_max", "eta"} for block time
     steps (order 6 or 8; step() then needs a multiple of dt_max);
-    symmetric: FP64 shared-step evaluation of each unordered pair once, both
-    bodies updated (default), or of every ordered pair (False);
+    symmetric: FP64 evaluation of each unordered pair once, both bodies
+    updated: 1/True = from 2048 padded bodies up (default), 2 = always,
+    0/False = never (every ordered pair);
     fp32_variant: precision form evaluation kernel, 0 = autotuned, 1/2/3 fixed
-    (one i-body per thread, two, two in packed FP32x2 lanes).
+    (one i-body per thread, two, two in packed FP32x2 lanes);
+    timesym_eta: not None for time-symmetric variable shared steps with this
+    eta of Eq. 24 (FP64; advance with step_timesym()).
     """
 
     def __init__(self, order: int, m, x, v, eps: float, precision: int = MH_PREC_FP64,
                  beta: int = MH_BETA_MODIFIED, G: float = 1.0, stream=None, split_j: int = 0,
                  heavy_frac: float | None = None, block: dict | None = None,
-                 symmetric: bool = True, fp32_variant: int = 0):
+                 symmetric: int = 1, fp32_variant: int = 0, timesym_eta: float | None = None):
         L = _capi.lib()
         m = _host(m)
         N = m.shape[0]
@@ -80,8 +83,11 @@ class Simulation:
         cfg.order, cfg.precision, cfg.beta_mode, cfg.G, cfg.split_j = order, precision, beta, G, split_j
         if heavy_frac is not None:
             cfg.heavy_frac = heavy_frac
-        cfg.symmetric = 1 if symmetric else 0
+        cfg.symmetric = int(symmetric)
         cfg.fp32_variant = int(fp32_variant)
+        if timesym_eta is not None:
+            cfg.step_mode = _capi.MH_STEP_TIMESYM
+            cfg.eta = float(timesym_eta)
         if block is not None:
             cfg.step_mode = _capi.MH_STEP_BLOCK
             cfg.dt_max = float(block.get("dt_max", cfg.dt_max))
@@ -116,6 +122,10 @@ class Simulation:
         L = _capi.lib()
         for _ in range(nsteps):
             check(L.mh_step(self._h, float(dt), int(n_iter)))
+
+    def step_timesym(self, nsteps: int, n_iter: int, backward: bool = False) -> None:
+        """nsteps time-symmetric variable steps (Section 3.3), stream-ordered."""
+        check(_capi.lib().mh_step_timesym(self._h, int(nsteps), int(n_iter), 1 if backward else 0))
 
     def sync(self):
         """(t, x (N,3), v (N,3), derivs (N,2p,3)) copied to the host."""

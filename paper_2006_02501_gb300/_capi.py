@@ -23,7 +23,7 @@ MH_ENOTCONV = 1
 
 MH_BETA_MODIFIED, MH_BETA_STANDARD = 0, 1
 MH_PREC_FP64, MH_PREC_FP32PAIR = 0, 1
-MH_STEP_SHARED, MH_STEP_BLOCK = 0, 1
+MH_STEP_SHARED, MH_STEP_BLOCK, MH_STEP_TIMESYM = 0, 1, 2
 
 # Every entry point declared in include/mh.h (checked by the CPU test suite).
 EXPORTS = [
@@ -32,7 +32,7 @@ EXPORTS = [
     "mh_set_timing", "mh_pair_eval_noalloc", "mh_create_batch", "mh_step_batch", "mh_batch_tune",
     "mh_batch_energy", "mh_step_converge", "mh_set_predictor", "mh_collect_samples", "mh_mlp_create",
     "mh_mlp_destroy", "mh_mlp_num_params", "mh_mlp_get_params", "mh_mlp_set_params", "mh_mlp_forward",
-    "mh_mlp_loss_grad", "mh_mlp_train", "mh_predict",
+    "mh_mlp_loss_grad", "mh_mlp_train", "mh_predict", "mh_step_timesym",
 ]
 
 
@@ -86,6 +86,7 @@ def lib() -> ctypes.CDLL:
             L.mh_destroy.restype = None
             L.mh_mlp_destroy.restype = None
             L.mh_step.argtypes = [P, D, I]
+            L.mh_step_timesym.argtypes = [P, I64, I, I]
             L.mh_sync.argtypes = [P, ctypes.POINTER(StateC)]
             L.mh_set_state.argtypes = [P, ctypes.POINTER(StateC)]
             L.mh_diagnostics.argtypes = [P, DP, DP, I]

@@ -4,6 +4,7 @@
     python -m paper_2006_02501_gb300.compare_forms block    # block steps, FP32-pair vs FP64, N = 262144
     python -m paper_2006_02501_gb300.compare_forms batch    # 4096 planetary systems, 10^4 steps
     python -m paper_2006_02501_gb300.compare_forms learned  # learned predictor on the N = 65536 disc
+    python -m paper_2006_02501_gb300.compare_forms table1   # Section 3.3 disc, time-symmetric steps
 
 Each prints JSON lines.  Throughputs are timed with CUDA events on the
 simulation's stream; pair interactions and particle steps come from the
@@ -208,6 +209,42 @@ def run_learned(args):
                       "tol": tol, **res}), flush=True)
 
 
+def run_table1(args):
+    """Section 3.3 N-body test: 100 bodies of 1e-5 around a unit mass, a
+    log-spaced in [0.1, 10], Rayleigh e, i with sigma_i = 2 sigma_e = 0.12,
+    eps = 1e-6, 8th order, time-symmetric variable shared step (Eq. 24), run to
+    t = 100 pi; the median |E - E0|/|E0| over the last time unit, per (n, eta)."""
+    torch, mh, I = _setup()
+    st = torch.cuda.Stream()
+    m, x, v = I.disc_100(seed=args.seed)
+    t_end = args.t_end
+    for n_iter in args.n:
+        for eta in args.eta:
+            with mh.Simulation(args.order, m, x, v, 1e-6, stream=st, timesym_eta=eta) as sim:
+                E0 = sim.energy()
+                t, steps, samples = 0.0, 0, []
+                w0 = time.perf_counter()
+                while t < t_end:
+                    # coarse chunks until just before the last time unit (sized from the
+                    # mean step so far), then sample every few steps
+                    if t < t_end - 1.2 and steps > 0:
+                        chunk = int(min(args.chunk, max(args.sample_every, (t_end - 1.2 - t) / (t / steps))))
+                    elif t < t_end - 1.2:
+                        chunk = args.sample_every
+                    else:
+                        chunk = args.sample_every
+                    sim.step_timesym(chunk, n_iter)
+                    steps += chunk
+                    t = sim.sync()[0]
+                    if t >= t_end - 1.0:
+                        samples.append(abs(sim.energy() / E0 - 1))
+                wall = time.perf_counter() - w0
+            print(json.dumps({"case": "table1", "order": args.order, "n": n_iter, "eta": eta, "t": t,
+                              "steps": steps, "median_dE_last_unit": float(np.median(samples)),
+                              "samples": len(samples), "seconds": wall, "us_per_step": wall / steps * 1e6,
+                              "seed": args.seed}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -229,8 +266,17 @@ def main():
     d.add_argument("--steps-per-disc", type=int, default=8)
     d.add_argument("--epochs", type=int, default=30)
     d.add_argument("--max-passes", type=int, default=6)
+    t1 = sub.add_parser("table1")
+    t1.add_argument("--n", type=int, nargs="+", default=[3, 4])
+    t1.add_argument("--eta", type=float, nargs="+", default=[0.08, 0.04, 0.02, 0.01, 0.005])
+    t1.add_argument("--order", type=int, default=8)
+    t1.add_argument("--t-end", type=float, default=100 * np.pi)
+    t1.add_argument("--seed", type=int, default=5)
+    t1.add_argument("--chunk", type=int, default=4000)
+    t1.add_argument("--sample-every", type=int, default=20)
     args = ap.parse_args()
-    {"ecc": run_ecc, "block": run_block, "batch": run_batch, "learned": run_learned}[args.cmd](args)
+    {"ecc": run_ecc, "block": run_block, "batch": run_batch, "learned": run_learned,
+     "table1": run_table1}[args.cmd](args)
 
 
 if __name__ == "__main__":

@@ -46,7 +46,7 @@ int dalloc(T **ptr, size_t count)
 void free_state(DeviceState &s)
 {
     void *ptrs[] = {s.m, s.x0, s.v0, s.d0, s.x1, s.v1, s.jrec, s.jrec32, s.part, s.diag, s.flag, s.bound,
-                    s.heavy, s.T, s.level, s.act, s.blk};
+                    s.heavy, s.T, s.level, s.act, s.blk, s.tsw, s.tst};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (s.blk_host) cudaFreeHost(s.blk_host);
@@ -167,10 +167,19 @@ int tuned_variant(mh_sim *sim, int P, int64_t n_i, const int *ilist, int *varian
 }
 
 // One O(N^2) evaluation of a^(0..P) for all bodies into s.part; returns S via *split.
-int evaluate(mh_sim *sim, int P, int precision, int *split)
+// wslot (optional, device, zeroed by the caller): raised to the maximum over
+// pairs of G (m_i + m_j) s^(-3/2) (Eq. 24); FP64 pair-symmetric kernel only.
+int evaluate(mh_sim *sim, int P, int precision, int *split, unsigned long long *wslot = nullptr)
 {
     DeviceState &s = sim->s;
-    if (precision == MH_PREC_FP64 && P <= 3 && sim->cfg.symmetric) {
+    if (wslot && (precision != MH_PREC_FP64 || P > 3)) {
+        set_error("evaluate: the Eq. 24 maximum is tracked by the FP64 kernels for P <= 3 only");
+        return MH_EINVAL;
+    }
+    // pair-symmetric kernel: always (symmetric = 2), or (symmetric = 1) once there
+    // are 16 blocks of 128 bodies; below, its blocks are too few to fill the GPU
+    const int sym_mode = sim->cfg.symmetric;
+    if (precision == MH_PREC_FP64 && P <= 3 && (sym_mode == 2 || (sym_mode == 1 && s.Np >= kSymMinNp))) {
         const SymPlan sp = plan_sym(P, s.Np, sim->device);
         const size_t need = (size_t)sp.slots * (P + 1) * 3 * s.Np;
         if (sp.nB > 0 && need * sizeof(double) <= kSymMaxPartBytes) {
@@ -181,7 +190,7 @@ int evaluate(mh_sim *sim, int P, int precision, int *split)
                 if ((rc = timed_event_pair(sim, &ev))) return rc;
                 MH_CUDA(cudaEventRecord(ev.first, sim->stream));
             }
-            rc = launch_pair_sym(P, sp, s.jrec, s.m, s.Np, s.N, sim->eps, sim->cfg.G, s.part, sim->stream);
+            rc = launch_pair_sym(P, sp, s.jrec, s.m, s.Np, s.N, sim->eps, sim->cfg.G, s.part, sim->stream, wslot);
             if (rc) return rc;
             if (sim->timing) {
                 MH_CUDA(cudaEventRecord(ev.second, sim->stream));
@@ -209,7 +218,7 @@ int evaluate(mh_sim *sim, int P, int precision, int *split)
     int rc = ensure_part(s, (size_t)slots * (P + 1) * 3 * s.Np, sim->stream);
     if (rc) return rc;
     rc = launch_pair(P, precision, s.N, s.Np, s.m, s.jrec, s.jrec32, sim->eps, sim->cfg.G, 0, s.N,
-                     s.part, s.Np, pl, sim->stream);
+                     s.part, s.Np, pl, sim->stream, nullptr, wslot);
     if (rc) return rc;
     if (sim->timing) {
         MH_CUDA(cudaEventRecord(ev.second, sim->stream));
@@ -221,7 +230,14 @@ int evaluate(mh_sim *sim, int P, int precision, int *split)
         if (rc) return rc;
         sim->ctr.kernel_launches += 1;
     }
-    *split = slots;
+    int out_slots = slots;
+    if (precision == MH_PREC_FP64 && s.N < kSmallN && slots >= 4) {
+        // small systems: pre-add the many j-chunk slots with one thread per (row, body)
+        if ((rc = launch_reduce_slots(s, (P + 1) * 3, slots, sim->stream))) return rc;
+        sim->ctr.kernel_launches += 1;
+        out_slots = 1;
+    }
+    *split = out_slots;
     sim->ctr.evaluations += 1;
     sim->ctr.pair_interactions += (double)s.N * (double)(s.N - 1);
     sim->ctr.kernel_launches += 1;
@@ -247,6 +263,25 @@ int initialise(mh_sim *sim)
     }
     sim->ctr.evaluations -= s.p;   // initialisation passes are not step evaluations
     sim->ctr.pair_interactions -= (double)s.p * (double)s.N * (double)(s.N - 1);
+    return MH_OK;
+}
+
+// Time-symmetric steps: Eq. 24 at the committed positions x0, written to word
+// kTsMaxIter of the Eq. 24 words (bank 1, pass 0), which becomes the next
+// step's H-.  One P = 1 evaluation of the pair-symmetric kernel (its partial
+// sums are scratch here).
+int timesym_start(mh_sim *sim)
+{
+    DeviceState &s = sim->s;
+    if (!s.tsw) return MH_OK;
+    MH_CUDA(cudaMemsetAsync(s.tsw + kTsMaxIter, 0, sizeof(unsigned long long), sim->stream));
+    if (int rc = launch_init_rows(s, 0, sim->stream)) return rc;
+    int split = 0;
+    if (int rc = evaluate(sim, 1, MH_PREC_FP64, &split, s.tsw + kTsMaxIter)) return rc;
+    sim->ctr.evaluations -= 1;        // not a step evaluation
+    sim->ctr.pair_interactions -= (double)s.N * (double)(s.N - 1);
+    sim->ctr.kernel_launches += 1;
+    s.ts_prev = kTsMaxIter;
     return MH_OK;
 }
 
@@ -328,7 +363,16 @@ int mh::create_shell(mh_sim **out, int64_t N, int order, const double *m, const 
     if (!(eps >= 0.0) || !std::isfinite(eps)) { set_error("mh_create: eps must be finite and >= 0"); return MH_EINVAL; }
     if (c.precision != MH_PREC_FP64 && c.precision != MH_PREC_FP32PAIR) { set_error("mh_create: bad precision"); return MH_EINVAL; }
     if (c.beta_mode != MH_BETA_MODIFIED && c.beta_mode != MH_BETA_STANDARD) { set_error("mh_create: bad beta_mode"); return MH_EINVAL; }
-    if (c.step_mode != MH_STEP_SHARED && c.step_mode != MH_STEP_BLOCK) { set_error("mh_create: bad step_mode"); return MH_EINVAL; }
+    if (c.step_mode != MH_STEP_SHARED && c.step_mode != MH_STEP_BLOCK && c.step_mode != MH_STEP_TIMESYM) {
+        set_error("mh_create: bad step_mode");
+        return MH_EINVAL;
+    }
+    if (c.step_mode == MH_STEP_TIMESYM &&
+        (c.precision != MH_PREC_FP64 || N < 2 || !(c.eta > 0.0) || !std::isfinite(c.eta))) {
+        set_error("mh_create: time-symmetric steps need FP64, N >= 2 and a finite eta > 0");
+        return MH_EINVAL;
+    }
+    if (c.symmetric < 0 || c.symmetric > 2) { set_error("mh_create: symmetric must be 0, 1 or 2"); return MH_EINVAL; }
     if (c.fp32_variant < 0 || c.fp32_variant > 3) { set_error("mh_create: fp32_variant must be 0..3"); return MH_EINVAL; }
     if (c.step_mode == MH_STEP_BLOCK) {
         if (p < 2) { set_error("mh_create: block steps need order 6 or 8"); return MH_EINVAL; }
@@ -378,6 +422,12 @@ int mh::create_shell(mh_sim **out, int64_t N, int order, const double *m, const 
             return fail(rc);
         cudaError_t eh = cudaMallocHost((void **)&s.blk_host, 2 * sizeof(unsigned long long));
         if (eh != cudaSuccess) return fail(cuda_fail(eh, "cudaMallocHost"));
+    }
+    if (c.step_mode == MH_STEP_TIMESYM) {
+        if ((rc = dalloc(&s.tsw, 2 * kTsMaxIter)) || (rc = dalloc(&s.tst, 1))) return fail(rc);
+        cudaError_t ez = cudaMemsetAsync(s.tsw, 0, 2 * kTsMaxIter * sizeof(unsigned long long), sim->stream);
+        if (ez == cudaSuccess) ez = cudaMemsetAsync(s.tst, 0, sizeof(double), sim->stream);
+        if (ez != cudaSuccess) return fail(cuda_fail(ez, "cudaMemsetAsync"));
     }
 
     std::vector<double> h;
@@ -430,6 +480,7 @@ int mh::create_shell(mh_sim **out, int64_t N, int order, const double *m, const 
     if (init) {
         if ((rc = initialise(sim))) return fail(rc);
         if (c.step_mode == MH_STEP_BLOCK && (rc = launch_block_init(s, c, sim->stream))) return fail(rc);
+        if ((rc = timesym_start(sim))) return fail(rc);
     }
     e = cudaStreamSynchronize(sim->stream);
     if (e != cudaSuccess) return fail(cuda_fail(e, "initialisation"));
@@ -466,6 +517,7 @@ void mh_destroy(mh_sim *sim)
     if (sim->lsave) cudaFree(sim->lsave);
     if (sim->conv) cudaFree(sim->conv);
     if (sim->conv_host) cudaFreeHost(sim->conv_host);
+    for (auto &kv : sim->ts_graphs) cudaGraphExecDestroy(kv.second);
     free_state(sim->s);
     if (sim->own_stream && sim->stream) cudaStreamDestroy(sim->stream);
     delete sim;
@@ -598,6 +650,101 @@ static int shared_step(mh_sim *sim, double dt, int n_iter, double tol, int *n_us
     return MH_OK;
 }
 
+// One time-symmetric variable step (Section 3.3): P with dt = dir H-, then
+// n_iter (E, C) passes; every E also finds Eq. 24's maximum at the positions
+// it evaluates and the C after it uses dt = dir (H- + H+)/2.  The last E's word
+// is the next step's H-.  dt and the clock stay on the device.
+static int timesym_step(mh_sim *sim, int n_iter, double dir)
+{
+    DeviceState &s = sim->s;
+    TimeSymArgs ts;
+    ts.w = s.tsw;
+    ts.t = s.tst;
+    ts.prev = s.ts_prev;
+    ts.bank = 1 - s.ts_prev / kTsMaxIter;
+    ts.n_iter = n_iter;
+    ts.eta = sim->cfg.eta;
+    ts.dir = dir;
+    int rc = launch_step_phase(s, sim->cfg, 0.0, 0, false, 0, sim->stream, nullptr, &ts);
+    if (rc) return rc;
+    sim->ctr.kernel_launches += 1;
+    for (int it = 0; it < n_iter; ++it) {
+        int split = 0;
+        if ((rc = evaluate(sim, s.p, MH_PREC_FP64, &split, s.tsw + ts.bank * kTsMaxIter + it))) return rc;
+        ts.pass = it;
+        const bool last = it == n_iter - 1;
+        if ((rc = launch_step_phase(s, sim->cfg, 0.0, 1, last, split, sim->stream, nullptr, &ts))) return rc;
+        sim->ctr.kernel_launches += 1;
+    }
+    s.ts_prev = ts.bank * kTsMaxIter + n_iter - 1;
+    sim->ctr.steps += 1;
+    sim->ctr.particle_steps += (double)s.N;
+    return MH_OK;
+}
+
+int mh_step_timesym(mh_sim *sim, int64_t nsteps, int n_iter, int backward)
+{
+    if (int rc = check_handle(sim)) return rc;
+    if (sim->cfg.step_mode != MH_STEP_TIMESYM || !sim->s.tsw) {
+        set_error("mh_step_timesym: the simulation was not created with step_mode MH_STEP_TIMESYM");
+        return MH_EINVAL;
+    }
+    if (nsteps < 0 || n_iter < 1 || n_iter > kTsMaxIter) {
+        set_error("mh_step_timesym: nsteps >= 0 and 1 <= n_iter <= 64 required");
+        return MH_EINVAL;
+    }
+    const double dir = backward ? -1.0 : 1.0;
+    const std::pair<int, int> key(n_iter, backward ? 1 : 0);
+    int64_t k = 0;
+    while (k < nsteps) {
+        // Two consecutive steps use the two banks of Eq. 24 words in turn and end
+        // where they began (H- in bank 0, word n_iter - 1), so from there pairs of
+        // steps replay one captured CUDA graph: the per-launch host cost of small
+        // systems goes away.  Plain launches: the first step(s), an odd last
+        // step, and while per-launch timing is on.
+        const bool graphable = sim->s.ts_prev == n_iter - 1 && nsteps - k >= 2 && !sim->timing &&
+                               sim->s.part != nullptr;
+        if (!graphable) {
+            if (int rc = timesym_step(sim, n_iter, dir)) return rc;
+            ++k;
+            continue;
+        }
+        auto it = sim->ts_graphs.find(key);
+        if (it == sim->ts_graphs.end()) {
+            const mh_counters before = sim->ctr;
+            cudaGraph_t g = nullptr;
+            MH_CUDA(cudaStreamBeginCapture(sim->stream, cudaStreamCaptureModeThreadLocal));
+            int rc = timesym_step(sim, n_iter, dir);
+            if (!rc) rc = timesym_step(sim, n_iter, dir);
+            cudaError_t e = cudaStreamEndCapture(sim->stream, &g);
+            mh_counters inc = sim->ctr;
+            sim->ctr = before;
+            if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+            if (e != cudaSuccess) return cuda_fail(e, "mh_step_timesym: stream capture");
+            cudaGraphExec_t ex = nullptr;
+            e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(e, "mh_step_timesym: graph instantiation");
+            inc.steps -= before.steps;
+            inc.evaluations -= before.evaluations;
+            inc.pair_interactions -= before.pair_interactions;
+            inc.particle_steps -= before.particle_steps;
+            inc.kernel_launches -= before.kernel_launches;
+            sim->ts_graph_inc[key] = inc;
+            it = sim->ts_graphs.emplace(key, ex).first;
+        }
+        MH_CUDA(cudaGraphLaunch(it->second, sim->stream));
+        const mh_counters &inc = sim->ts_graph_inc[key];
+        sim->ctr.steps += inc.steps;
+        sim->ctr.evaluations += inc.evaluations;
+        sim->ctr.pair_interactions += inc.pair_interactions;
+        sim->ctr.particle_steps += inc.particle_steps;
+        sim->ctr.kernel_launches += inc.kernel_launches;
+        k += 2;
+    }
+    return MH_OK;
+}
+
 int mh_step(mh_sim *sim, double dt, int n_iter)
 {
     if (int rc = check_handle(sim)) return rc;
@@ -605,6 +752,10 @@ int mh_step(mh_sim *sim, double dt, int n_iter)
     if (n_iter < 1 || n_iter > 64) { set_error("mh_step: n_iter must be in [1, 64]"); return MH_EINVAL; }
     if (sim->batch) { set_error("mh_step: batched simulations advance with mh_step_batch"); return MH_EINVAL; }
     if (sim->cfg.step_mode == MH_STEP_BLOCK) return block_advance(sim, dt, n_iter);
+    if (sim->cfg.step_mode == MH_STEP_TIMESYM) {
+        set_error("mh_step: time-symmetric simulations advance with mh_step_timesym");
+        return MH_EINVAL;
+    }
     return shared_step(sim, dt, n_iter, -1.0, nullptr);
 }
 
@@ -727,6 +878,7 @@ int mh_sync(mh_sim *sim, mh_state *out)
     DeviceState &s = sim->s;
     MH_CUDA(cudaStreamSynchronize(sim->stream));
     if (int rc = collect_timing(sim)) return rc;
+    if (s.tst) MH_CUDA(cudaMemcpy(&sim->t, s.tst, sizeof(double), cudaMemcpyDeviceToHost));
     out->t = sim->t;
     std::vector<double> h;
     if (out->x) {
@@ -764,12 +916,14 @@ int mh_set_state(mh_sim *sim, const mh_state *in)
     MH_CUDA(cudaMemsetAsync(s.flag, 0, sizeof(int), sim->stream));
     if (int rc = upload_bounds(s, in->x, in->v, sim->stream)) return rc;
     sim->t = in->t;
+    if (s.tst) MH_CUDA(cudaMemcpy(s.tst, &in->t, sizeof(double), cudaMemcpyHostToDevice));
     if (in->derivs) {
         to_soa(in->derivs, s.N, 2 * s.p, s.Np, h, 0.0);
         MH_CUDA(cudaMemcpy(s.d0, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
     } else if (int rc = initialise(sim)) {
         return rc;
     }
+    if (int rc = timesym_start(sim)) return rc;
     if (sim->cfg.step_mode == MH_STEP_BLOCK) {
         // every body restarts at the given time; levels from the caller or the criterion
         s.T_now = 0;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <utility>
 #include <vector>
@@ -53,6 +54,21 @@ struct PairPlan {
     bool packed = false;  // FP32 form: the two i-bodies of a thread share paired FP32 instructions
 };
 
+// Time-symmetric variable shared step (Section 3.3): dt = dir (H- + H+)/2 with
+// H = eta w^(-1/2) (Eq. 24), w the maximum over pairs of G (m_i + m_j) s^(-3/2).
+// The evaluations write w into device words; the predictor and corrector read
+// them and compute dt on the device, so a step needs no host round trip.
+constexpr int kTsMaxIter = 64;       // words per bank (one per evaluation of a step)
+struct TimeSymArgs {
+    unsigned long long *w = nullptr; // [2][kTsMaxIter] bit patterns of w, by bank and pass; null: constant dt
+    double *t = nullptr;             // simulation time (device)
+    int prev = 0;                    // index into w of the evaluation that gives this step's H-
+    int bank = 0;                    // this step's evaluations write w[bank * kTsMaxIter + pass]
+    int pass = 0;                    // corrector: the evaluation it follows
+    int n_iter = 0;                  // passes of this step (the predictor clears that many words)
+    double eta = 0.0, dir = 1.0;
+};
+
 // Device buffers of one simulation (every per-particle array is padded to Np).
 struct DeviceState {
     int64_t N = 0, Np = 0;
@@ -84,6 +100,11 @@ struct DeviceState {
     unsigned long long *blk = nullptr;
     unsigned long long *blk_host = nullptr;   // pinned host mirror of blk
     long long T_now = 0;
+    // Time-symmetric variable steps: [2][kTsMaxIter] words of Eq. 24, the device
+    // clock, and the index of the word holding the next step's H-.
+    unsigned long long *tsw = nullptr;
+    double *tst = nullptr;
+    int ts_prev = 0;
 };
 
 constexpr int kMaxHeavy = 32;
@@ -92,6 +113,12 @@ constexpr int kMaxHeavy = 32;
 // 0.375 Np^2 bytes at order 8, i.e. Np up to ~146k); above it the one-sided
 // kernel runs.
 constexpr size_t kSymMaxPartBytes = (size_t)8 << 30;
+// Smallest padded body count for which symmetric = 1 picks the pair-symmetric
+// kernel (16 blocks of 128 bodies, 144 block pairs).
+constexpr int64_t kSymMinNp = 2048;
+// Below this many bodies the O(N) step kernels run one warp per block and the
+// FP64 evaluation's j-chunk partial sums are pre-added in parallel.
+constexpr int64_t kSmallN = 8192;
 
 }  // namespace mh
 
@@ -112,6 +139,9 @@ struct mh_sim {
     float *lfeat = nullptr, *lout = nullptr;
     double *lsave = nullptr;      // x0, v0, d0 copies for mh_collect_samples
     unsigned long long *conv = nullptr, *conv_host = nullptr;
+    // time-symmetric steps: CUDA graphs of two consecutive steps, by (n_iter, backward)
+    std::map<std::pair<int, int>, cudaGraphExec_t> ts_graphs;
+    std::map<std::pair<int, int>, mh_counters> ts_graph_inc;   // counter increments of one replay
 };
 
 namespace mh {
@@ -130,13 +160,17 @@ void free_batch(mh_sim *sim);
 // with masses m, or jrec32 (precision form, nf32(P) rows, mass last).
 // ilist (optional, device): position i in [i0, i1) evaluates body ilist[i]; the
 // partial sums are stored by position.
+// wmax (optional, device, FP64 and P <= 3): raised to the maximum over pairs of
+// G (m_i + m_j) s^(-3/2) as a bit pattern (Section 3.3, Eq. 24).
 int launch_pair(int P, int precision, int64_t n_j, int64_t ld, const double *m, const double *jrec,
                 const float *jrec32, double eps, double G, int64_t i0, int64_t i1, double *part,
-                int64_t part_ld, const PairPlan &plan, cudaStream_t st, const int *ilist = nullptr);
+                int64_t part_ld, const PairPlan &plan, cudaStream_t st, const int *ilist = nullptr,
+                unsigned long long *wmax = nullptr);
 
 // O(N) step kernels (integrator.cu): phase 0 = predict, 1 = correct.
 int launch_step_phase(const DeviceState &s, const mh_config &cfg, double dt, int phase, bool last,
-                      int split, cudaStream_t st, unsigned long long *conv = nullptr);
+                      int split, cudaStream_t st, unsigned long long *conv = nullptr,
+                      const TimeSymArgs *ts = nullptr);
 int launch_collect(const DeviceState &s, double dt, const double *x0s, const double *v0s, const double *d0s,
                    float *feats, float *targ, cudaStream_t st);
 int launch_learned_features(const DeviceState &s, double dt, float *feats, cudaStream_t st);
@@ -151,6 +185,8 @@ int launch_block_schedule(const DeviceState &s, const mh_config &cfg, cudaStream
 int launch_block_phase(const DeviceState &s, const mh_config &cfg, long long T_next, int64_t n_act,
                        int phase, bool last, int split, cudaStream_t st);
 int launch_init_reduce(const DeviceState &s, int nr, int lo, int hi, int split, cudaStream_t st);
+// Small systems: slot 0 of s.part <- sum of its first `split` slots (rows nr).
+int launch_reduce_slots(const DeviceState &s, int nr, int split, cudaStream_t st);
 int launch_reduce_out(int64_t n, int64_t ld_part, int nr, int split, const double *part, double *out,
                       cudaStream_t st);
 int launch_split32(int64_t N, int P, const double *traj, const double *m, double G, float *rows,
@@ -193,8 +229,10 @@ struct SymPlan {
     int slots = 0;                      // C + D
 };
 SymPlan plan_sym(int P, int64_t ld, int device);
+// wmax (optional, device): raised to the maximum over pairs of G (m_i + m_j) s^(-3/2)
+// as a bit pattern (the time-step criterion of Section 3.3, Eq. 24).
 int launch_pair_sym(int P, const SymPlan &plan, const double *jrec, const double *m, int64_t ld, int64_t N,
-                    double eps, double G, double *part, cudaStream_t st);
+                    double eps, double G, double *part, cudaStream_t st, unsigned long long *wmax = nullptr);
 
 // FP64 contributions of the heavy source bodies to every body i < N, written
 // to partial slot `slot` (rows (P+1)*3 of stride ld) of part.

@@ -33,7 +33,36 @@ struct StepArgs {
     const unsigned long long *bound_rd;   // [x, v] grid bounds read by this kernel
     unsigned long long *bound_wr;         // [x, v] raised with this kernel's values
     unsigned long long *conv = nullptr;   // optional [max |x_new - x_old|, max |x_new|] (double bits)
+    TimeSymArgs ts{};                     // time-symmetric variable step (ts.w != null), else dt above
 };
+
+// H of Eq. 24 from a word holding the maximum over pairs of G (m_i + m_j) s^(-3/2).
+__device__ __forceinline__ double eq24_H(const TimeSymArgs &ts, int idx)
+{
+    return ts.eta * rsqrt(__longlong_as_double((long long)ts.w[idx]));
+}
+
+// Step of the predictor: dir H- (Section 3.3; the first estimate of dt).
+__device__ __forceinline__ double predictor_dt(const StepArgs &a)
+{
+    return a.ts.w ? a.ts.dir * eq24_H(a.ts, a.ts.prev) : a.dt;
+}
+
+// Time-symmetric steps (Section 3.3, reading R15): pass k corrects with the dt
+// its evaluation was made at -- dir H- for the first pass, dir (H- + H+_(k-1))/2
+// after -- and, unless it is the last pass, moves the corrected end state to the
+// next dt = dir (H- + H+_k)/2, H+_k being Eq. 24 at the positions pass k evaluated.
+__device__ __forceinline__ double timesym_dt(const StepArgs &a, int after_pass)
+{
+    const double Hm = eq24_H(a.ts, a.ts.prev);
+    return after_pass < 0 ? a.ts.dir * Hm
+                          : a.ts.dir * 0.5 * (Hm + eq24_H(a.ts, a.ts.bank * kTsMaxIter + after_pass));
+}
+
+__device__ __forceinline__ double corrector_dt(const StepArgs &a)
+{
+    return a.ts.w ? timesym_dt(a, a.ts.pass - 1) : a.dt;
+}
 
 __device__ __forceinline__ void raise_bound(unsigned long long *slot, double val)
 {
@@ -100,7 +129,9 @@ __global__ void k_predict(StepArgs a)
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i0 < a.N;
     const int64_t i = live ? i0 : a.N - 1;      // idle lanes recompute the last body, store nothing
-    const double dt = a.dt;
+    const double dt = predictor_dt(a);
+    if (a.ts.w && i0 == 0)                                // this step's words (other bank than prev)
+        for (int k = 0; k < a.ts.n_iter; ++k) a.ts.w[a.ts.bank * kTsMaxIter + k] = 0ull;
     double x[3], v[3], ad[p > 1 ? p - 1 : 1][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -141,7 +172,10 @@ __global__ void k_correct(StepArgs a)
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i0 < a.N;
     const int64_t i = live ? i0 : a.N - 1;      // idle lanes recompute the last body, store nothing
-    const double dt = a.dt;
+    const double dt = corrector_dt(a);
+    if (kLast && a.ts.t && i0 == 0) *a.ts.t += dt;    // the device clock (read and written by this thread only)
+    // time-symmetric steps, all passes but the last: shift of the end time for the next pass
+    const double shift = (!kLast && a.ts.w) ? timesym_dt(a, a.ts.pass) - dt : 0.0;
     double x[3], v[3], ad[p > 1 ? p - 1 : 1][3];
     bool finite = true;
 #pragma unroll
@@ -157,10 +191,28 @@ __global__ void k_correct(StepArgs a)
         for (int k = 0; k < K; ++k) d0[k] = a.d0[(3 * k + c) * a.ld + i];
         double xn, vn;
         correct_comp<p>(dt, a.beta_mode, d0, d1, a.x0[c * a.ld + i], a.v0[c * a.ld + i], xn, vn);
-        x[c] = xn;
-        v[c] = vn;
 #pragma unroll
         for (int q = 0; q + 2 <= p; ++q) ad[q][c] = d1[q];
+        if (!kLast && a.ts.w) {
+            // Taylor series of the end state over the change of dt, with a^(0..p) just evaluated
+            double sx = 0.0, sv = 0.0;
+#pragma unroll
+            for (int k = p; k >= 0; --k) {
+                sx = fma(sx, shift, d1[k] * inv_fact(k + 2));
+                sv = fma(sv, shift, d1[k] * inv_fact(k + 1));
+            }
+            xn = fma(fma(sx, shift, vn), shift, xn);
+            vn = fma(sv, shift, vn);
+#pragma unroll
+            for (int q = 0; q + 2 <= p; ++q) {
+                double sa = 0.0;
+#pragma unroll
+                for (int k = p; k >= q; --k) sa = fma(sa, shift, d1[k] * inv_fact(k - q));
+                ad[q][c] = sa;
+            }
+        }
+        x[c] = xn;
+        v[c] = vn;
         finite = finite && isfinite(xn) && isfinite(vn);
         if (!live) continue;
         if (kLast) {
@@ -563,6 +615,21 @@ __global__ void k_init_rows(int64_t N, int64_t ld, int have, const double *x0, c
     }
 }
 
+// Slot 0 of part <- the sum of slots 0 .. split-1, one thread per (row, body), in
+// the order the corrector adds them (so the corrector, given split = 1, gives
+// the same bits).  For small systems, whose many j-chunk slots would otherwise be
+// added serially by one thread per body.
+__global__ void k_reduce_slots(int64_t N, int64_t ld, int nr, int split, double *part)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)nr * N) return;
+    const int r = (int)(e / N);
+    const int64_t i = e - (int64_t)r * N;
+    double s = 0.0;
+    for (int q = 0; q < split; ++q) s += part[((int64_t)q * nr + r) * ld + i];
+    part[(int64_t)r * ld + i] = s;
+}
+
 // d0 rows [lo, hi) <- sum over S partial slots of rows [lo, hi) (slot row count nr).
 __global__ void k_init_reduce(int64_t N, int64_t ld, int nr, int lo, int hi, int split,
                               const double *part, double *d0)
@@ -635,7 +702,9 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 template <int p>
 int launch_step_kernels(const StepArgs &a, int phase, bool last, cudaStream_t st)
 {
-    const int T = 128;
+    // one warp per block for small systems: the FP64 work of a body then spreads
+    // over N/32 SMs instead of N/128 (two FP64 lanes per SM)
+    const int T = a.N < kSmallN ? 32 : 128;
     const unsigned g = blocks_for(a.N, T);
     if (phase == 0) {
         k_predict<p><<<g, T, 0, st>>>(a);
@@ -754,12 +823,13 @@ int launch_block_phase(const DeviceState &s, const mh_config &cfg, long long T_n
 
 // phase 0: predict; phase 1: correct (last = final pass of the step).
 int launch_step_phase(const DeviceState &s, const mh_config &cfg, double dt, int phase, bool last,
-                      int split, cudaStream_t st, unsigned long long *conv)
+                      int split, cudaStream_t st, unsigned long long *conv, const TimeSymArgs *ts)
 {
     StepArgs a{s.N, s.Np, dt, s.m, s.x0, s.v0, s.d0, s.x1, s.v1, s.jrec, s.jrec32, s.part,
                split, cfg.precision, cfg.beta_mode, s.flag,
                s.bound ? s.bound + 2 * s.flip : nullptr, s.bound ? s.bound + 2 * (1 - s.flip) : nullptr,
                conv};
+    if (ts) a.ts = *ts;
     switch (s.p) {
     case 1: return launch_step_kernels<1>(a, phase, last, st);
     case 2: return launch_step_kernels<2>(a, phase, last, st);
@@ -773,6 +843,14 @@ int launch_init_rows(const DeviceState &s, int have, cudaStream_t st)
 {
     k_init_rows<<<blocks_for(s.N, 128), 128, 0, st>>>(s.N, s.Np, have, s.x0, s.v0, s.d0, s.jrec);
     MH_LAUNCHED("k_init_rows");
+    return MH_OK;
+}
+
+int launch_reduce_slots(const DeviceState &s, int nr, int split, cudaStream_t st)
+{
+    const int64_t n = (int64_t)nr * s.N;
+    k_reduce_slots<<<blocks_for(n, 32), 32, 0, st>>>(s.N, s.Np, nr, split, s.part);
+    MH_LAUNCHED("k_reduce_slots");
     return MH_OK;
 }
 

@@ -50,12 +50,15 @@ struct PairArgs64 {
     int64_t n_itiles, chunk;
     int split, tj;
     const int *ilist;     // optional: body index of position i (active list); else i itself
+    unsigned long long *wmax;   // kH: max over pairs of G (m_i + m_j) s^(-3/2) (bit pattern), raised
 };
 
-template <int P, bool kGuard>
+// kH: also raise wm with w = G (m_i + m_j) s^(-3/2) of the pair (gmi = G m_i), whose
+// maximum over pairs gives the time-step criterion of Section 3.3 (Eq. 24).
+template <int P, bool kGuard, bool kH>
 __device__ __forceinline__ void interact64(const double *sh, int tj, int jj, bool self,
                                            const double (&ri)[P + 1][3], const PairArgs64<P> &a,
-                                           double (&acc)[P + 1][3])
+                                           double (&acc)[P + 1][3], double gmi, unsigned long long &wm)
 {
     constexpr int NF = 3 * (P + 1);
     double r[P + 1][3];
@@ -71,13 +74,20 @@ __device__ __forceinline__ void interact64(const double *sh, int tj, int jj, boo
     }
     const double rinv = rsqrt_fp64(s);
     const double sinv = rinv * rinv;
-    const double mS = a.G * mj * (rinv * sinv);
+    const double gmj = a.G * mj;
+    const double mS = gmj * (rinv * sinv);
+    if constexpr (kH) {
+        const unsigned long long wb =
+            (kGuard && self) ? 0ull : (unsigned long long)__double_as_longlong((gmi + gmj) * (rinv * sinv));
+        wm = wb > wm ? wb : wm;
+    }
     pair_derivs<P, double>(r, mS, sinv, acc);
 }
 
-template <int P>
+template <int P, bool kH>
 __global__ void __launch_bounds__(128) k_pair_fp64(PairArgs64<P> a)
 {
+    unsigned long long wm = 0ull;
     constexpr int NF = 3 * (P + 1);
     extern __shared__ double sh[];      // [NF + 1][tj]
     const int tj = a.tj;
@@ -94,6 +104,8 @@ __global__ void __launch_bounds__(128) k_pair_fp64(PairArgs64<P> a)
         for (int k = 0; k <= P; ++k)
 #pragma unroll
             for (int c = 0; c < 3; ++c) ri[k][c] = a.jrec[(3 * k + c) * a.ld + ic];
+        const double gmi = kH ? a.G * a.m[ic] : 0.0;
+        unsigned long long wm_item = 0ull;   // this item's pairs; kept only for a live position
         double acc[P + 1][3];
 #pragma unroll
         for (int k = 0; k <= P; ++k)
@@ -116,11 +128,16 @@ __global__ void __launch_bounds__(128) k_pair_fp64(PairArgs64<P> a)
             // (with an index list any tile may hold it)
             const int64_t ib = a.i0 + itile * blockDim.x;
             if (a.ilist || (j0 < ib + (int64_t)blockDim.x && ib < j0 + tj)) {
-                for (int jj = 0; jj < tj; ++jj) interact64<P, true>(sh, tj, jj, j0 + jj == ic, ri, a, acc);
+                for (int jj = 0; jj < tj; ++jj)
+                    interact64<P, true, kH>(sh, tj, jj, j0 + jj == ic, ri, a, acc, gmi, wm_item);
             } else {
-                for (int jj = 0; jj < tj; ++jj) interact64<P, false>(sh, tj, jj, false, ri, a, acc);
+                for (int jj = 0; jj < tj; ++jj)
+                    interact64<P, false, kH>(sh, tj, jj, false, ri, a, acc, gmi, wm_item);
             }
         }
+        // an idle position evaluates body i0 with the guard of its own tile only, so its
+        // pairs (possibly i0 with itself) must not enter the maximum
+        if (kH && live) wm = wm_item > wm ? wm_item : wm;
         if (live) {
             double *out = a.part + (int64_t)jc * (P + 1) * 3 * a.part_ld + (i - a.i0);
 #pragma unroll
@@ -128,6 +145,14 @@ __global__ void __launch_bounds__(128) k_pair_fp64(PairArgs64<P> a)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) out[(3 * k + c) * a.part_ld] = acc[k][c];
         }
+    }
+    if constexpr (kH) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long q = __shfl_xor_sync(0xffffffffu, wm, o);
+            wm = q > wm ? q : wm;
+        }
+        if ((threadIdx.x & 31) == 0 && wm) atomicMax(a.wmax, wm);
     }
 }
 
@@ -517,12 +542,15 @@ __global__ void k_pair_heavy(int64_t N, int64_t ld, const double *__restrict__ m
 template <int P>
 int launch_fp64(const double *jrec, const double *m, int64_t ld, int64_t n_j, double eps,
                 double G, int64_t i0, int64_t i1, double *part, int64_t part_ld,
-                const PairPlan &pl, const int *ilist, cudaStream_t st)
+                const PairPlan &pl, const int *ilist, cudaStream_t st, unsigned long long *wmax)
 {
     PairArgs64<P> a{jrec, m, ld, n_j, i0, i1, eps * eps, G, part, part_ld,
-                    pl.n_itiles, pl.chunk, pl.split, pl.tj, ilist};
+                    pl.n_itiles, pl.chunk, pl.split, pl.tj, ilist, wmax};
     const size_t smem = sizeof(double) * (3 * (P + 1) + 1) * pl.tj;
-    k_pair_fp64<P><<<pl.grid, pl.threads, smem, st>>>(a);
+    if (wmax)
+        k_pair_fp64<P, true><<<pl.grid, pl.threads, smem, st>>>(a);
+    else
+        k_pair_fp64<P, false><<<pl.grid, pl.threads, smem, st>>>(a);
     MH_LAUNCHED("k_pair_fp64");
     return MH_OK;
 }
@@ -588,6 +616,38 @@ int launch_pair_heavy(int P, int64_t N, int64_t ld, const double *m, const doubl
     return MH_OK;
 }
 
+// FP64 plan for evaluations too small to fill the GPU with 128-body i-tiles
+// (few bodies, or a short active list): one warp per CTA, 32-body i-tiles and
+// j-tiles as short as 2, so that the pairs spread over every SM (GB300 has two
+// FP64 lanes per SM, so an SM left idle is a large loss).
+static PairPlan plan_fine64(int64_t n_i, int64_t n_j, int split_hint, int n_sm)
+{
+    PairPlan pl{};
+    pl.threads = 32;
+    pl.i_per_cta = 32;
+    pl.n_itiles = (n_i + 31) / 32;
+    const int slots = n_sm * 16;                          // resident one-warp CTAs per device
+    pl.tj = 64;
+    while (pl.tj > 2 && pl.n_itiles * std::min<int64_t>(64, (n_j + pl.tj - 1) / pl.tj) < 4 * (int64_t)n_sm)
+        pl.tj /= 2;
+    const int64_t n_jt = (n_j + pl.tj - 1) / pl.tj;
+    int best_S = 1;
+    double best_cost = 1e300;
+    const int s_max = (int)std::min<int64_t>(64, n_jt);
+    for (int S = 1; S <= s_max; ++S) {
+        if (split_hint > 0 && S != std::min(split_hint, s_max)) continue;
+        const int64_t tiles_per_chunk = (n_jt + S - 1) / S;
+        if ((n_jt + tiles_per_chunk - 1) / tiles_per_chunk != S) continue;
+        const int64_t waves = (pl.n_itiles * S + slots - 1) / slots;
+        const double cost = (double)waves * tiles_per_chunk * (1.0 + 0.002 * S);
+        if (cost < best_cost) { best_cost = cost; best_S = S; }
+    }
+    pl.split = best_S;
+    pl.chunk = (n_jt + best_S - 1) / best_S * pl.tj;
+    pl.grid = (int)std::min<int64_t>(pl.n_itiles * pl.split, slots);
+    return pl;
+}
+
 PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hint, int device, int variant)
 {
     const int ipt = variant;
@@ -627,20 +687,26 @@ PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hin
     pl.chunk = tiles_per_chunk * pl.tj;
     const int64_t items = pl.n_itiles * pl.split;
     pl.grid = (int)std::min<int64_t>(items, slots);
+    if (precision == MH_PREC_FP64 && items < 2 * (int64_t)n_sm) return plan_fine64(n_i, n_j, split_hint, n_sm);
     return pl;
 }
 
 int launch_pair(int P, int precision, int64_t n_j, int64_t ld, const double *m, const double *jrec,
                 const float *jrec32, double eps, double G, int64_t i0, int64_t i1, double *part,
-                int64_t part_ld, const PairPlan &pl, cudaStream_t st, const int *ilist)
+                int64_t part_ld, const PairPlan &pl, cudaStream_t st, const int *ilist,
+                unsigned long long *wmax)
 {
     if (precision == MH_PREC_FP64) {
+        if (wmax && P > 3) {
+            set_error("launch_pair: the Eq. 24 maximum is tracked for P <= 3 only");
+            return MH_EINVAL;
+        }
         switch (P) {
-        case 1: return launch_fp64<1>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st);
-        case 2: return launch_fp64<2>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st);
-        case 3: return launch_fp64<3>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st);
-        case 4: return launch_fp64<4>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st);
-        case 5: return launch_fp64<5>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st);
+        case 1: return launch_fp64<1>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st, wmax);
+        case 2: return launch_fp64<2>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st, wmax);
+        case 3: return launch_fp64<3>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st, wmax);
+        case 4: return launch_fp64<4>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st, nullptr);
+        case 5: return launch_fp64<5>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st, nullptr);
         }
     } else {
         switch (P) {

@@ -53,6 +53,7 @@ struct SymArgs {
     int nB, D, C, Bc;     // blocks, distances, row chunks, blocks per chunk
     double eps2, G;
     double *part;         // [C + D][(P+1)*3][ld]
+    unsigned long long *wmax;   // kH: max over pairs of G (m_i + m_j) s^(-3/2) (bit pattern), raised
 };
 
 // Record of body b.  Padding bodies get mass 0 and distinct far-away positions,
@@ -86,10 +87,16 @@ __device__ __forceinline__ void rotate(double (&r)[P + 1][3], double &gm, int sr
     gm = __shfl_sync(0xffffffffu, gm, src);
 }
 
-template <int P>
+// kH: also track w = G (m_i + m_j) s^(-3/2) over all pairs i != j, whose maximum
+// gives the time-step criterion of Section 3.3 (Eq. 24: H = eta w_max^(-1/2)).
+// Non-negative doubles order as their bit patterns, so the maximum is an
+// integer maximum (off the FP64 pipe) and the result does not depend on the
+// order of the pairs.
+template <int P, bool kH>
 __global__ void __launch_bounds__(kSymR, 2) k_pair_fp64_sym(SymArgs<P> a)
 {
     constexpr int NR = 3 * (P + 1);
+    unsigned long long wm = 0ull;
     __shared__ double accs[NR][kSymR];    // j-side sums of the current block, by column
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
@@ -129,7 +136,12 @@ __global__ void __launch_bounds__(kSymR, 2) k_pair_fp64_sym(SymArgs<P> a)
                         const double wi = self ? 0.0 : gmj;
                         const double rinv = rsqrt_fp64(s);
                         const double sinv = rinv * rinv;
-                        const double mS = wi * (rinv * sinv);
+                        const double S = rinv * sinv;
+                        const double mS = wi * S;
+                        if constexpr (kH) {
+                            const unsigned long long wb = self ? 0ull : (unsigned long long)__double_as_longlong((gmi + gmj) * S);
+                            wm = wb > wm ? wb : wm;
+                        }
                         pair_abg_terms<P, double>(r, sinv, [&](int k, int c, double B) {
                             acci[k][c] = fma(mS, B, acci[k][c]);
                         });
@@ -158,6 +170,10 @@ __global__ void __launch_bounds__(kSymR, 2) k_pair_fp64_sym(SymArgs<P> a)
                     const double sinv = rinv * rinv;
                     const double S = rinv * sinv;
                     const double wi = gmj * S, wj = gmi * S;
+                    if constexpr (kH) {
+                        const unsigned long long wb = (unsigned long long)__double_as_longlong(wi + wj);
+                        wm = wb > wm ? wb : wm;
+                    }
                     pair_abg_terms<P, double>(r, sinv, [&](int k, int c, double B) {
                         acci[k][c] = fma(wi, B, acci[k][c]);
                         accj[k][c] = fma(-wj, B, accj[k][c]);
@@ -192,14 +208,25 @@ __global__ void __launch_bounds__(kSymR, 2) k_pair_fp64_sym(SymArgs<P> a)
 #pragma unroll
             for (int c = 0; c < 3; ++c) out[(3 * k + c) * a.ld] = acci[k][c];
     }
+    if constexpr (kH) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long q = __shfl_xor_sync(0xffffffffu, wm, o);
+            wm = q > wm ? q : wm;
+        }
+        if (lane == 0 && wm) atomicMax(a.wmax, wm);
+    }
 }
 
 template <int P>
 int launch_sym(const SymPlan &pl, const double *jrec, const double *m, int64_t ld, int64_t N, double eps,
-               double G, double *part, cudaStream_t st)
+               double G, double *part, unsigned long long *wmax, cudaStream_t st)
 {
-    SymArgs<P> a{jrec, m, ld, N, pl.nB, pl.D, pl.C, pl.Bc, eps * eps, G, part};
-    k_pair_fp64_sym<P><<<pl.grid, kSymR, 0, st>>>(a);
+    SymArgs<P> a{jrec, m, ld, N, pl.nB, pl.D, pl.C, pl.Bc, eps * eps, G, part, wmax};
+    if (wmax)
+        k_pair_fp64_sym<P, true><<<pl.grid, kSymR, 0, st>>>(a);
+    else
+        k_pair_fp64_sym<P, false><<<pl.grid, kSymR, 0, st>>>(a);
     MH_LAUNCHED("k_pair_fp64_sym");
     return MH_OK;
 }
@@ -216,8 +243,8 @@ SymPlan plan_sym(int P, int64_t ld, int device)
     if (slots == 0) {
         int n_sm = 0, occ = 0;
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
-        const void *fn = P == 1 ? (const void *)k_pair_fp64_sym<1>
-                       : P == 2 ? (const void *)k_pair_fp64_sym<2> : (const void *)k_pair_fp64_sym<3>;
+        const void *fn = P == 1 ? (const void *)k_pair_fp64_sym<1, false>
+                       : P == 2 ? (const void *)k_pair_fp64_sym<2, false> : (const void *)k_pair_fp64_sym<3, false>;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kSymR, 0);
         slots = std::max(n_sm, 1) * std::max(occ, 1);
         if (device >= 0 && device < 64) slot_cache[device][P] = slots;
@@ -246,12 +273,12 @@ SymPlan plan_sym(int P, int64_t ld, int device)
 }
 
 int launch_pair_sym(int P, const SymPlan &pl, const double *jrec, const double *m, int64_t ld, int64_t N,
-                    double eps, double G, double *part, cudaStream_t st)
+                    double eps, double G, double *part, cudaStream_t st, unsigned long long *wmax)
 {
     switch (P) {
-    case 1: return launch_sym<1>(pl, jrec, m, ld, N, eps, G, part, st);
-    case 2: return launch_sym<2>(pl, jrec, m, ld, N, eps, G, part, st);
-    case 3: return launch_sym<3>(pl, jrec, m, ld, N, eps, G, part, st);
+    case 1: return launch_sym<1>(pl, jrec, m, ld, N, eps, G, part, wmax, st);
+    case 2: return launch_sym<2>(pl, jrec, m, ld, N, eps, G, part, wmax, st);
+    case 3: return launch_sym<3>(pl, jrec, m, ld, N, eps, G, part, wmax, st);
     }
     set_error("launch_pair_sym: P must be 1..3");
     return MH_EINVAL;

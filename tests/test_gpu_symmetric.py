@@ -1,8 +1,8 @@
 """GPU parity of the pair-symmetric FP64 evaluation (each unordered pair once,
 its odd terms added to both bodies).
 
-The symmetric kernel runs in every FP64 shared-step simulation by default; here
-it is checked against the CPU oracle at sizes that cover every branch of its
+The symmetric kernel runs in FP64 simulations of 2048 or more padded bodies by
+default (symmetric = 2 forces it at any size); here it is checked against the CPU oracle at sizes that cover every branch of its
 block schedule (one block, odd and even block counts, ragged padding, eps = 0
 with its guarded diagonal) and against the ordered-pair kernel at the full
 SMBH-disc size.  Tolerance: 1e-12 relative, as for the plain FP64 form.
@@ -34,7 +34,7 @@ def mh():
 def test_symmetric_initialisation_parity(mh, orc, N, order):
     m, x, v = I.smbh_disc(seed=20 + N, N=max(N - 1, 1))
     m, x, v = m[:N], x[:N], v[:N]
-    with mh.Simulation(order, m, x, v, 1e-4) as sim:
+    with mh.Simulation(order, m, x, v, 1e-4, symmetric=2) as sim:
         _, _, _, dg = sim.sync()
     ref = orc.initialise(order, m, x, v, 1e-4)
     if N == 1:
@@ -46,7 +46,7 @@ def test_symmetric_initialisation_parity(mh, orc, N, order):
 def test_symmetric_unsoftened(mh, orc):
     """eps = 0: the diagonal block skips i = j instead of evaluating r = 0."""
     m, x, v = I.planetesimal_ring(seed=1)
-    with mh.Simulation(8, m, x, v, 0.0) as sim:
+    with mh.Simulation(8, m, x, v, 0.0, symmetric=2) as sim:
         _, _, _, dg = sim.sync()
     assert np.all(np.isfinite(dg))
     assert scaled_stack_err(dg, orc.initialise(8, m, x, v, 0.0), 0.05) < 1e-12
@@ -57,7 +57,7 @@ def test_symmetric_unsoftened(mh, orc):
 def test_symmetric_step_parity(mh, orc, N, order):
     m, x, v = I.planetesimal_ring(seed=N, n=N, m=1e-6, a_lo=0.5, a_hi=1.5, sigma_e=0.1, sigma_i=0.05)
     dt, eps = 0.08, 1e-3
-    with mh.Simulation(order, m, x, v, eps) as sim:
+    with mh.Simulation(order, m, x, v, eps, symmetric=2) as sim:
         sim.step(dt, 3)
         _, xg, vg, dg = sim.sync()
     ref = orc.State(order, m, x, v, eps)
