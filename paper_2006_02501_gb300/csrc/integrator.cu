@@ -181,11 +181,17 @@ __global__ void k_correct(StepArgs a)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         double d1[p + 1], d0[K];
+        if (a.split == 1) {
+            // one slot (small systems pre-add theirs): straight-line loads that overlap
 #pragma unroll
-        for (int k = 0; k <= p; ++k) {
-            double s = 0.0;
-            for (int q = 0; q < a.split; ++q) s += a.part[((int64_t)q * NR + 3 * k + c) * a.ld + i];
-            d1[k] = s;
+            for (int k = 0; k <= p; ++k) d1[k] = 0.0 + a.part[(int64_t)(3 * k + c) * a.ld + i];
+        } else {
+#pragma unroll
+            for (int k = 0; k <= p; ++k) {
+                double s = 0.0;
+                for (int q = 0; q < a.split; ++q) s += a.part[((int64_t)q * NR + 3 * k + c) * a.ld + i];
+                d1[k] = s;
+            }
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) d0[k] = a.d0[(3 * k + c) * a.ld + i];
@@ -625,8 +631,16 @@ __global__ void k_reduce_slots(int64_t N, int64_t ld, int nr, int split, double 
     if (e >= (int64_t)nr * N) return;
     const int r = (int)(e / N);
     const int64_t i = e - (int64_t)r * N;
+    // loads issued in independent batches of 8 (a latency-bound kernel), added in slot order
     double s = 0.0;
-    for (int q = 0; q < split; ++q) s += part[((int64_t)q * nr + r) * ld + i];
+    for (int q0 = 0; q0 < split; q0 += 8) {
+        double b[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) b[u] = q0 + u < split ? part[((int64_t)(q0 + u) * nr + r) * ld + i] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (q0 + u < split) s += b[u];
+    }
     part[(int64_t)r * ld + i] = s;
 }
 
