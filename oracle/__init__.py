@@ -88,9 +88,10 @@ def _f64(a) -> np.ndarray:
 
 
 def order_to_p(order: int) -> int:
-    """Order 2(p+1) -> p (Section 2: p derivatives of a give order 2(p+1))."""
-    if order not in (4, 6, 8):
-        raise ValueError("order must be 4, 6 or 8")
+    """Order 2(p+1) -> p (Section 2: p derivatives of a give order 2(p+1)); the
+    paper's schemes are of arbitrary order, the oracle takes 4 .. 12."""
+    if order not in (4, 6, 8, 10, 12):
+        raise ValueError("order must be 4, 6, 8, 10 or 12")
     return order // 2 - 1
 
 

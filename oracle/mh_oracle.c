@@ -42,7 +42,7 @@
 #include <string.h>
 #include <limits.h>
 
-#define ORC_MAXP 5           /* highest acceleration derivative supported in a pair */
+#define ORC_MAXP 9           /* highest acceleration derivative supported in a pair (a^(9): 12th-order initialisation) */
 #define ORC_MAXSYS 8         /* largest Pascal sub-system (p+2 for p <= 6) */
 
 /* ------------------------------------------------------------------------- */

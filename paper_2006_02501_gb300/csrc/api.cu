@@ -32,7 +32,12 @@ int cuda_fail(cudaError_t e, const char *what)
 
 namespace {
 
-int order_to_p(int order) { return order == 4 ? 1 : order == 6 ? 2 : order == 8 ? 3 : 0; }
+// Order 2(p+1) -> p.  The paper's schemes are of arbitrary order (Section 2);
+// the library builds orders 4 to 12.
+int order_to_p(int order)
+{
+    return order == 4 ? 1 : order == 6 ? 2 : order == 8 ? 3 : order == 10 ? 4 : order == 12 ? 5 : 0;
+}
 
 template <typename T>
 int dalloc(T **ptr, size_t count)
@@ -172,8 +177,8 @@ int tuned_variant(mh_sim *sim, int P, int64_t n_i, const int *ilist, int *varian
 int evaluate(mh_sim *sim, int P, int precision, int *split, unsigned long long *wslot = nullptr)
 {
     DeviceState &s = sim->s;
-    if (wslot && (precision != MH_PREC_FP64 || P > 3)) {
-        set_error("evaluate: the Eq. 24 maximum is tracked by the FP64 kernels for P <= 3 only");
+    if (wslot && (precision != MH_PREC_FP64 || P > 5)) {
+        set_error("evaluate: the Eq. 24 maximum is tracked by the FP64 kernels for P <= 5 only");
         return MH_EINVAL;
     }
     // pair-symmetric kernel: always (symmetric = 2), or (symmetric = 1) once there
@@ -358,7 +363,11 @@ int mh::create_shell(mh_sim **out, int64_t N, int order, const double *m, const 
     if (cfg) c = *cfg; else mh_config_default(&c);
     c.order = order;
     const int p = order_to_p(order);
-    if (p == 0) { set_error("mh_create: order must be 4, 6 or 8"); return MH_EINVAL; }
+    if (p == 0) { set_error("mh_create: order must be 4, 6, 8, 10 or 12"); return MH_EINVAL; }
+    if (p > 3 && c.precision != MH_PREC_FP64) {
+        set_error("mh_create: the FP32-pair form is built for orders 4 to 8");
+        return MH_EINVAL;
+    }
     if (N < 1 || !m || !x || !v) { set_error("mh_create: N >= 1 and non-NULL m, x, v required"); return MH_EINVAL; }
     if (!(eps >= 0.0) || !std::isfinite(eps)) { set_error("mh_create: eps must be finite and >= 0"); return MH_EINVAL; }
     if (c.precision != MH_PREC_FP64 && c.precision != MH_PREC_FP32PAIR) { set_error("mh_create: bad precision"); return MH_EINVAL; }
@@ -375,7 +384,7 @@ int mh::create_shell(mh_sim **out, int64_t N, int order, const double *m, const 
     if (c.symmetric < 0 || c.symmetric > 2) { set_error("mh_create: symmetric must be 0, 1 or 2"); return MH_EINVAL; }
     if (c.fp32_variant < 0 || c.fp32_variant > 3) { set_error("mh_create: fp32_variant must be 0..3"); return MH_EINVAL; }
     if (c.step_mode == MH_STEP_BLOCK) {
-        if (p < 2) { set_error("mh_create: block steps need order 6 or 8"); return MH_EINVAL; }
+        if (p < 2 || p > 3) { set_error("mh_create: block steps need order 6 or 8"); return MH_EINVAL; }
         if (!(c.dt_max > 0.0) || !std::isfinite(c.dt_max) || c.k_max < 0 || c.k_max > 30 || !(c.eta > 0.0)) {
             set_error("mh_create: block steps need dt_max > 0, 0 <= k_max <= 30, eta > 0");
             return MH_EINVAL;
@@ -790,6 +799,10 @@ int mh_set_predictor(mh_sim *sim, mh_mlp *net)
         return MH_EINVAL;
     }
     if (net) {
+        if (sim->s.p > 3) {
+            set_error("mh_set_predictor: the learned residual is built for orders 4 to 8");
+            return MH_EINVAL;
+        }
         int n_in = 0, n_out = 0;
         mlp_dims(net, &n_in, &n_out);
         if (n_in != 6 * sim->s.p + 1 || n_out != 6) {
@@ -836,8 +849,8 @@ int mh_collect_samples(mh_sim *sim, double dt, int n_iter, float *feats, float *
         set_error("mh_collect_samples: device feats/targets, dt != 0, 1 <= n_iter <= 64");
         return MH_EINVAL;
     }
-    if (sim->batch || sim->cfg.step_mode != MH_STEP_SHARED) {
-        set_error("mh_collect_samples: shared-step simulations only");
+    if (sim->batch || sim->cfg.step_mode != MH_STEP_SHARED || sim->s.p > 3) {
+        set_error("mh_collect_samples: shared-step simulations of order 4 to 8 only");
         return MH_EINVAL;
     }
     DeviceState &s = sim->s;

@@ -6,10 +6,13 @@ Method (independent of the quadrature-on-F+- route of Section 2): build the
 two-point Hermite interpolant of f on [t0, t1 = t0 + dt] in the monomial basis
 centred on t1, matching f^(0..q) at both ends, then
   - integrate it over the step (velocity corrector for f = a, q = p; the
-    standard beta = 1 position corrector for f = v, q = p + 1), and
-  - differentiate it at t1 (a^(p+1) .. a^(2p-1) for the next predictor).
-The modified position correctors are the ones printed in Section 2.1
-(Eqs. 21, 22, 23) and are not derived here.
+    standard beta = 1 position corrector for f = v, q = p + 1),
+  - differentiate it at t1 (a^(p+1) .. a^(2p-1) for the next predictor), and
+  - for the modified position corrector (Eq. 7, beta of Eq. 20): add
+    (beta - 1)/(2p + 3) F_(2p+2) dt, where F_(2p+2) = h^(2p+2) v^(2p+2)(mid)/(2p+2)!
+    is the interpolant's scaled derivative at the midpoint (h = dt/2).  For
+    orders 4, 6, 8 this reproduces the correctors printed in Section 2.1
+    (Eqs. 21, 22, 23), checked below; orders 10 and 12 come from the same formula.
 """
 import sympy as sp
 
@@ -46,7 +49,46 @@ def end_derivs(q, orders):
     return out
 
 
+def beta(p):
+    """Eq. 20: beta = 1 + (-1)^(p+1) (2p+2)!! / (2p+1)!!."""
+    return 1 + (-1) ** (p + 1) * sp.factorial2(2 * p + 2) / sp.factorial2(2 * p + 1)
+
+
+def modified_position_coeffs(p):
+    """Coefficients of (v1^(k) +- v0^(k)) dt^(k+1), k = 0 .. p+1, of the modified
+    position corrector (Eq. 7 with beta of Eq. 20)."""
+    q = p + 1
+    poly, tau, dt, f0, f1 = interpolant(q)
+    h = dt / 2
+    n = 2 * p + 2
+    Fn = sp.expand(h ** n * sp.diff(poly, tau, n).subs(tau, -h) / sp.factorial(n))
+    extra = sp.expand((beta(p) - 1) / (2 * p + 3) * Fn * dt)
+    I = sp.expand(sp.integrate(poly, (tau, -dt, 0))) + extra
+    return [sp.simplify(I.coeff(f1[k]) / dt ** (k + 1)) for k in range(q + 1)], \
+           [sp.simplify(I.coeff(f0[k]) / dt ** (k + 1)) for k in range(q + 1)]
+
+
+PRINTED = {   # Section 2.1: Eq. 21 (p = 1), Eq. 22 (p = 2), Eq. 23 (p = 3), on (v1^(k) +- v0^(k)) dt^(k+1)
+    1: [sp.Rational(1, 2), sp.Rational(-7, 60), sp.Rational(1, 60)],
+    2: [sp.Rational(1, 2), sp.Rational(-4, 35), sp.Rational(13, 840), sp.Rational(-1, 840)],
+    3: [sp.Rational(1, 2), sp.Rational(-29, 252), sp.Rational(1, 63), sp.Rational(-1, 720), sp.Rational(1, 15120)],
+}
+
+
 if __name__ == "__main__":
+    for p in (1, 2, 3):
+        c1, c0 = modified_position_coeffs(p)
+        assert c1 == PRINTED[p], (p, c1)
+        assert all(c0[k] == (-1) ** k * c1[k] for k in range(len(c1))), (p, c0)
+    print("modified position correctors of Eqs. 21-23 reproduced")
+    for p in (4, 5):
+        print(f"p={p} beta = {beta(p)}")
+        print(f"p={p} velocity:", integral_coeffs(p)[0])
+        print(f"p={p} modified position:", modified_position_coeffs(p)[0])
+        print(f"p={p} standard position:", integral_coeffs(p + 1)[0])
+        d = end_derivs(p, range(p + 1, 2 * p))
+        for n in range(p + 1, 2 * p):
+            print(f"p={p} end derivative n={n}: e1 = {d[n][0]}  e0 = {d[n][1]}")
     for p in (1, 2, 3):
         print(f"p={p} velocity (a1^(k), a0^(k)) x dt^(k+1):", integral_coeffs(p))
         print(f"p={p} standard position (v1^(k), v0^(k)) x dt^(k+1):", integral_coeffs(p + 1))

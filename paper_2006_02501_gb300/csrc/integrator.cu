@@ -848,6 +848,8 @@ int launch_step_phase(const DeviceState &s, const mh_config &cfg, double dt, int
     case 1: return launch_step_kernels<1>(a, phase, last, st);
     case 2: return launch_step_kernels<2>(a, phase, last, st);
     case 3: return launch_step_kernels<3>(a, phase, last, st);
+    case 4: return launch_step_kernels<4>(a, phase, last, st);
+    case 5: return launch_step_kernels<5>(a, phase, last, st);
     }
     set_error("unsupported p");
     return MH_EINVAL;

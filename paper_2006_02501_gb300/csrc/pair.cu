@@ -697,16 +697,19 @@ int launch_pair(int P, int precision, int64_t n_j, int64_t ld, const double *m, 
                 unsigned long long *wmax)
 {
     if (precision == MH_PREC_FP64) {
-        if (wmax && P > 3) {
-            set_error("launch_pair: the Eq. 24 maximum is tracked for P <= 3 only");
+        if (wmax && P > 5) {
+            set_error("launch_pair: the Eq. 24 maximum is tracked for P <= 5 only");
             return MH_EINVAL;
         }
         switch (P) {
         case 1: return launch_fp64<1>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st, wmax);
         case 2: return launch_fp64<2>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st, wmax);
         case 3: return launch_fp64<3>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st, wmax);
-        case 4: return launch_fp64<4>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st, nullptr);
-        case 5: return launch_fp64<5>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st, nullptr);
+        // P = 4, 5: the 10th- and 12th-order steps; P = 5, 7, 9: initialisation passes
+        case 4: return launch_fp64<4>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st, wmax);
+        case 5: return launch_fp64<5>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st, wmax);
+        case 7: return launch_fp64<7>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st, nullptr);
+        case 9: return launch_fp64<9>(jrec, m, ld, n_j, eps, G, i0, i1, part, part_ld, pl, ilist, st, nullptr);
         }
     } else {
         switch (P) {

@@ -33,11 +33,12 @@ def _kepler(orc, order, e, dt, nsteps, n_iter, modified=True, m=1e-3, eps=0.0):
 
 
 @pytest.mark.parametrize("order,e,ks", [(4, 0.5, (128, 256)), (6, 0.5, (128, 256)),
-                                        (8, 0.5, (64, 128)), (6, 0.1, (64, 128))])
+                                        (8, 0.5, (64, 128)), (6, 0.1, (64, 128)),
+                                        (10, 0.5, (48, 96)), (12, 0.5, (32, 64))])
 def test_measured_convergence_order(orc, order, e, ks):
     errs = [_kepler(orc, order, e, 2 * np.pi / k, k, 6)[0] for k in ks]
     slope = np.log2(errs[0] / errs[1])
-    assert abs(slope - order) < 0.35, (errs, slope)
+    assert abs(slope - order) < (0.35 if order <= 8 else 0.6), (errs, slope)
 
 
 @pytest.mark.parametrize("order,tol", [(4, 2e-4), (6, 1e-7), (8, 1e-10)])
@@ -66,14 +67,13 @@ def test_time_symmetry_forward_backward(orc, order):
     assert np.abs(T.x - x0).max() > 100 * max(np.abs(S.x - x0).max(), 1e-15)
 
 
-def _omega_run(orc, order, modified, eps):
+def _omega_run(orc, order, modified, eps, dt=2.0 ** -4, e=0.1):
     """Section 3.1 setup: m = 1e-3 about M = 1, a = 1, e = 0.1, dt = 2^-4, n = 3,
     t = 100 pi.  Returns (fitted secular slope of the longitude of periapsis,
     max |dE/E0|)."""
-    mm, x, v = I.kepler_pair(a=1.0, e=0.1, M=1.0, m=1e-3)
+    mm, x, v = I.kepler_pair(a=1.0, e=e, M=1.0, m=1e-3)
     S = orc.State(order, mm, x, v, eps, modified=modified)
     E0 = S.energy()
-    dt = 2.0 ** -4
     nst = int(100 * np.pi / dt)
     ts, om, dE = [], [], []
     for _ in range(50):
@@ -90,6 +90,16 @@ def test_modified_corrector_removes_periapsis_drift(orc, order, eps):
     s_mod, _ = _omega_run(orc, order, True, eps)
     s_std, _ = _omega_run(orc, order, False, eps)
     assert abs(s_mod) < 0.1 * abs(s_std), (s_mod, s_std)
+
+
+@pytest.mark.parametrize("order,dt,e", [(10, 0.35, 0.1), (12, 0.25, 0.3)])
+def test_modified_corrector_orders_10_12(orc, order, dt, e):
+    """The beta of Eq. 20 holds for any p: at orders 10 and 12 (correctors not
+    printed in the paper) the modified scheme still cuts the secular drift of
+    the periapsis, at steps where the leading truncation term dominates."""
+    s_mod, _ = _omega_run(orc, order, True, 0.0, dt, e)
+    s_std, _ = _omega_run(orc, order, False, 0.0, dt, e)
+    assert abs(s_mod) < 0.2 * abs(s_std), (s_mod, s_std)
 
 
 def test_energy_error_drops_with_order(orc):
