@@ -2,8 +2,9 @@
  * mh.h - C ABI of the GB300 (sm_103a) modified Hermite N-body library.
  *
  * The library integrates the Newtonian N-body problem with the modified
- * Hermite integrators of order 4, 6 and 8 of Dittmann (2020), "Modified Hermite
- * Integrators of Arbitrary Order", MNRAS:
+ * Hermite integrators of Dittmann (2020), "Modified Hermite Integrators of
+ * Arbitrary Order", MNRAS, of order 4, 6, 8 (correctors printed in Section 2.1)
+ * and 10, 12 (the same construction, Eq. 7 with beta of Eq. 20):
  *   - softened pair acceleration a_ij = G m_j r_ij (r_ij^2 + eps^2)^(-3/2) and
  *     its time derivatives (Section 3, intro), summed over all j != i;
  *   - explicit initial derivatives a^(0) .. a^(2p-1) (Section 3, intro);
@@ -13,7 +14,10 @@
  *   - P(EC)^n iteration (Section 2.1, end);
  *   - energy and Laplace-Runge-Lenz (eccentricity) vectors (Appendix A, Eq. A1).
  * The integrator order is 2(p+1) where p is the number of acceleration
- * derivatives evaluated (Section 2): order 4, 6, 8 <-> p = 1, 2, 3.
+ * derivatives evaluated (Section 2): order 4, 6, 8, 10, 12 <-> p = 1 .. 5.
+ * Orders 10 and 12 run in the FP64 form with shared or time-symmetric steps;
+ * the FP32-pair form, block steps, the learned residual and the batched form
+ * are built for orders 4 to 8.
  *
  * Conventions shared by every entry point
  *   - Return value: an mh_status; 0 is success, negative values are errors.
@@ -57,7 +61,7 @@ enum { MH_STEP_SHARED = 0, MH_STEP_BLOCK = 1, MH_STEP_TIMESYM = 2 };
 
 /* Integrator configuration.  Fill with mh_config_default() first. */
 typedef struct {
-    int order;          /* 4, 6 or 8 (default 8) */
+    int order;          /* 4, 6, 8, 10 or 12 (default 8) */
     int beta_mode;      /* MH_BETA_MODIFIED: beta of Eq. 20; MH_BETA_STANDARD: beta = 1 */
     int precision;      /* MH_PREC_FP64: all arithmetic FP64.
                            MH_PREC_FP32PAIR: pair arithmetic in FP32, state, pre-cast
