@@ -60,6 +60,7 @@ def _lib_handle():
             lib.orc_correct.argtypes = [i, i, i, d, _D, _D, _D, _D, _D, _D]
             lib.orc_step.argtypes = [i, i, i, i, d, _D, d, d, _D, _D, _D]
             lib.orc_run.argtypes = [i, i, i, i, d, i, _D, d, d, _D, _D, _D]
+            lib.orc_run_comp.argtypes = [i, i, i, i, d, i, _D, d, d, _D, _D, _D, _D]
             lib.orc_energy.argtypes = [i, _D, _D, _D, d, d]
             lib.orc_energy.restype = d
             lib.orc_ecc.argtypes = [i, _D, _D, _D, d, i, _D]
@@ -195,11 +196,20 @@ class State:
     def N(self) -> int:
         return self.m.shape[0]
 
-    def step(self, dt: float, n_iter: int, nsteps: int = 1) -> None:
-        """nsteps shared P(EC)^n steps of constant dt (negative dt runs backward)."""
-        _lib_handle().orc_run(self.N, self.p, 0 if self.modified else 1, n_iter, dt, nsteps,
-                              _p(self.m), self.eps, self.G, _p(self.x), _p(self.v),
-                              _p(self.derivs))
+    def step(self, dt: float, n_iter: int, nsteps: int = 1, compensated: bool = False) -> None:
+        """nsteps shared P(EC)^n steps of constant dt (negative dt runs backward).
+        compensated: Kahan-compensated summation of the x, v updates (Section
+        3.2); the compensation is carried in self.comp between calls."""
+        if compensated:
+            if getattr(self, "comp", None) is None:
+                self.comp = np.zeros((self.N, 6))
+            _lib_handle().orc_run_comp(self.N, self.p, 0 if self.modified else 1, n_iter, dt, nsteps,
+                                       _p(self.m), self.eps, self.G, _p(self.x), _p(self.v),
+                                       _p(self.derivs), _p(self.comp))
+        else:
+            _lib_handle().orc_run(self.N, self.p, 0 if self.modified else 1, n_iter, dt, nsteps,
+                                  _p(self.m), self.eps, self.G, _p(self.x), _p(self.v),
+                                  _p(self.derivs))
         self.t += dt * nsteps
 
     def step_timesym(self, eta: float, n_iter: int, nsteps: int = 1, backward: bool = False) -> np.ndarray:

@@ -316,10 +316,15 @@ void orc_predict(int N, int p, double dt, const double *x, const double *v,
 
 /* One correction of particle i.  d0, d1: a^(0..p) at t and t+dt.
  * Velocity first (Eq. 6, f = a), then position (Eq. 7, f = v) with the new
- * v1, as Section 2 prescribes.                                               */
-static void correct_one(int p, double dt, const double *cv, const double *cx,
-                        const double *x0, const double *v0,
-                        const double *d0, const double *d1, double *x1, double *v1)
+ * v1, as Section 2 prescribes.
+ * comp (optional): compensated summation of the updates over the steps
+ * (Section 3.2, after Kahan): comp[0..2] and comp[3..5] hold the parts of x and
+ * v lost to rounding so far (negated, as Kahan's c); the update y = inc - c is
+ * added to x0, and comp_out receives the new c = ((x0 + y) - x0) - y.          */
+static void correct_one_c(int p, double dt, const double *cv, const double *cx,
+                          const double *x0, const double *v0,
+                          const double *d0, const double *d1, double *x1, double *v1,
+                          const double *comp, double *comp_out)
 {
     const double h = 0.5 * dt;
     for (int c = 0; c < 3; ++c) {
@@ -331,7 +336,14 @@ static void correct_one(int p, double dt, const double *cv, const double *cx,
                                       : sc * (d1[n * 3 + c] - d0[n * 3 + c]);
             dv += cv[n] * fpm;
         }
-        v1[c] = v0[c] + dv * dt;
+        if (comp) {
+            const double y = dv * dt - comp[3 + c];
+            const double t = v0[c] + y;
+            comp_out[3 + c] = (t - v0[c]) - y;
+            v1[c] = t;
+        } else {
+            v1[c] = v0[c] + dv * dt;
+        }
     }
     for (int c = 0; c < 3; ++c) {
         /* f = v: f^(0) = v, f^(n) = a^(n-1) */
@@ -343,8 +355,22 @@ static void correct_one(int p, double dt, const double *cv, const double *cx,
             double fpm = (n % 2 == 0) ? sc * (f1 + f0) : sc * (f1 - f0);
             dx += cx[n] * fpm;
         }
-        x1[c] = x0[c] + dx * dt;
+        if (comp) {
+            const double y = dx * dt - comp[c];
+            const double t = x0[c] + y;
+            comp_out[c] = (t - x0[c]) - y;
+            x1[c] = t;
+        } else {
+            x1[c] = x0[c] + dx * dt;
+        }
     }
+}
+
+static void correct_one(int p, double dt, const double *cv, const double *cx,
+                        const double *x0, const double *v0,
+                        const double *d0, const double *d1, double *x1, double *v1)
+{
+    correct_one_c(p, dt, cv, cx, x0, v0, d0, d1, x1, v1, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -375,7 +401,8 @@ double orc_timestep_H(int N, const double *m, const double *x, double eps, doubl
  * *H holds H+ of the last evaluation, the next step's H-.  Returns the dt of
  * the final correction.                                                        */
 static double step_impl(int N, int p, int beta_mode, int n_iter, double dt, double eta, double *H,
-                        const double *m, double eps, double G, double *x, double *v, double *derivs)
+                        const double *m, double eps, double G, double *x, double *v, double *derivs,
+                        double *comp)
 {
     const int K = 2 * p;
     const int P = p;                          /* pair derivatives evaluated */
@@ -391,6 +418,7 @@ static double step_impl(int N, int p, int beta_mode, int n_iter, double dt, doub
     double *d1 = (double *)malloc((size_t)N * (P + 1) * 3 * sizeof(double));
     double *x1 = (double *)malloc((size_t)N * 3 * sizeof(double));
     double *v1 = (double *)malloc((size_t)N * 3 * sizeof(double));
+    double *cnew = comp ? (double *)malloc((size_t)N * 6 * sizeof(double)) : NULL;
 
     const double H_minus = eta > 0 ? *H : 0.0;
     if (eta > 0) dt = dir * H_minus;
@@ -420,8 +448,9 @@ static double step_impl(int N, int p, int beta_mode, int n_iter, double dt, doub
             double d0[(ORC_MAXP + 1) * 3];
             for (int q = 0; q <= P; ++q)
                 for (int c = 0; c < 3; ++c) d0[q * 3 + c] = derivs[((size_t)i * K + q) * 3 + c];
-            correct_one(p, dt, cv, cx, x + 3 * i, v + 3 * i, d0,
-                        d1 + (size_t)i * (P + 1) * 3, x1 + 3 * i, v1 + 3 * i);
+            correct_one_c(p, dt, cv, cx, x + 3 * i, v + 3 * i, d0,
+                          d1 + (size_t)i * (P + 1) * 3, x1 + 3 * i, v1 + 3 * i,
+                          comp ? comp + 6 * i : NULL, comp ? cnew + 6 * i : NULL);
         }
         if (eta > 0 && it < n_iter - 1) {
             const double dt_new = dir * 0.5 * (H_minus + H_plus);
@@ -462,7 +491,8 @@ static double step_impl(int N, int p, int beta_mode, int n_iter, double dt, doub
                 derivs[((size_t)i * K + q) * 3 + c] = (q <= P) ? e1[q * 3 + c] : hi[q * 3 + c];
         for (int c = 0; c < 3; ++c) { x[i * 3 + c] = x1[i * 3 + c]; v[i * 3 + c] = v1[i * 3 + c]; }
     }
-    free(xp); free(vp); free(ap); free(tr); free(d1); free(x1); free(v1);
+    if (comp) memcpy(comp, cnew, (size_t)N * 6 * sizeof(double));   /* the committed step's compensation */
+    free(xp); free(vp); free(ap); free(tr); free(d1); free(x1); free(v1); free(cnew);
     return dt;
 }
 
@@ -470,7 +500,17 @@ static double step_impl(int N, int p, int beta_mode, int n_iter, double dt, doub
 void orc_step(int N, int p, int beta_mode, int n_iter, double dt, const double *m,
               double eps, double G, double *x, double *v, double *derivs)
 {
-    step_impl(N, p, beta_mode, n_iter, dt, 0.0, NULL, m, eps, G, x, v, derivs);
+    step_impl(N, p, beta_mode, n_iter, dt, 0.0, NULL, m, eps, G, x, v, derivs, NULL);
+}
+
+/* nsteps constant steps with compensated summation of the x, v updates
+ * (Section 3.2); comp: N x 6 carried compensation (zero at the start). */
+void orc_run_comp(int N, int p, int beta_mode, int n_iter, double dt, int nsteps,
+                  const double *m, double eps, double G, double *x, double *v, double *derivs,
+                  double *comp)
+{
+    for (int s = 0; s < nsteps; ++s)
+        step_impl(N, p, beta_mode, n_iter, dt, 0.0, NULL, m, eps, G, x, v, derivs, comp);
 }
 
 /* nsteps time-symmetric variable steps (Section 3.3) forward (dir > 0) or
@@ -483,7 +523,7 @@ double orc_run_timesym(int N, int p, int beta_mode, int n_iter, int dir, double 
     double t = 0.0;
     for (int s = 0; s < nsteps; ++s) {
         const double dt = step_impl(N, p, beta_mode, n_iter, dir < 0 ? -1.0 : 1.0, eta, H, m, eps, G,
-                                    x, v, derivs);
+                                    x, v, derivs, NULL);
         if (dts) dts[s] = dt;
         t += dt;
     }
