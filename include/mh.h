@@ -95,6 +95,11 @@ typedef struct {
                            per thread, 2 = two, 3 = two in packed FP32x2 lanes.  The
                            autotuner only runs for 8192 or more evaluated bodies; below,
                            0 means 1. */
+    int compensated;    /* shared constant steps: 1 sums the x and v updates of successive
+                           steps with compensated summation (Kahan; Section 3.2 uses it
+                           with the 8th-order scheme to push round-off down), carrying a
+                           per-body compensation that mh_set_state resets; 0 (default)
+                           plain sums. */
 } mh_config;
 
 /* Snapshot of a simulation (mh_sync / mh_set_state).  Each pointer may be NULL

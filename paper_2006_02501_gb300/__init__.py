@@ -67,13 +67,15 @@ class Simulation:
     fp32_variant: precision form evaluation kernel, 0 = autotuned, 1/2/3 fixed
     (one i-body per thread, two, two in packed FP32x2 lanes);
     timesym_eta: not None for time-symmetric variable shared steps with this
-    eta of Eq. 24 (FP64; advance with step_timesym()).
+    eta of Eq. 24 (FP64; advance with step_timesym());
+    compensated: compensated summation of the x, v updates (shared steps).
     """
 
     def __init__(self, order: int, m, x, v, eps: float, precision: int = MH_PREC_FP64,
                  beta: int = MH_BETA_MODIFIED, G: float = 1.0, stream=None, split_j: int = 0,
                  heavy_frac: float | None = None, block: dict | None = None,
-                 symmetric: int = 1, fp32_variant: int = 0, timesym_eta: float | None = None):
+                 symmetric: int = 1, fp32_variant: int = 0, timesym_eta: float | None = None,
+                 compensated: bool = False):
         L = _capi.lib()
         m = _host(m)
         N = m.shape[0]
@@ -85,6 +87,7 @@ class Simulation:
             cfg.heavy_frac = heavy_frac
         cfg.symmetric = int(symmetric)
         cfg.fp32_variant = int(fp32_variant)
+        cfg.compensated = 1 if compensated else 0
         if timesym_eta is not None:
             cfg.step_mode = _capi.MH_STEP_TIMESYM
             cfg.eta = float(timesym_eta)

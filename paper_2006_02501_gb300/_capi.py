@@ -41,7 +41,7 @@ class Config(ctypes.Structure):
                 ("step_mode", ctypes.c_int), ("G", ctypes.c_double), ("eta", ctypes.c_double),
                 ("dt_max", ctypes.c_double), ("k_max", ctypes.c_int), ("split_j", ctypes.c_int),
                 ("heavy_frac", ctypes.c_double), ("symmetric", ctypes.c_int),
-                ("fp32_variant", ctypes.c_int)]
+                ("fp32_variant", ctypes.c_int), ("compensated", ctypes.c_int)]
 
 
 class StateC(ctypes.Structure):

@@ -51,7 +51,7 @@ int dalloc(T **ptr, size_t count)
 void free_state(DeviceState &s)
 {
     void *ptrs[] = {s.m, s.x0, s.v0, s.d0, s.x1, s.v1, s.jrec, s.jrec32, s.part, s.diag, s.flag, s.bound,
-                    s.heavy, s.T, s.level, s.act, s.blk, s.tsw, s.tst};
+                    s.heavy, s.T, s.level, s.act, s.blk, s.tsw, s.tst, s.comp};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (s.blk_host) cudaFreeHost(s.blk_host);
@@ -341,6 +341,7 @@ void mh_config_default(mh_config *cfg)
     cfg->split_j = 0;
     cfg->symmetric = 1;
     cfg->fp32_variant = 0;
+    cfg->compensated = 0;
     cfg->heavy_frac = 1e-3;
 }
 
@@ -382,6 +383,10 @@ int mh::create_shell(mh_sim **out, int64_t N, int order, const double *m, const 
         return MH_EINVAL;
     }
     if (c.symmetric < 0 || c.symmetric > 2) { set_error("mh_create: symmetric must be 0, 1 or 2"); return MH_EINVAL; }
+    if (c.compensated != 0 && (c.compensated != 1 || c.step_mode != MH_STEP_SHARED)) {
+        set_error("mh_create: compensated summation (compensated = 1) is built for shared constant steps");
+        return MH_EINVAL;
+    }
     if (c.fp32_variant < 0 || c.fp32_variant > 3) { set_error("mh_create: fp32_variant must be 0..3"); return MH_EINVAL; }
     if (c.step_mode == MH_STEP_BLOCK) {
         if (p < 2 || p > 3) { set_error("mh_create: block steps need order 6 or 8"); return MH_EINVAL; }
@@ -431,6 +436,11 @@ int mh::create_shell(mh_sim **out, int64_t N, int order, const double *m, const 
             return fail(rc);
         cudaError_t eh = cudaMallocHost((void **)&s.blk_host, 2 * sizeof(unsigned long long));
         if (eh != cudaSuccess) return fail(cuda_fail(eh, "cudaMallocHost"));
+    }
+    if (c.compensated) {
+        if ((rc = dalloc(&s.comp, 6 * s.Np))) return fail(rc);
+        cudaError_t ez = cudaMemsetAsync(s.comp, 0, 6 * s.Np * sizeof(double), sim->stream);
+        if (ez != cudaSuccess) return fail(cuda_fail(ez, "cudaMemsetAsync"));
     }
     if (c.step_mode == MH_STEP_TIMESYM) {
         if ((rc = dalloc(&s.tsw, 2 * kTsMaxIter)) || (rc = dalloc(&s.tst, 1))) return fail(rc);
@@ -930,6 +940,7 @@ int mh_set_state(mh_sim *sim, const mh_state *in)
     if (int rc = upload_bounds(s, in->x, in->v, sim->stream)) return rc;
     sim->t = in->t;
     if (s.tst) MH_CUDA(cudaMemcpy(s.tst, &in->t, sizeof(double), cudaMemcpyHostToDevice));
+    if (s.comp) MH_CUDA(cudaMemset(s.comp, 0, 6 * s.Np * sizeof(double)));   // a new state starts exact
     if (in->derivs) {
         to_soa(in->derivs, s.N, 2 * s.p, s.Np, h, 0.0);
         MH_CUDA(cudaMemcpy(s.d0, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));

@@ -105,6 +105,8 @@ struct DeviceState {
     unsigned long long *tsw = nullptr;
     double *tst = nullptr;
     int ts_prev = 0;
+    // Compensated summation (Section 3.2): [6][Np] carried compensation of x, v.
+    double *comp = nullptr;
 };
 
 constexpr int kMaxHeavy = 32;

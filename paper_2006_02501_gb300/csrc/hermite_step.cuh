@@ -57,6 +57,36 @@ __device__ __forceinline__ void correct_comp(double dt, int bm, const double (&d
     xn = fma(sx, dt, x0);
 }
 
+// The corrector with compensated summation of the two updates (Section 3.2,
+// after Kahan): cx, cv carry the parts of x, v lost to rounding in earlier
+// steps (negated, Kahan's c) and return the new ones.  The increment minus the
+// compensation is formed by one fused multiply-add.
+template <int p>
+__device__ __forceinline__ void correct_comp_kahan(double dt, int bm, const double (&d0)[2 * p],
+                                                   const double (&d1)[p + 1], double x0, double v0,
+                                                   double &cx, double &cv, double &xn, double &vn)
+{
+    double sv = 0.0;
+#pragma unroll
+    for (int k = p; k >= 0; --k) {
+        const double f = (k & 1) ? d1[k] - d0[k] : d1[k] + d0[k];
+        sv = fma(sv, dt, kv<p>(k) * f);
+    }
+    const double yv = fma(sv, dt, -cv);
+    vn = v0 + yv;
+    cv = (vn - v0) - yv;
+    double sx = 0.0;
+#pragma unroll
+    for (int k = p + 1; k >= 1; --k) {
+        const double f = (k & 1) ? d1[k - 1] - d0[k - 1] : d1[k - 1] + d0[k - 1];
+        sx = fma(sx, dt, (bm == 0 ? kx<p>(0, k) : kx<p>(1, k)) * f);
+    }
+    sx = fma(sx, dt, (bm == 0 ? kx<p>(0, 0) : kx<p>(1, 0)) * (vn + v0));
+    const double yx = fma(sx, dt, -cx);
+    xn = x0 + yx;
+    cx = (xn - x0) - yx;
+}
+
 // a^(p+1..2p-1)(t1) of one component from the degree-(2p+1) Hermite interpolant:
 // a^(n)(t1) = sum_k (e1(n,k) a1^(k) + e0(n,k) a0^(k)) dt^(k-n).
 template <int p>

@@ -34,6 +34,7 @@ struct StepArgs {
     unsigned long long *bound_wr;         // [x, v] raised with this kernel's values
     unsigned long long *conv = nullptr;   // optional [max |x_new - x_old|, max |x_new|] (double bits)
     TimeSymArgs ts{};                     // time-symmetric variable step (ts.w != null), else dt above
+    double *comp = nullptr;               // optional [6][ld]: compensation of x, v (Kahan), committed by the last pass
 };
 
 // H of Eq. 24 from a word holding the maximum over pairs of G (m_i + m_j) s^(-3/2).
@@ -196,7 +197,18 @@ __global__ void k_correct(StepArgs a)
 #pragma unroll
         for (int k = 0; k < K; ++k) d0[k] = a.d0[(3 * k + c) * a.ld + i];
         double xn, vn;
-        correct_comp<p>(dt, a.beta_mode, d0, d1, a.x0[c * a.ld + i], a.v0[c * a.ld + i], xn, vn);
+        if (a.comp) {
+            // compensated summation of the updates (Section 3.2): the new compensation
+            // is committed with the step, every pass starts from the committed one
+            double cx = a.comp[c * a.ld + i], cv = a.comp[(3 + c) * a.ld + i];
+            correct_comp_kahan<p>(dt, a.beta_mode, d0, d1, a.x0[c * a.ld + i], a.v0[c * a.ld + i], cx, cv, xn, vn);
+            if (kLast && live) {
+                a.comp[c * a.ld + i] = cx;
+                a.comp[(3 + c) * a.ld + i] = cv;
+            }
+        } else {
+            correct_comp<p>(dt, a.beta_mode, d0, d1, a.x0[c * a.ld + i], a.v0[c * a.ld + i], xn, vn);
+        }
 #pragma unroll
         for (int q = 0; q + 2 <= p; ++q) ad[q][c] = d1[q];
         if (!kLast && a.ts.w) {
@@ -844,6 +856,7 @@ int launch_step_phase(const DeviceState &s, const mh_config &cfg, double dt, int
                s.bound ? s.bound + 2 * s.flip : nullptr, s.bound ? s.bound + 2 * (1 - s.flip) : nullptr,
                conv};
     if (ts) a.ts = *ts;
+    a.comp = s.comp;
     switch (s.p) {
     case 1: return launch_step_kernels<1>(a, phase, last, st);
     case 2: return launch_step_kernels<2>(a, phase, last, st);
