@@ -318,10 +318,29 @@ def run_ours(args, rank, world, local_rank):
     d1 = sim32.counters()
     sim32.close()
     variant32 = d1["pair_variant"]
-    kernel32 = {1: "k_pair_fp32<3,1>", 2: "k_pair_fp32<3,2>", 3: "k_pair_fp32x2<3>"}.get(variant32, "?")
+    kernel32 = {1: "k_pair_fp32<3,1>", 2: "k_pair_fp32<3,2>", 3: "k_pair_fp32x2<3>",
+                4: "k_pair_fp32_sym<3>"}.get(variant32, "?")
     el32 = reduce_max(sum(t32))
     pair32_ms = (d1["pair_kernel_ms"] - d0["pair_kernel_ms"]) / max(d1["pair_kernel_timed"] - d0["pair_kernel_timed"], 1)
-    ach32 = FLOPS_PER_PAIR[ORDER] * N * (N - 1) / (pair32_ms * 1e-3)
+    flops32 = FLOPS_PER_UNORDERED_PAIR[ORDER] * N * (N - 1) / 2 if d1["pair_variant"] == 4 \
+        else FLOPS_PER_PAIR[ORDER] * N * (N - 1)
+    ach32 = flops32 / (pair32_ms * 1e-3)
+
+    # ---- FP32-pair form with the ordered-pair packed kernel (variant 3), same workload ----
+    simp = mh.Simulation(ORDER, m, x, v, EPS, stream=stream, precision=mh.MH_PREC_FP32PAIR, fp32_variant=3)
+    for _ in range(3):
+        simp.step(DT, N_ITER)
+    kp = 5
+    p0 = simp.counters()
+    barrier()
+    simp.set_timing(True)
+    tp = time_steps(simp, stream, torch, kp, flush)
+    barrier()
+    p1 = simp.counters()
+    simp.close()
+    elp = reduce_max(sum(tp))
+    pairp_ms = (p1["pair_kernel_ms"] - p0["pair_kernel_ms"]) / max(p1["pair_kernel_timed"] - p0["pair_kernel_timed"], 1)
+    achp = FLOPS_PER_PAIR[ORDER] * N * (N - 1) / (pairp_ms * 1e-3)
 
     # ---- batched form: 4096 planetary systems, 6th order, 10^4 steps in one launch ----
     from paper_2006_02501_gb300 import inputs as _inp
@@ -373,12 +392,14 @@ def run_ours(args, rank, world, local_rank):
             "fp32pair": {
             "value": world * k32 * units / (el32 * 1e-3), "unit": UNIT, "ms_per_step": el32 / k32,
             "steps": k32, "pair_kernel": kernel32, "launch_ms": pair32_ms,
-            "autotuner_us": {"one_per_thread": d1["pair_tune_ms_x1000"][0],
-                             "two_per_thread": d1["pair_tune_ms_x1000"][1],
-                             "two_packed_fp32x2": d1["pair_tune_ms_x1000"][2]},
+            "flops_per_launch": flops32,
             "achieved_tflops": ach32 / 1e12, "peak_tflops": PEAK_FP32 / 1e12,
             "frac": ach32 / PEAK_FP32,
             "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"},
+            "fp32pair_ordered_packed": {
+            "value": world * kp * units / (elp * 1e-3), "unit": UNIT, "ms_per_step": elp / kp, "steps": kp,
+            "pair_kernel": "k_pair_fp32x2<3>", "launch_ms": pairp_ms, "achieved_tflops": achp / 1e12,
+            "peak_tflops": PEAK_FP32 / 1e12, "frac": achp / PEAK_FP32, "flops_per_pair": FLOPS_PER_PAIR[ORDER]},
             "batched": {
             "workload": "4096 planetary systems (3..64 bodies), 6th order FP64, P(EC)^2, dt_s = P_min/128, "
                         "10^4 steps in one launch",

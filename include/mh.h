@@ -80,7 +80,7 @@ typedef struct {
                            (at most 32 such bodies; 0 disables; default 1e-3).  In
                            a disc around a central mass this keeps the dominant
                            central force at FP64 accuracy for O(N) extra work. */
-    int symmetric;      /* FP64 form, shared and time-symmetric steps: 2 evaluates every
+    int symmetric;      /* shared and time-symmetric steps (both forms): 2 evaluates every
                            unordered pair once and adds its terms to both bodies (each
                            term of the Section 3 pair derivatives is odd under i <-> j),
                            which halves the FP64 work; 0 evaluates every ordered pair;
@@ -90,11 +90,12 @@ typedef struct {
                            (P+1)*3*Np doubles (C ~ 10; Np = N padded to 256), about
                            1.7 GB at N = 65536 and order 8; above 8 GiB, or with block
                            steps, the ordered kernel runs. */
-    int fp32_variant;   /* precision form, evaluation kernel: 0 (default) = chosen per size
-                           class by timing each once (autotuner), or fixed: 1 = one i-body
-                           per thread, 2 = two, 3 = two in packed FP32x2 lanes.  The
-                           autotuner only runs for 8192 or more evaluated bodies; below,
-                           0 means 1. */
+    int fp32_variant;   /* precision form, ordered-pair evaluation kernel: 0 (default) =
+                           chosen per size class by timing each once (autotuner), or
+                           fixed: 1 = one i-body per thread, 2 = two, 3 = two in packed
+                           FP32x2 lanes (a fixed variant also turns the pair-symmetric
+                           kernel off).  The autotuner only runs for 8192 or more
+                           evaluated bodies; below, 0 means 1. */
     int compensated;    /* shared constant steps: 1 sums the x and v updates of successive
                            steps with compensated summation (Kahan; Section 3.2 uses it
                            with the 8th-order scheme to push round-off down), carrying a
@@ -122,9 +123,10 @@ typedef struct {
     double pair_kernel_ms;       /* with timing on: summed device time of the O(N^2)
                                     evaluation kernels (CUDA events around each launch) */
     int64_t pair_kernel_timed;   /* number of evaluation launches in pair_kernel_ms */
-    int32_t pair_variant;        /* precision form: evaluation kernel of the last evaluation, as
-                                    chosen by the autotuner: 1 = one i-body per thread, 2 = two,
-                                    3 = two in the lanes of packed FP32x2 instructions */
+    int32_t pair_variant;        /* precision form: evaluation kernel of the last evaluation:
+                                    1 = one i-body per thread, 2 = two, 3 = two in the lanes of
+                                    packed FP32x2 instructions (1-3 chosen by the autotuner),
+                                    4 = each unordered pair once (see mh_config.symmetric) */
     int32_t pair_tune_ms_x1000[3];   /* the tuner's last timings of the three variants, microseconds */
 } mh_counters;
 

@@ -208,6 +208,40 @@ int evaluate(mh_sim *sim, int P, int precision, int *split, unsigned long long *
             return MH_OK;
         }
     }
+    if (precision == MH_PREC_FP32PAIR && P <= 3 && sim->cfg.fp32_variant == 0 &&
+        (sym_mode == 2 || (sym_mode == 1 && s.Np >= kSymMinNp))) {
+        // precision form, each unordered pair once; the heavy bodies' FP64 pairs in the slot after
+        const SymPlan sp = plan_sym(P, s.Np, sim->device, true);
+        const bool heavy = s.n_heavy > 0;
+        const int slots = sp.slots + (heavy ? 1 : 0);
+        const size_t need = (size_t)slots * (P + 1) * 3 * s.Np;
+        if (sp.nB > 0 && need * sizeof(double) <= kSymMaxPartBytes) {
+            int rc = ensure_part(s, need, sim->stream);
+            if (rc) return rc;
+            std::pair<cudaEvent_t, cudaEvent_t> ev{};
+            if (sim->timing) {
+                if ((rc = timed_event_pair(sim, &ev))) return rc;
+                MH_CUDA(cudaEventRecord(ev.first, sim->stream));
+            }
+            if ((rc = launch_pair_sym32(P, sp, s.jrec32, s.Np, s.N, sim->eps, s.part, sim->stream))) return rc;
+            if (sim->timing) {
+                MH_CUDA(cudaEventRecord(ev.second, sim->stream));
+                sim->ev_pending.push_back(ev);
+            }
+            if (heavy) {
+                if ((rc = launch_pair_heavy(P, s.N, s.Np, s.m, s.jrec, s.heavy, s.n_heavy, sim->eps, sim->cfg.G,
+                                            s.part, sp.slots, sim->stream)))
+                    return rc;
+                sim->ctr.kernel_launches += 1;
+            }
+            sim->ctr.pair_variant = 4;
+            *split = slots;
+            sim->ctr.evaluations += 1;
+            sim->ctr.pair_interactions += (double)s.N * (double)(s.N - 1);
+            sim->ctr.kernel_launches += 1;
+            return MH_OK;
+        }
+    }
     int ipt = 1;
     if (precision == MH_PREC_FP32PAIR)
         if (int rc = tuned_variant(sim, P, s.N, nullptr, &ipt)) return rc;

@@ -230,7 +230,11 @@ struct SymPlan {
     int grid = 0;
     int slots = 0;                      // C + D
 };
-SymPlan plan_sym(int P, int64_t ld, int device);
+SymPlan plan_sym(int P, int64_t ld, int device, bool fp32 = false);
+// The precision form's pair-symmetric evaluation (FP32 pairs, FP64 sums), same
+// plan and slots; jrec32 as written by the step kernels (mass row holding G m).
+int launch_pair_sym32(int P, const SymPlan &plan, const float *jrec32, int64_t ld, int64_t N, double eps,
+                      double *part, cudaStream_t st);
 // wmax (optional, device): raised to the maximum over pairs of G (m_i + m_j) s^(-3/2)
 // as a bit pattern (the time-step criterion of Section 3.3, Eq. 24).
 int launch_pair_sym(int P, const SymPlan &plan, const double *jrec, const double *m, int64_t ld, int64_t N,

@@ -231,23 +231,221 @@ int launch_sym(const SymPlan &pl, const double *jrec, const double *m, int64_t l
     return MH_OK;
 }
 
+// ---------------------------------------------------------------------------
+// FP32-pair form, each unordered pair once.  Same block schedule, ring and
+// partial-sum slots as the FP64 kernel above; the pair arithmetic is the
+// precision form's: x and v differences from the hi/lo split, (hi_j - hi_i) +
+// (lo_j - lo_i), everything else of the pair in FP32.  The FP32 sums cover one
+// 32-step ring and are then added to FP64 accumulators: registers for the
+// i-side, the shared-memory column sums for the j-side.
+// ---------------------------------------------------------------------------
+
+template <int P>
+struct SymArgs32 {
+    const float *jrec32;  // [nf32(P)][ld]: x_hi, x_lo, v_hi, v_lo, a, a-dot, G m
+    int64_t ld, N;
+    int nB, D, C, Bc;
+    float eps2;
+    double *part;         // [C + D][(P+1)*3][ld]
+};
+
+template <int P>
+struct Rec32s {
+    static constexpr int NF = nf32(P);
+};
+
+// Record of body b; padding bodies massless at distinct far-away positions.
+template <int P>
+__device__ __forceinline__ void load_body32(const SymArgs32<P> &a, int64_t b, float (&r)[Rec32s<P>::NF])
+{
+    constexpr int NF = Rec32s<P>::NF;
+    if (b < a.N) {
+#pragma unroll
+        for (int q = 0; q < NF; ++q) r[q] = a.jrec32[q * a.ld + b];
+    } else {
+#pragma unroll
+        for (int q = 0; q < NF; ++q) r[q] = 0.0f;
+        r[0] = (float)kFarAway + (float)(b - a.N);
+    }
+}
+
+// Relative trajectory derivatives of the pair (j - i) from two records.
+template <int P>
+__device__ __forceinline__ void rel32(const float (&ri)[Rec32s<P>::NF], const float (&rj)[Rec32s<P>::NF],
+                                      float (&r)[P + 1][3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        r[0][c] = (rj[c] - ri[c]) + (rj[3 + c] - ri[3 + c]);
+        r[1][c] = (rj[6 + c] - ri[6 + c]) + (rj[9 + c] - ri[9 + c]);
+        if constexpr (P >= 2) r[2][c] = rj[12 + c] - ri[12 + c];
+        if constexpr (P >= 3) r[3][c] = rj[15 + c] - ri[15 + c];
+    }
+}
+
+// Two warps per CTA, two i-bodies per lane: lane l of warp w holds the bodies
+// of i-subtiles 2w and 2w + 1, so every j-record passed around the ring serves
+// two pairs.  FP32 sums cover one 128-body block (as the tiles of the ordered
+// kernels) and are added to FP64 once per block.
+constexpr int kSym32Warps = 2;
+
+template <int P>
+__global__ void __launch_bounds__(32 * kSym32Warps, 4) k_pair_fp32_sym(SymArgs32<P> a)
+{
+    constexpr int NF = Rec32s<P>::NF;
+    constexpr int NR = 3 * (P + 1);
+    __shared__ float accs[NR][kSymR];     // j-side FP32 sums of the current block, by column
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int src = (lane + 1) & 31;
+    const bool even = (a.nB & 1) == 0;
+    const int64_t items = (int64_t)a.nB * a.C;
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int I = (int)(item % a.nB);
+        const int ch = (int)(item / a.nB);
+        float ri[2][NF], gmi[2];
+        double acc64[2][NR];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            load_body32<P>(a, (int64_t)I * kSymR + (2 * w + k) * 32 + lane, ri[k]);
+            gmi[k] = ri[k][NF - 1];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) acc64[k][q] = 0.0;
+        }
+
+        const int dmax = (even && I >= a.nB / 2) ? a.D - 1 : a.D;
+        const int b0 = ch * a.Bc;
+        const int b1 = min(b0 + a.Bc, dmax + 1);
+        for (int b = b0; b < b1; ++b) {
+            const bool diag = b == 0;
+            const int J = (I + b) % a.nB;
+            float acci[2][P + 1][3];
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int n = 0; n <= P; ++n)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) acci[k][n][c] = 0.0f;
+            for (int jt = 0; jt < 4; ++jt) {
+                // off-diagonal: at stage jt warp w takes j-subtile (2w + jt) mod 4 (the two
+                // warps never share one); diagonal block: every warp takes every subtile
+                const int js = diag ? jt : (2 * w + jt) & 3;
+                float rj[NF];
+                load_body32<P>(a, (int64_t)J * kSymR + js * 32 + lane, rj);
+                float accj[P + 1][3];
+#pragma unroll
+                for (int n = 0; n <= P; ++n)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) accj[n][c] = 0.0f;
+                for (int t = 0; t < 32; ++t) {
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        float r[P + 1][3];
+                        rel32<P>(ri[k], rj, r);
+                        float s = fmaf(r[0][0], r[0][0], fmaf(r[0][1], r[0][1], fmaf(r[0][2], r[0][2], a.eps2)));
+                        const bool self = diag && js == 2 * w + k && t == 0;
+                        s = self ? 1.0f : s;
+                        const float rinv = rsqrt_mufu(s);
+                        const float sinv = rinv * rinv;
+                        const float S = rinv * sinv;
+                        const float wi = self ? 0.0f : rj[NF - 1] * S;
+                        const float wj = diag ? 0.0f : gmi[k] * S;
+                        pair_abg_terms<P, float>(r, sinv, [&](int n, int c, float B) {
+                            acci[k][n][c] = fmaf(wi, B, acci[k][n][c]);
+                            accj[n][c] = fmaf(-wj, B, accj[n][c]);
+                        });
+                    }
+#pragma unroll
+                    for (int q = 0; q < NF; ++q) rj[q] = __shfl_sync(0xffffffffu, rj[q], src);
+                    if (!diag) {
+#pragma unroll
+                        for (int n = 0; n <= P; ++n)
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) accj[n][c] = __shfl_sync(0xffffffffu, accj[n][c], src);
+                    }
+                }
+                if (!diag) {
+                    // each column is visited twice, by warp 0 and by warp 1: first at stage
+                    // 0 (columns 0, 2) or 1 (columns 1, 3), second at stage 2 or 3
+#pragma unroll
+                    for (int n = 0; n <= P; ++n)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            float &cell = accs[3 * n + c][js * 32 + lane];
+                            cell = (jt < 2 ? 0.0f : cell) + accj[n][c];
+                        }
+                    __syncthreads();
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int n = 0; n <= P; ++n)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) acc64[k][3 * n + c] += (double)acci[k][n][c];
+            if (!diag) {
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int col = threadIdx.x + k * 64;
+                    double *out = a.part + (int64_t)(a.C + b - 1) * NR * a.ld + (int64_t)J * kSymR + col;
+#pragma unroll
+                    for (int q = 0; q < NR; ++q) out[q * a.ld] = (double)accs[q][col];
+                }
+                __syncthreads();
+            }
+        }
+        if (even && I >= a.nB / 2 && ch == a.C - 1) {
+            const int J = (I + a.D) % a.nB;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                double *out = a.part + (int64_t)(a.C + a.D - 1) * NR * a.ld + (int64_t)J * kSymR + threadIdx.x + k * 64;
+#pragma unroll
+                for (int q = 0; q < NR; ++q) out[q * a.ld] = 0.0;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            double *out = a.part + (int64_t)ch * NR * a.ld + (int64_t)I * kSymR + (2 * w + k) * 32 + lane;
+#pragma unroll
+            for (int q = 0; q < NR; ++q) out[q * a.ld] = acc64[k][q];
+        }
+    }
+}
+
+template <int P>
+int launch_sym32(const SymPlan &pl, const float *jrec32, int64_t ld, int64_t N, double eps, double *part,
+                 cudaStream_t st)
+{
+    SymArgs32<P> a{jrec32, ld, N, pl.nB, pl.D, pl.C, pl.Bc, (float)(eps * eps), part};
+    k_pair_fp32_sym<P><<<pl.grid, 32 * kSym32Warps, 0, st>>>(a);
+    MH_LAUNCHED("k_pair_fp32_sym");
+    return MH_OK;
+}
+
 }  // namespace
 
-SymPlan plan_sym(int P, int64_t ld, int device)
+SymPlan plan_sym(int P, int64_t ld, int device, bool fp32)
 {
     SymPlan pl{};
     if (ld % kSymR != 0 || ld < kSymR || P < 1 || P > 3) return pl;
-    // resident CTAs per device, cached per (device, P)
-    static int slot_cache[64][4] = {{0}};
-    int slots = device >= 0 && device < 64 ? slot_cache[device][P] : 0;
+    // resident CTAs per device, cached per (device, P, form)
+    static int slot_cache[64][8] = {{0}};
+    const int ci = P + (fp32 ? 4 : 0);
+    int slots = device >= 0 && device < 64 ? slot_cache[device][ci] : 0;
     if (slots == 0) {
         int n_sm = 0, occ = 0;
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
-        const void *fn = P == 1 ? (const void *)k_pair_fp64_sym<1, false>
-                       : P == 2 ? (const void *)k_pair_fp64_sym<2, false> : (const void *)k_pair_fp64_sym<3, false>;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kSymR, 0);
+        if (fp32) {
+            const void *fn = P == 1 ? (const void *)k_pair_fp32_sym<1>
+                           : P == 2 ? (const void *)k_pair_fp32_sym<2> : (const void *)k_pair_fp32_sym<3>;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * kSym32Warps, 0);
+        } else {
+            const void *fn = P == 1 ? (const void *)k_pair_fp64_sym<1, false>
+                           : P == 2 ? (const void *)k_pair_fp64_sym<2, false> : (const void *)k_pair_fp64_sym<3, false>;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kSymR, 0);
+        }
         slots = std::max(n_sm, 1) * std::max(occ, 1);
-        if (device >= 0 && device < 64) slot_cache[device][P] = slots;
+        if (device >= 0 && device < 64) slot_cache[device][ci] = slots;
     }
     pl.nB = (int)(ld / kSymR);
     pl.D = pl.nB / 2;
@@ -270,6 +468,18 @@ SymPlan plan_sym(int P, int64_t ld, int device)
     pl.grid = (int)std::min<int64_t>((int64_t)pl.nB * pl.C, slots);
     pl.slots = pl.C + pl.D;
     return pl;
+}
+
+int launch_pair_sym32(int P, const SymPlan &pl, const float *jrec32, int64_t ld, int64_t N, double eps,
+                      double *part, cudaStream_t st)
+{
+    switch (P) {
+    case 1: return launch_sym32<1>(pl, jrec32, ld, N, eps, part, st);
+    case 2: return launch_sym32<2>(pl, jrec32, ld, N, eps, part, st);
+    case 3: return launch_sym32<3>(pl, jrec32, ld, N, eps, part, st);
+    }
+    set_error("launch_pair_sym32: P must be 1..3");
+    return MH_EINVAL;
 }
 
 int launch_pair_sym(int P, const SymPlan &pl, const double *jrec, const double *m, int64_t ld, int64_t N,

@@ -239,8 +239,8 @@ def fp32_disc_case(orc):
     return m, x, v, dt, eps, nst, ref
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3])
-def test_fp32_pair_form_accuracy(mh, orc, fp32_disc_case, variant):
+@pytest.mark.parametrize("variant,symmetric", [(1, 1), (2, 1), (3, 1), (0, 2)])
+def test_fp32_pair_form_accuracy(mh, orc, fp32_disc_case, variant, symmetric):
     """Precision form: the relative energy error after the run within 1e-9 of
     the oracle's, and accelerations within 2e-6 of the oracle's, for each
     evaluation kernel.  Stars of 1e-9 each keep star-star encounters
@@ -248,9 +248,11 @@ def test_fp32_pair_form_accuracy(mh, orc, fp32_disc_case, variant):
     the inner orbits (about 31 steps per orbit at r = 0.1) rather than a
     chaotic quantity."""
     m, x, v, dt, eps, nst, ref = fp32_disc_case
-    with mh.Simulation(8, m, x, v, eps, precision=mh.MH_PREC_FP32PAIR, fp32_variant=variant) as s32:
+    with mh.Simulation(8, m, x, v, eps, precision=mh.MH_PREC_FP32PAIR, fp32_variant=variant,
+                       symmetric=symmetric) as s32:
         E0 = s32.energy()
         s32.step(dt, 3, nsteps=nst)
+        assert s32.counters()["pair_variant"] == (4 if symmetric == 2 else variant)
         _, x32, v32, d32 = s32.sync()
         E32 = s32.energy()
     dE_ref = ref.energy() / orc.energy(m, x, v, eps) - 1
@@ -262,20 +264,21 @@ def test_fp32_pair_form_accuracy(mh, orc, fp32_disc_case, variant):
 
 def test_fp32_variants_full_size(mh):
     """SMBH disc, 65536 stars + SMBH, one 8th-order P(EC)^3 step in the precision
-    form with each evaluation kernel: one and two i-bodies per thread agree
-    bit for bit; every variant's accelerations lie within 2e-6 of the FP64
-    form's (itself held to the oracle at 1e-12)."""
+    form with each evaluation kernel (three ordered-pair variants and the
+    pair-symmetric default): one and two i-bodies per thread agree bit for bit;
+    every kernel's accelerations lie within 2e-6 of the FP64 form's (itself
+    held to the oracle at 1e-12)."""
     m, x, v = I.smbh_disc(seed=2, N=65536)
     dt, eps = 2 * np.pi * 1e-3, 1e-4
     with mh.Simulation(8, m, x, v, eps) as s64:
         s64.step(dt, 3)
         _, _, _, d64 = s64.sync()
     got = {}
-    for variant in (1, 2, 3):
+    for variant in (1, 2, 3, 0):                  # 0: the default, each unordered pair once
         with mh.Simulation(8, m, x, v, eps, precision=mh.MH_PREC_FP32PAIR, fp32_variant=variant) as s32:
             s32.step(dt, 3)
             _, _, _, d32 = s32.sync()
-            assert s32.counters()["pair_variant"] == variant
+            assert s32.counters()["pair_variant"] == (variant or 4)
         got[variant] = d32
         assert rel_rows(d32[:, 0], d64[:, 0]) < 2e-6, variant
     np.testing.assert_array_equal(got[1][:, :4], got[2][:, :4])
