@@ -222,6 +222,25 @@ def time_steps_batch(b, stream, torch, steps):
     return e0.elapsed_time(e1) * 1e-3
 
 
+def reduce_max(val: float, world: int) -> float:
+    """Maximum of a per-rank value over all ranks (the job's time is the slowest
+    rank's); the tensor lives where the process group's backend wants it."""
+    if world == 1:
+        return val
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([val], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, seconds_max: float) -> float:
+    """Whole-job throughput: every rank advances its own replica (weak scaling),
+    so the job processes world x units in the slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2006_02501_gb300 as mh
@@ -244,14 +263,6 @@ def run_ours(args, rank, world, local_rank):
             import torch.distributed as dist
             dist.barrier()
 
-    def reduce_max(val):
-        if world == 1:
-            return val
-        import torch.distributed as dist
-        t = torch.tensor([val], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     # ---- FP64 form: the headline ----
     sim = mh.Simulation(ORDER, m, x, v, EPS, stream=stream)
     for _ in range(args.warmup):
@@ -264,8 +275,8 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     sim.set_timing(False)
     c1 = sim.counters()
-    elapsed_ms = reduce_max(sum(times))
-    value = world * args.steps * units / (elapsed_ms * 1e-3)
+    elapsed_ms = reduce_max(sum(times), world)
+    value = job_rate(world, args.steps * units, elapsed_ms * 1e-3)
     pair_launches = c1["pair_kernel_timed"] - c0["pair_kernel_timed"]
     pair_ms = (c1["pair_kernel_ms"] - c0["pair_kernel_ms"]) / max(pair_launches, 1)
     gpu_launches = c1["kernel_launches"] - c0["kernel_launches"]
@@ -285,7 +296,7 @@ def run_ours(args, rank, world, local_rank):
         sim.step(DT, N_ITER)
         _, hx2, hv2, hd2 = sim.sync()
     barrier()
-    e2e_s = reduce_max(time.perf_counter() - t0)
+    e2e_s = reduce_max(time.perf_counter() - t0, world)
     h2d = hx.nbytes + hv.nbytes + hd.nbytes
     d2h = hx2.nbytes + hv2.nbytes + hd2.nbytes
     sim.close()
@@ -301,7 +312,7 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     o1 = simo.counters()
     simo.close()
-    elo = reduce_max(sum(to))
+    elo = reduce_max(sum(to), world)
     pairo_ms = (o1["pair_kernel_ms"] - o0["pair_kernel_ms"]) / max(o1["pair_kernel_timed"] - o0["pair_kernel_timed"], 1)
     acho = FLOPS_PER_PAIR[ORDER] * N * (N - 1) / (pairo_ms * 1e-3)
 
@@ -320,7 +331,7 @@ def run_ours(args, rank, world, local_rank):
     variant32 = d1["pair_variant"]
     kernel32 = {1: "k_pair_fp32<3,1>", 2: "k_pair_fp32<3,2>", 3: "k_pair_fp32x2<3>",
                 4: "k_pair_fp32_sym<3>"}.get(variant32, "?")
-    el32 = reduce_max(sum(t32))
+    el32 = reduce_max(sum(t32), world)
     pair32_ms = (d1["pair_kernel_ms"] - d0["pair_kernel_ms"]) / max(d1["pair_kernel_timed"] - d0["pair_kernel_timed"], 1)
     flops32 = FLOPS_PER_UNORDERED_PAIR[ORDER] * N * (N - 1) / 2 if d1["pair_variant"] == 4 \
         else FLOPS_PER_PAIR[ORDER] * N * (N - 1)
@@ -338,7 +349,7 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     p1 = simp.counters()
     simp.close()
-    elp = reduce_max(sum(tp))
+    elp = reduce_max(sum(tp), world)
     pairp_ms = (p1["pair_kernel_ms"] - p0["pair_kernel_ms"]) / max(p1["pair_kernel_timed"] - p0["pair_kernel_timed"], 1)
     achp = FLOPS_PER_PAIR[ORDER] * N * (N - 1) / (pairp_ms * 1e-3)
 
@@ -350,7 +361,7 @@ def run_ours(args, rank, world, local_rank):
         b.step(10, 2)
         g0 = b.counters()
         barrier()
-        tb = time_steps_batch(b, stream, torch, 10000)
+        tb = reduce_max(time_steps_batch(b, stream, torch, 10000), world)
         barrier()
         g1 = b.counters()
     sizes = np.diff(off)
