@@ -284,10 +284,63 @@ __device__ __forceinline__ void rel32(const float (&ri)[Rec32s<P>::NF], const fl
 }
 
 // Two warps per CTA, two i-bodies per lane: lane l of warp w holds the bodies
-// of i-subtiles 2w and 2w + 1, so every j-record passed around the ring serves
-// two pairs.  FP32 sums cover one 128-body block (as the tiles of the ordered
-// kernels) and are added to FP64 once per block.
+// of i-subtiles 2w and 2w + 1 in the two lanes of Blackwell's paired FP32
+// instructions (FFMA2/FMUL2/FADD2), so every j-record passed around the ring
+// serves two pairs and one issue slot advances both.  The i-side sums are
+// packed too; the j-side sum of a ring lane adds both pairs' terms in FP32.
+// FP32 sums cover one 128-body block (as the tiles of the ordered kernels) and
+// are added to FP64 once per block.
 constexpr int kSym32Warps = 2;
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// The scaled terms B_k of pair_abg_terms for two pairs at once (negated
+// coefficients so that every update is one multiply-add); sink(k, c, B).
+template <int P, typename Sink>
+__device__ __forceinline__ void pair_abg_terms_x2(const float2 (&r)[P + 1][3], float2 sinv, Sink &&sink)
+{
+    const float2 rv = fma2(r[0][2], r[1][2], fma2(r[0][1], r[1][1], mul2(r[0][0], r[1][0])));
+    const float2 al = mul2(rv, sinv);
+    const float2 na3 = mul2(f2(-3.0f), al);
+    float2 B1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        B1[c] = fma2(na3, r[0][c], r[1][c]);
+        sink(0, c, r[0][c]);
+        sink(1, c, B1[c]);
+    }
+    if constexpr (P >= 2) {
+        const float2 al2 = mul2(al, al);
+        float2 w2 = mul2(r[1][0], r[1][0]);
+        w2 = fma2(r[1][1], r[1][1], w2);
+        w2 = fma2(r[1][2], r[1][2], w2);
+        w2 = fma2(r[0][0], r[2][0], w2);
+        w2 = fma2(r[0][1], r[2][1], w2);
+        w2 = fma2(r[0][2], r[2][2], w2);
+        const float2 be = fma2(w2, sinv, al2);
+        const float2 na6 = mul2(f2(-6.0f), al), nb3 = mul2(f2(-3.0f), be);
+        float2 B2[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            B2[c] = fma2(nb3, r[0][c], fma2(na6, B1[c], r[2][c]));
+            sink(2, c, B2[c]);
+        }
+        if constexpr (P >= 3) {
+            const float2 va = fma2(r[1][2], r[2][2], fma2(r[1][1], r[2][1], mul2(r[1][0], r[2][0])));
+            const float2 rj = fma2(r[0][2], r[3][2], fma2(r[0][1], r[3][1], mul2(r[0][0], r[3][0])));
+            const float2 w3 = fma2(f2(3.0f), va, rj);
+            // gamma = w3/s + alpha (3 beta - 4 alpha^2), 3 beta - 4 alpha^2 = -(nb3 + 4 alpha^2)
+            const float2 u = fma2(f2(4.0f), al2, nb3);
+            const float2 ga = fma2(w3, sinv, mul2(mul2(f2(-1.0f), al), u));
+            const float2 na9 = mul2(f2(-9.0f), al), nb9 = mul2(f2(-9.0f), be), ng3 = mul2(f2(-3.0f), ga);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sink(3, c, fma2(ng3, r[0][c], fma2(nb9, B1[c], fma2(na9, B2[c], r[3][c]))));
+        }
+    }
+}
 
 template <int P>
 __global__ void __launch_bounds__(32 * kSym32Warps, 4) k_pair_fp32_sym(SymArgs32<P> a)
@@ -299,19 +352,26 @@ __global__ void __launch_bounds__(32 * kSym32Warps, 4) k_pair_fp32_sym(SymArgs32
     const int w = threadIdx.x >> 5;
     const int src = (lane + 1) & 31;
     const bool even = (a.nB & 1) == 0;
+    const float2 eps2 = f2(a.eps2);
     const int64_t items = (int64_t)a.nB * a.C;
     for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
         const int I = (int)(item % a.nB);
         const int ch = (int)(item / a.nB);
-        float ri[2][NF], gmi[2];
+        // the lane's two i-bodies, negated (differences become additions), packed
+        float2 ni[NF - 1], gmi;
+        {
+            float r0[NF], r1[NF];
+            load_body32<P>(a, (int64_t)I * kSymR + (2 * w) * 32 + lane, r0);
+            load_body32<P>(a, (int64_t)I * kSymR + (2 * w + 1) * 32 + lane, r1);
+#pragma unroll
+            for (int q = 0; q < NF - 1; ++q) ni[q] = make_float2(-r0[q], -r1[q]);
+            gmi = make_float2(r0[NF - 1], r1[NF - 1]);
+        }
         double acc64[2][NR];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            load_body32<P>(a, (int64_t)I * kSymR + (2 * w + k) * 32 + lane, ri[k]);
-            gmi[k] = ri[k][NF - 1];
+        for (int k = 0; k < 2; ++k)
 #pragma unroll
             for (int q = 0; q < NR; ++q) acc64[k][q] = 0.0;
-        }
 
         const int dmax = (even && I >= a.nB / 2) ? a.D - 1 : a.D;
         const int b0 = ch * a.Bc;
@@ -319,13 +379,11 @@ __global__ void __launch_bounds__(32 * kSym32Warps, 4) k_pair_fp32_sym(SymArgs32
         for (int b = b0; b < b1; ++b) {
             const bool diag = b == 0;
             const int J = (I + b) % a.nB;
-            float acci[2][P + 1][3];
+            float2 acci[P + 1][3];
 #pragma unroll
-            for (int k = 0; k < 2; ++k)
+            for (int n = 0; n <= P; ++n)
 #pragma unroll
-                for (int n = 0; n <= P; ++n)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) acci[k][n][c] = 0.0f;
+                for (int c = 0; c < 3; ++c) acci[n][c] = f2(0.0f);
             for (int jt = 0; jt < 4; ++jt) {
                 // off-diagonal: at stage jt warp w takes j-subtile (2w + jt) mod 4 (the two
                 // warps never share one); diagonal block: every warp takes every subtile
@@ -338,23 +396,30 @@ __global__ void __launch_bounds__(32 * kSym32Warps, 4) k_pair_fp32_sym(SymArgs32
 #pragma unroll
                     for (int c = 0; c < 3; ++c) accj[n][c] = 0.0f;
                 for (int t = 0; t < 32; ++t) {
+                    float2 r[P + 1][3];
 #pragma unroll
-                    for (int k = 0; k < 2; ++k) {
-                        float r[P + 1][3];
-                        rel32<P>(ri[k], rj, r);
-                        float s = fmaf(r[0][0], r[0][0], fmaf(r[0][1], r[0][1], fmaf(r[0][2], r[0][2], a.eps2)));
-                        const bool self = diag && js == 2 * w + k && t == 0;
-                        s = self ? 1.0f : s;
-                        const float rinv = rsqrt_mufu(s);
-                        const float sinv = rinv * rinv;
-                        const float S = rinv * sinv;
-                        const float wi = self ? 0.0f : rj[NF - 1] * S;
-                        const float wj = diag ? 0.0f : gmi[k] * S;
-                        pair_abg_terms<P, float>(r, sinv, [&](int n, int c, float B) {
-                            acci[k][n][c] = fmaf(wi, B, acci[k][n][c]);
-                            accj[n][c] = fmaf(-wj, B, accj[n][c]);
-                        });
+                    for (int c = 0; c < 3; ++c) {
+                        r[0][c] = add2(add2(f2(rj[c]), ni[c]), add2(f2(rj[3 + c]), ni[3 + c]));
+                        r[1][c] = add2(add2(f2(rj[6 + c]), ni[6 + c]), add2(f2(rj[9 + c]), ni[9 + c]));
+                        if constexpr (P >= 2) r[2][c] = add2(f2(rj[12 + c]), ni[12 + c]);
+                        if constexpr (P >= 3) r[3][c] = add2(f2(rj[15 + c]), ni[15 + c]);
                     }
+                    float2 s = fma2(r[0][0], r[0][0], fma2(r[0][1], r[0][1], fma2(r[0][2], r[0][2], eps2)));
+                    const bool self0 = diag && js == 2 * w && t == 0;
+                    const bool self1 = diag && js == 2 * w + 1 && t == 0;
+                    s.x = self0 ? 1.0f : s.x;
+                    s.y = self1 ? 1.0f : s.y;
+                    const float2 rinv = make_float2(rsqrt_mufu(s.x), rsqrt_mufu(s.y));
+                    const float2 sinv = mul2(rinv, rinv);
+                    const float2 S = mul2(rinv, sinv);
+                    float2 wi = mul2(f2(rj[NF - 1]), S);
+                    wi.x = self0 ? 0.0f : wi.x;
+                    wi.y = self1 ? 0.0f : wi.y;
+                    const float2 wj = diag ? f2(0.0f) : mul2(gmi, S);
+                    pair_abg_terms_x2<P>(r, sinv, [&](int n, int c, float2 B) {
+                        acci[n][c] = fma2(wi, B, acci[n][c]);
+                        accj[n][c] = fmaf(-wj.y, B.y, fmaf(-wj.x, B.x, accj[n][c]));
+                    });
 #pragma unroll
                     for (int q = 0; q < NF; ++q) rj[q] = __shfl_sync(0xffffffffu, rj[q], src);
                     if (!diag) {
@@ -378,11 +443,12 @@ __global__ void __launch_bounds__(32 * kSym32Warps, 4) k_pair_fp32_sym(SymArgs32
                 }
             }
 #pragma unroll
-            for (int k = 0; k < 2; ++k)
+            for (int n = 0; n <= P; ++n)
 #pragma unroll
-                for (int n = 0; n <= P; ++n)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) acc64[k][3 * n + c] += (double)acci[k][n][c];
+                for (int c = 0; c < 3; ++c) {
+                    acc64[0][3 * n + c] += (double)acci[n][c].x;
+                    acc64[1][3 * n + c] += (double)acci[n][c].y;
+                }
             if (!diag) {
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
