@@ -86,3 +86,20 @@ def test_symmetric_matches_ordered_full_size(mh):
     assert scaled_stack_err(a[0], b[0], dt) < 1e-13
     assert rel_rows(a[1], b[1]) < 1e-14 and rel_rows(a[2], b[2]) < 1e-13
     assert scaled_stack_err(a[3], b[3], dt) < 1e-12
+
+
+@pytest.mark.parametrize("N", [2, 3, 129, 300, 1100])
+def test_symmetric_fp32_small_sizes(mh, orc, N):
+    """The precision form's pair-symmetric kernel forced at small sizes (one
+    block of 128 with its ring guard, ragged padding, several blocks): the
+    accelerations after one step within 2e-6 of the oracle's."""
+    m, x, v = I.smbh_disc(seed=50 + N, N=max(N - 1, 1), m_total=N * 1e-9)
+    m, x, v = m[:N], x[:N], v[:N]
+    dt, eps = 2 * np.pi * 1e-3, 1e-4
+    with mh.Simulation(8, m, x, v, eps, precision=mh.MH_PREC_FP32PAIR, symmetric=2) as sim:
+        sim.step(dt, 3)
+        _, _, _, dg = sim.sync()
+        assert sim.counters()["pair_variant"] == 4
+    ref = orc.State(8, m, x, v, eps)
+    ref.step(dt, 3)
+    assert rel_rows(dg[:, 0], ref.derivs[:, 0]) < 2e-6

@@ -108,3 +108,20 @@ def test_timesym_graph_replay_matches_plain_launches(mh):
     assert out[0][0] == out[1][0]
     for a, b in zip(out[0][1:], out[1][1:]):
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("n_bodies", [60, 300])
+def test_timesym_pair_symmetric_kernel(mh, orc, n_bodies):
+    """The Eq. 24 maximum inside the pair-symmetric kernel (forced with
+    symmetric = 2; by default small systems take the ordered kernel): its
+    diagonal blocks (ordered pairs, guarded self pair) and its off-diagonal
+    blocks (each pair once) both feed w_max."""
+    m, x, v = I.disc_100(seed=8, n=n_bodies)
+    eta, n, K, eps = 0.02, 4, 20, 1e-6
+    with mh.Simulation(8, m, x, v, eps, timesym_eta=eta, symmetric=2) as sim:
+        sim.step_timesym(K, n)
+        t, xg, vg, _ = sim.sync()
+    ref = orc.State(8, m, x, v, eps)
+    ref.step_timesym(eta, n, K)
+    assert abs(t - ref.t) / ref.t < 1e-12
+    assert rel_rows(xg, ref.x) < 1e-12 and rel_rows(vg, ref.v, 1e-3) < 1e-11
