@@ -54,7 +54,8 @@ def _stream_handle(stream) -> int | None:
 class Simulation:
     """One N-body system advanced by the shared-step P(EC)^n scheme.
 
-    order: 4, 6 or 8; precision: MH_PREC_FP64 or MH_PREC_FP32PAIR; beta:
+    order: 4, 6, 8, 10 or 12 (10 and 12: FP64 form, shared or time-symmetric
+    steps); precision: MH_PREC_FP64 or MH_PREC_FP32PAIR; beta:
     MH_BETA_MODIFIED (Eq. 20) or MH_BETA_STANDARD (beta = 1); stream: a
     torch.cuda.Stream, a raw cudaStream_t integer, or None (library stream);
     heavy_frac: precision form, mass fraction above which a source body's

@@ -1,4 +1,8 @@
-// O(N^2) direct-summation evaluation of a^(0..P) (the E of P(EC)^n).
+// O(N^2) direct-summation evaluation of a^(0..P) (the E of P(EC)^n), every
+// ordered pair: the kernels for active lists (block steps), small systems,
+// the initialisation passes above P = 3, and mh_pair_eval.  Shared-step
+// evaluations of larger systems take the pair-symmetric kernels of
+// pair_sym.cu instead.
 //
 // Pair physics (Dittmann 2020, Section 3, intro): a_ij = G m_j r_ij s^(-3/2),
 // s = r_ij^2 + eps^2.  Its time derivatives along the trajectory follow from
@@ -9,9 +13,10 @@
 // For P = 3 this is the familiar alpha/beta/gamma form: tau_1 = 3 alpha,
 // tau_2 = 3 beta, tau_3 = 3 gamma.
 //
-// Decomposition: items = (i-tile of `threads` bodies, one per thread) x
+// Decomposition: items = (i-tile of `threads` bodies, one or two per thread) x
 // (j-chunk); a CTA loops over items with a grid stride; j-records of a chunk
-// are staged through shared memory in tiles of `tj`.  Each item writes its own
+// are staged through shared memory in tiles of `tj` (FP64 evaluations too small
+// to fill the GPU use one-warp CTAs and tiles as short as 2: plan_fine64).  Each item writes its own
 // partial-sum slot; the corrector (or mh_pair_eval's reduction) adds the
 // slots in a fixed order, so the result is deterministic.
 //
