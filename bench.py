@@ -53,11 +53,14 @@ FLOPS_PER_PAIR = {4: 60, 6: 97, 8: 144}
 # second body, 3 (p + 1) of them.
 FLOPS_PER_UNORDERED_PAIR = {o: FLOPS_PER_PAIR[o] + 2 * 3 * (o // 2) for o in (4, 6, 8)}
 # Peaks from unit counts and the maximum SM clock (2070 MHz), 152 SMs:
-#   FP32: 128 FMA lanes/SM x 2 flops; FP64: the GB300 nominal 1.25 TFLOP/s.
+#   FP32: 128 FMA lanes/SM x 2 flops; FP64: 2 DFMA lanes/SM x 2 flops (ncu's
+#   peak of 304 DFMA thread-instructions per cycle on 152 SMs; the GB300
+#   nominal figure is 1.25 TFLOP/s).  mh.measure_peaks() measures both on the
+#   box and the JSON line reports them beside these.
 SM_MAX_MHZ = 2070.0
 N_SM = 152
 PEAK_FP32 = N_SM * 128 * 2 * SM_MAX_MHZ * 1e6
-PEAK_FP64 = 1.25e12
+PEAK_FP64 = N_SM * 2 * 2 * SM_MAX_MHZ * 1e6
 # DRAM traffic per launch of the dominant kernel from one ncu capture
 # (profiles/); valid only while the kernel source is the one captured.
 TRAFFIC = {"files": ["paper_2006_02501_gb300/csrc/pair_sym.cu", "paper_2006_02501_gb300/csrc/pair_math.cuh"],
@@ -368,6 +371,7 @@ def run_ours(args, rank, world, local_rank):
     batch_pairs = float((sizes * (sizes - 1)).sum()) * 2 * 10000
     batch_ps = (g1["particle_steps"] - g0["particle_steps"]) / tb
 
+    peaks = mh.measure_peaks()       # measured ALU rates of this GPU, reported beside the unit-count peaks
     if rank != 0:
         return
     cpu = None
@@ -388,12 +392,13 @@ def run_ours(args, rank, world, local_rank):
                      "kernel": "k_pair_fp64_sym<3>",
                      "flops_per_unordered_pair": FLOPS_PER_UNORDERED_PAIR[ORDER],
                      "unordered_pairs_per_launch": N * (N - 1) // 2,
-                     "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (profiling recipe table)",
+                     "peak_source": "152 SMs x 2 FP64 lanes x 2 flops x 2070 MHz (nominal 1.25 TFLOP/s)",
                      "launch_ms": pair_ms, "launches": pair_launches},
         "cpu_baseline": cpu,
         "e2e": {"value": world * e2e_steps * units / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clocks,
+        "measured_alu_peaks": peaks,
         "gpu_launches": gpu_launches,
         "forms": {"fp64_ordered": {
             "value": world * ko * units / (elo * 1e-3), "unit": UNIT, "ms_per_step": elo / ko,

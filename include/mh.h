@@ -285,6 +285,14 @@ int mh_mlp_loss_grad(mh_mlp *net, const float *x, const float *t, int64_t rows, 
 int mh_mlp_train(mh_mlp *net, const float *x, const float *t, int64_t rows, int epochs, int batch,
                  float lr, uint64_t seed, double *final_loss, void *stream);
 
+/* Measured arithmetic rates of the current device, the denominators of the
+ * evaluation kernels' rooflines (not part of the paper's method).  out4[0..3]:
+ * FP64 fused multiply-add TFLOP/s, FP32 fused multiply-add TFLOP/s, packed
+ * FP32x2 multiply-add TFLOP/s, single-precision reciprocal square roots in
+ * 10^12 per second.  Every SM runs independent chains; each rate is one
+ * CUDA-event timed launch after a warm-up launch (about 2 s in all).  Waits. */
+int mh_measure_peaks(double *out4);
+
 /* Number of bodies, order and counters of a handle. */
 int mh_info(mh_sim *sim, int64_t *N, int *order, mh_counters *counters);
 

@@ -330,3 +330,11 @@ def pair_eval(P: int, precision: int, m, traj, eps: float, out, G: float = 1.0, 
         stream = torch.cuda.current_stream()
     check(_capi.lib().mh_pair_eval(int(P), int(precision), N, _dev_ptr(m), _dev_ptr(traj), float(eps),
                                    float(G), int(i0), int(i1), _dev_ptr(out), _stream_handle(stream)))
+
+
+def measure_peaks() -> dict:
+    """Measured FP64 / FP32 / packed FP32x2 multiply-add TFLOP/s and MUFU
+    reciprocal square roots (10^12/s) of the current device (mh_measure_peaks)."""
+    out = (ctypes.c_double * 4)()
+    check(_capi.lib().mh_measure_peaks(out))
+    return {"fp64_tflops": out[0], "fp32_tflops": out[1], "fp32x2_tflops": out[2], "rsqrt_tera_per_s": out[3]}

@@ -32,7 +32,7 @@ EXPORTS = [
     "mh_set_timing", "mh_pair_eval_noalloc", "mh_create_batch", "mh_step_batch", "mh_batch_tune",
     "mh_batch_energy", "mh_step_converge", "mh_set_predictor", "mh_collect_samples", "mh_mlp_create",
     "mh_mlp_destroy", "mh_mlp_num_params", "mh_mlp_get_params", "mh_mlp_set_params", "mh_mlp_forward",
-    "mh_mlp_loss_grad", "mh_mlp_train", "mh_predict", "mh_step_timesym",
+    "mh_mlp_loss_grad", "mh_mlp_train", "mh_predict", "mh_step_timesym", "mh_measure_peaks",
 ]
 
 
@@ -87,6 +87,7 @@ def lib() -> ctypes.CDLL:
             L.mh_mlp_destroy.restype = None
             L.mh_step.argtypes = [P, D, I]
             L.mh_step_timesym.argtypes = [P, I64, I, I]
+            L.mh_measure_peaks.argtypes = [DP]
             L.mh_sync.argtypes = [P, ctypes.POINTER(StateC)]
             L.mh_set_state.argtypes = [P, ctypes.POINTER(StateC)]
             L.mh_diagnostics.argtypes = [P, DP, DP, I]
