@@ -184,7 +184,7 @@ int evaluate(mh_sim *sim, int P, int precision, int *split, unsigned long long *
     // pair-symmetric kernel: always (symmetric = 2), or (symmetric = 1) once there
     // are 16 blocks of 128 bodies; below, its blocks are too few to fill the GPU
     const int sym_mode = sim->cfg.symmetric;
-    if (precision == MH_PREC_FP64 && P <= 3 && (sym_mode == 2 || (sym_mode == 1 && s.Np >= kSymMinNp))) {
+    if (precision == MH_PREC_FP64 && P <= 5 && (sym_mode == 2 || (sym_mode == 1 && s.Np >= kSymMinNp))) {
         const SymPlan sp = plan_sym(P, s.Np, sim->device);
         const size_t need = (size_t)sp.slots * (P + 1) * 3 * s.Np;
         if (sp.nB > 0 && need * sizeof(double) <= kSymMaxPartBytes) {

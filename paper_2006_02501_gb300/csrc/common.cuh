@@ -222,7 +222,8 @@ size_t energy_scratch_doubles(int64_t N);
 // FP32 form variant: 1 = one i-body per thread, 2 = two, 3 = two in packed FP32x2 lanes.
 PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hint, int device, int variant = 1);
 
-// All-pairs FP64 evaluation that computes each unordered pair once (pair_sym.cu).
+// All-pairs FP64 evaluation that computes each unordered pair once (pair_sym.cu),
+// P = 1 .. 5 (the precision form's, P = 1 .. 3).
 // Valid (nB > 0) when ld is a positive multiple of its 128-body block; writes
 // `slots` partial-sum slots of (P+1)*3 rows of stride ld, every one of them in full.
 struct SymPlan {

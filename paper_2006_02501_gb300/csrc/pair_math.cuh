@@ -108,6 +108,52 @@ __device__ __forceinline__ void pair_abg_terms(const T (&r)[P + 1][3], T sinv, S
     }
 }
 
+// The scaled terms B^(n) = A^(n) / (G m S) of the general recursion, for any P:
+// B^(0) = r, B^(n) = r^(n) - sum_{k=1..n} C(n,k) tau_k B^(n-k), with tau_k from
+// q_k = s^(k)/s as in pair_terms.  Odd under i <-> j like the P <= 3 form
+// (r^(k) changes sign, q_k and tau_k do not).  sink(n, c, B) receives component c of B^(n).
+template <int P, typename T, typename Sink>
+__device__ __forceinline__ void pair_general_terms(const T (&r)[P + 1][3], T sinv, Sink &&sink)
+{
+    T q[P + 1];
+    s_ratios<P, T>(r, sinv, q);
+    T tau[P + 1];
+    tau[0] = T(1);
+#pragma unroll
+    for (int n = 1; n <= P; ++n) {
+        T t = T(1.5) * q[n];
+#pragma unroll
+        for (int j = 1; j <= n - 1; ++j) {
+            const T w = T(1.5 * binom(n - 1, j - 1) - binom(n - 1, j));
+            t += w * q[j] * tau[n - j];
+        }
+        tau[n] = t;
+    }
+    T B[P + 1][3];
+#pragma unroll
+    for (int n = 0; n <= P; ++n) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            T b = r[n][c];
+#pragma unroll
+            for (int k = 1; k <= n; ++k) b -= (T(binom(n, k)) * tau[k]) * B[n - k][c];
+            B[n][c] = b;
+            sink(n, c, b);
+        }
+    }
+}
+
+// The odd terms of any supported P: the alpha/beta/gamma form up to P = 3, the
+// general recursion above.
+template <int P, typename T, typename Sink>
+__device__ __forceinline__ void pair_odd_terms(const T (&r)[P + 1][3], T sinv, Sink &&sink)
+{
+    if constexpr (P <= 3)
+        pair_abg_terms<P, T>(r, sinv, sink);
+    else
+        pair_general_terms<P, T>(r, sinv, sink);
+}
+
 // acc_k += (G m S) B_k for one ordered pair.
 template <int P, typename T>
 __device__ __forceinline__ void pair_abg(const T (&r)[P + 1][3], T mS, T sinv, T (&acc)[P + 1][3])

@@ -1,5 +1,5 @@
 // FP64 all-pairs evaluation of a^(0..P) that computes every unordered pair once
-// (the E of P(EC)^n under shared steps, and the initialisation passes P <= 3).
+// (the E of P(EC)^n under shared steps, and the initialisation passes P <= 5).
 //
 // Pair physics (Dittmann 2020, Section 3, intro): a_ij = G m_j r_ij s^(-3/2).
 // With the scaled terms B_k of pair_math.cuh, body i receives G m_j S B_k(i,j)
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kSymR, 2) k_pair_fp64_sym(SymArgs<P> a)
                             const unsigned long long wb = self ? 0ull : (unsigned long long)__double_as_longlong((gmi + gmj) * S);
                             wm = wb > wm ? wb : wm;
                         }
-                        pair_abg_terms<P, double>(r, sinv, [&](int k, int c, double B) {
+                        pair_odd_terms<P, double>(r, sinv, [&](int k, int c, double B) {
                             acci[k][c] = fma(mS, B, acci[k][c]);
                         });
                         rotate<P>(rj, gmj, src);
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kSymR, 2) k_pair_fp64_sym(SymArgs<P> a)
                         const unsigned long long wb = (unsigned long long)__double_as_longlong(wi + wj);
                         wm = wb > wm ? wb : wm;
                     }
-                    pair_abg_terms<P, double>(r, sinv, [&](int k, int c, double B) {
+                    pair_odd_terms<P, double>(r, sinv, [&](int k, int c, double B) {
                         acci[k][c] = fma(wi, B, acci[k][c]);
                         accj[k][c] = fma(-wj, B, accj[k][c]);
                     });
@@ -493,10 +493,10 @@ int launch_sym32(const SymPlan &pl, const float *jrec32, int64_t ld, int64_t N, 
 SymPlan plan_sym(int P, int64_t ld, int device, bool fp32)
 {
     SymPlan pl{};
-    if (ld % kSymR != 0 || ld < kSymR || P < 1 || P > 3) return pl;
+    if (ld % kSymR != 0 || ld < kSymR || P < 1 || P > (fp32 ? 3 : 5)) return pl;
     // resident CTAs per device, cached per (device, P, form)
-    static int slot_cache[64][8] = {{0}};
-    const int ci = P + (fp32 ? 4 : 0);
+    static int slot_cache[64][16] = {{0}};
+    const int ci = P + (fp32 ? 8 : 0);
     int slots = device >= 0 && device < 64 ? slot_cache[device][ci] : 0;
     if (slots == 0) {
         int n_sm = 0, occ = 0;
@@ -507,7 +507,9 @@ SymPlan plan_sym(int P, int64_t ld, int device, bool fp32)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * kSym32Warps, 0);
         } else {
             const void *fn = P == 1 ? (const void *)k_pair_fp64_sym<1, false>
-                           : P == 2 ? (const void *)k_pair_fp64_sym<2, false> : (const void *)k_pair_fp64_sym<3, false>;
+                           : P == 2 ? (const void *)k_pair_fp64_sym<2, false>
+                           : P == 3 ? (const void *)k_pair_fp64_sym<3, false>
+                           : P == 4 ? (const void *)k_pair_fp64_sym<4, false> : (const void *)k_pair_fp64_sym<5, false>;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kSymR, 0);
         }
         slots = std::max(n_sm, 1) * std::max(occ, 1);
@@ -555,8 +557,10 @@ int launch_pair_sym(int P, const SymPlan &pl, const double *jrec, const double *
     case 1: return launch_sym<1>(pl, jrec, m, ld, N, eps, G, part, wmax, st);
     case 2: return launch_sym<2>(pl, jrec, m, ld, N, eps, G, part, wmax, st);
     case 3: return launch_sym<3>(pl, jrec, m, ld, N, eps, G, part, wmax, st);
+    case 4: return launch_sym<4>(pl, jrec, m, ld, N, eps, G, part, wmax, st);
+    case 5: return launch_sym<5>(pl, jrec, m, ld, N, eps, G, part, wmax, st);
     }
-    set_error("launch_pair_sym: P must be 1..3");
+    set_error("launch_pair_sym: P must be 1..5");
     return MH_EINVAL;
 }
 

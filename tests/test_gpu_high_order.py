@@ -24,9 +24,10 @@ def mh():
 
 
 @pytest.mark.parametrize("order", [10, 12])
-def test_high_order_initialisation(mh, orc, order):
+@pytest.mark.parametrize("symmetric", [1, 2])          # 2: the pair-symmetric kernel (P <= 5) forced
+def test_high_order_initialisation(mh, orc, order, symmetric):
     m, x, v = I.smbh_disc(seed=41, N=400)
-    with mh.Simulation(order, m, x, v, 1e-4) as sim:
+    with mh.Simulation(order, m, x, v, 1e-4, symmetric=symmetric) as sim:
         _, _, _, dg = sim.sync()
     ref = orc.initialise(order, m, x, v, 1e-4)
     assert dg.shape == ref.shape == (401, order - 2, 3)
@@ -34,11 +35,11 @@ def test_high_order_initialisation(mh, orc, order):
 
 
 @pytest.mark.parametrize("order", [10, 12])
-@pytest.mark.parametrize("beta", [0, 1])
-def test_high_order_one_step(mh, orc, order, beta):
+@pytest.mark.parametrize("beta,symmetric", [(0, 1), (1, 1), (0, 2)])
+def test_high_order_one_step(mh, orc, order, beta, symmetric):
     m, x, v = I.planetesimal_ring(seed=42, n=200, m=1e-6, a_lo=0.5, a_hi=1.5, sigma_e=0.1, sigma_i=0.05)
     dt, eps = 0.08, 1e-3
-    with mh.Simulation(order, m, x, v, eps, beta=beta) as sim:
+    with mh.Simulation(order, m, x, v, eps, beta=beta, symmetric=symmetric) as sim:
         sim.step(dt, 3)
         _, xg, vg, dg = sim.sync()
     ref = orc.State(order, m, x, v, eps, modified=(beta == 0))
@@ -83,3 +84,14 @@ def test_high_order_rejects_unsupported_forms(mh):
         mh.Simulation(12, m, x, v, 0.0, block=dict(dt_max=2.0 ** -5, k_max=8, eta=0.05))
     with pytest.raises(mh.MHError):
         mh.Simulation(14, m, x, v, 0.0)
+
+
+def test_tenth_order_variable_step_pair_symmetric(mh, orc):
+    m, x, v = I.disc_100(seed=9, n=150)
+    with mh.Simulation(10, m, x, v, 1e-6, timesym_eta=0.03, symmetric=2) as sim:
+        sim.step_timesym(20, 4)
+        t, xg, vg, _ = sim.sync()
+    ref = orc.State(10, m, x, v, 1e-6)
+    ref.step_timesym(0.03, 4, 20)
+    assert abs(t - ref.t) / ref.t < 1e-12
+    assert rel_rows(xg, ref.x) < 1e-12 and rel_rows(vg, ref.v, 1e-3) < 1e-11
