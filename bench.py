@@ -64,10 +64,10 @@ PEAK_FP64 = N_SM * 2 * 2 * SM_MAX_MHZ * 1e6
 # DRAM traffic per launch of the dominant kernel from one ncu capture
 # (profiles/); valid only while the kernel source is the one captured.
 TRAFFIC = {"files": ["paper_2006_02501_gb300/csrc/pair_sym.cu", "paper_2006_02501_gb300/csrc/pair_math.cuh"],
-           "sha256": ["a0e24fb7dc060bd6efb4d845f16b28ef0dc47b3af92a4aabdc1fb271354e2b7d",
-                      "6fb5de969d2e5ff8a196395d0212ae24b655b7d4cf57b83ec55fbaef9aaaecc7"],
-           # profiles/k_pair_fp64_sym_disc_N65536_order8_dram.md: 56.33 MB read + 1.61 GB written
-           "bytes_per_launch": 56.33e6 + 1.61e9}
+           "sha256": ["84f31dcb0c93839f5125f35d08be4ff5cb8728a200a5de1b7407e1d7749496d5",
+                      "7b05f4cd731085ffd18547e017c5352bbda74f8e674505c0fb411285746659be"],
+           # profiles/k_pair_fp64_sym_disc_N65536_order8_dram.md: 56.26 MB read + 1.61 GB written
+           "bytes_per_launch": 56.26e6 + 1.61e9}
 
 
 def _sha(path):
