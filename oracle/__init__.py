@@ -8,6 +8,8 @@ no code: the oracle is plain C (``mh_oracle.c``, compiled with gcc and
 
 Array conventions (all float64, C-contiguous):
   m        (N,)
+  x2, ...  (..., 2)      double-double values (hi, lo), value = hi + lo, for the
+                         binary128 oracle of the double-double form (dd_*)
   x, v     (N, 3)
   derivs   (N, 2p, 3)    a^(0) .. a^(2p-1) of each particle
   traj     (N, P+1, 3)   x, v, a, a-dot, ... fed to a direct-summation evaluation
@@ -28,14 +30,25 @@ _lock = threading.Lock()
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile the C oracle with gcc (plain -O2, no FMA contraction, OpenMP over i)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-               "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+_SRC_Q = os.path.join(_HERE, "mh_oracle_q.c")
+_LIB_Q = os.path.join(_HERE, "libmh_oracle_q.so")
+_lib_q = None
+
+
+def _compile(src: str, lib: str, force: bool) -> None:
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+               "-fPIC", "-shared", src, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
+        os.replace(tmp, lib)
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracles with gcc (plain -O2, no FMA contraction, OpenMP over
+    i): the FP64 oracle and its binary128 twin for the double-double form."""
+    _compile(_SRC, _LIB, force)
+    _compile(_SRC_Q, _LIB_Q, force)
     return _LIB
 
 
@@ -315,3 +328,87 @@ class BlockState(State):
         target = int(round((self.T.max() * self.tick + dt) / self.tick))
         while self.T.min() < target:
             self.block_step(n_iter)
+
+
+# --------------------------------------------------------------------------- #
+# binary128 oracle of the double-double form (mh_oracle_q.c)
+# --------------------------------------------------------------------------- #
+
+def _lib_q_handle():
+    global _lib_q
+    with _lock:
+        if _lib_q is None:
+            build()
+            lib = ctypes.CDLL(_LIB_Q)
+            i, d = ctypes.c_int, ctypes.c_double
+            lib.orq_corrector_weights.argtypes = [i, i, _D, _D]
+            lib.orq_hermite_interp.argtypes = [i, d, _D, _D, i, _D]
+            lib.orq_run.argtypes = [i, i, i, i, d, i, _D, d, d, i, _D, _D, _D]
+            lib.orq_energy.argtypes = [i, _D, _D, _D, d, d, _D]
+            lib.orq_ecc.argtypes = [i, _D, _D, _D, d, i, _D]
+            _lib_q = lib
+    return _lib_q
+
+
+def as_dd(a) -> np.ndarray:
+    """A double-double array (..., 2): doubles get lo = 0, pairs pass through."""
+    a = np.asarray(a, dtype=np.float64)
+    if a.ndim >= 1 and a.shape[-1] == 2 and getattr(a, "_is_dd", False):
+        return np.ascontiguousarray(a)
+    return np.ascontiguousarray(np.stack([a, np.zeros_like(a)], axis=-1))
+
+
+def dd_value(a2) -> np.ndarray:
+    """hi + lo rounded to double (for display and FP64 comparisons)."""
+    a2 = np.asarray(a2)
+    return a2[..., 0] + a2[..., 1]
+
+
+def dd_corrector_weights(p: int, modified: bool = True):
+    """(cv, cx) on the F+- vectors from the Eq. 8 system solved in binary128,
+    as double-double pairs: (p+1, 2) and (p+2, 2)."""
+    cv, cx = np.zeros((8, 2)), np.zeros((8, 2))
+    _lib_q_handle().orq_corrector_weights(p, 0 if modified else 1, _p(cv), _p(cx))
+    return cv[:p + 1].copy(), cx[:p + 2].copy()
+
+
+def dd_hermite_interp(p: int, dt: float, f0_2, f1_2, nout: int) -> np.ndarray:
+    """f^(0..nout-1) at the end of the step (binary128), from (p+1, 3, 2) pairs."""
+    f0_2 = _f64(f0_2).reshape(p + 1, 3, 2)
+    f1_2 = _f64(f1_2).reshape(p + 1, 3, 2)
+    out = np.zeros((nout, 3, 2))
+    _lib_q_handle().orq_hermite_interp(p, dt, _p(f0_2), _p(f1_2), nout, _p(out))
+    return out
+
+
+def dd_run(order: int, m, x2, v2, eps: float, dt: float, n_iter: int, nsteps: int,
+           G: float = 1.0, modified: bool = True, d2=None):
+    """Initialise (d2 None) and take nsteps constant P(EC)^n steps, all in
+    binary128.  x2, v2: (N, 3, 2) pairs (or (N, 3) doubles); d2: (N, 2p, 3, 2).
+    Returns (x2, v2, d2) rounded to double-double pairs."""
+    p = order_to_p(order)
+    m = _f64(m)
+    N = m.shape[0]
+    x2 = _f64(x2).copy() if np.asarray(x2).ndim == 3 else as_dd(x2)
+    v2 = _f64(v2).copy() if np.asarray(v2).ndim == 3 else as_dd(v2)
+    init = d2 is None
+    d2 = np.zeros((N, 2 * p, 3, 2)) if init else _f64(d2).copy()
+    _lib_q_handle().orq_run(N, p, 0 if modified else 1, n_iter, dt, nsteps, _p(m), eps, G,
+                            1 if init else 0, _p(x2), _p(v2), _p(d2))
+    return x2, v2, d2
+
+
+def dd_energy(m, x2, v2, eps: float, G: float = 1.0) -> np.ndarray:
+    """Energy (R4) in binary128 as a (hi, lo) pair."""
+    m, x2, v2 = _f64(m), _f64(x2), _f64(v2)
+    E2 = np.zeros(2)
+    _lib_q_handle().orq_energy(m.shape[0], _p(m), _p(x2), _p(v2), eps, G, _p(E2))
+    return E2
+
+
+def dd_ecc(m, x2, v2, G: float = 1.0, central: int = 0) -> np.ndarray:
+    """Eccentricity vectors (Eq. A1) in binary128 as (N, 3, 2) pairs."""
+    m, x2, v2 = _f64(m), _f64(x2), _f64(v2)
+    e2 = np.zeros_like(x2)
+    _lib_q_handle().orq_ecc(m.shape[0], _p(m), _p(x2), _p(v2), G, central, _p(e2))
+    return e2
