@@ -220,6 +220,63 @@ int mh_batch_tune(mh_sim *sim, int probe_steps, int n_iter, int *warps, int *ord
 int mh_batch_energy(mh_sim *sim, double *energy);
 
 /* ------------------------------------------------------------------------- */
+/* Double-double form: extended precision for few-body systems.               */
+/* Section 3.1 shows the 8th-order scheme reaching the round-off of double     */
+/* precision at dt = 2^-4 on a Kepler orbit, and the Discussion proposes high- */
+/* order schemes with higher-precision arithmetic for such integrations.  In   */
+/* this form the state x, v, a^(0..2p-1), the prediction, every pair term and  */
+/* every sum are double-double (hi + lo, ~106 bits, relative rounding ~1e-32   */
+/* per operation); the step is the shared P(EC)^n step of mh_step.             */
+/* A double-double array holds each value as two consecutive doubles (hi, lo): */
+/* vectors are N x 3 x 2 (x2[2*(3*i + c)] = hi, x2[2*(3*i + c) + 1] = lo),      */
+/* derivative stacks N x 2p x 3 x 2, scalars 2 doubles.  Masses, eps, G and dt  */
+/* are doubles (exact inputs).  The cost per pair is about 20 times that of    */
+/* the FP64 form: the form is meant for systems of a few to a few thousand     */
+/* bodies.                                                                     */
+/* ------------------------------------------------------------------------- */
+
+typedef struct mh_dd mh_dd;
+
+/* Create a double-double simulation of N bodies (1 <= N <= 2^24) of order 4, 6,
+ * 8 or 10 (order 12 is refused with MH_EINVAL: its start needs the P = 9 pair
+ * derivatives, whose double-double kernel is not built).  m: N masses; x2, v2: N x 3 x 2 positions and velocities (a
+ * plain double state has lo = 0); eps >= 0; cfg: NULL for defaults, only
+ * beta_mode and G are read; stream as for mh_create.  Computes a^(0..2p-1) at
+ * t = 0 by explicit pair derivatives in double-double (Section 3 intro).  On
+ * error *out is NULL. */
+int mh_dd_create(mh_dd **out, int64_t N, int order, const double *m, const double *x2,
+                 const double *v2, double eps, const mh_config *cfg, void *stream);
+
+/* Release every resource of the handle (NULL is a no-op). */
+void mh_dd_destroy(mh_dd *sim);
+
+/* nsteps >= 0 shared P(EC)^n_iter steps of constant dt (dt finite and non-zero,
+ * 1 <= n_iter <= 64), as mh_step: prediction, n_iter evaluate-correct passes
+ * (velocity by Eq. 6, then position by Eq. 7 with beta of Eq. 20), a^(p+1..2p-1)
+ * from the Hermite interpolant.  For nsteps > 1 one step is captured as a CUDA
+ * graph (kept while dt and n_iter stay the same) and replayed.  Stream-ordered;
+ * the time is kept in double-double. */
+int mh_dd_step(mh_dd *sim, double dt, int n_iter, int64_t nsteps);
+
+/* Copy the state to host buffers (any may be NULL; waits): t2 (2 doubles),
+ * x2, v2 (N x 3 x 2), d2 (N x 2p x 3 x 2).  MH_ENONFINITE if a step produced a
+ * non-finite position or velocity. */
+int mh_dd_sync(mh_dd *sim, double *t2, double *x2, double *v2, double *d2);
+
+/* Overwrite the state: x2, v2 required; t2 may be NULL (time kept); d2 NULL
+ * recomputes a^(0..2p-1) by the initialisation passes.  Waits. */
+int mh_dd_set_state(mh_dd *sim, const double *t2, const double *x2, const double *v2, const double *d2);
+
+/* Diagnostics in double-double (waits).  energy2 (may be NULL): the energy
+ * sum m v^2/2 - sum_{i<j} G m_i m_j / sqrt(r^2 + eps^2) as (hi, lo).  ecc2 (may
+ * be NULL): N x 3 x 2 eccentricity vectors about body `central` (Appendix A,
+ * Eq. A1), the central body's row zero. */
+int mh_dd_diagnostics(mh_dd *sim, double *energy2, double *ecc2, int central);
+
+/* Size, order and counters of a double-double simulation (outputs may be NULL). */
+int mh_dd_info(mh_dd *sim, int64_t *N, int *order, mh_counters *counters);
+
+/* ------------------------------------------------------------------------- */
 /* Convergence-controlled stepping and the learned predictor residual.        */
 /* The paper has no learned component; it iterates P(EC)^n (Section 2.1, end)  */
 /* and these entry points measure how many passes a step needs.               */

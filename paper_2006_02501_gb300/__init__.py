@@ -20,7 +20,7 @@ from . import _capi
 from ._capi import (MH_BETA_MODIFIED, MH_BETA_STANDARD, MH_PREC_FP32PAIR, MH_PREC_FP64,  # noqa: F401
                     MHError, check)
 
-__all__ = ["Simulation", "Batch", "MLP", "pair_eval", "MHError", "build_library", "MH_PREC_FP64", "MH_PREC_FP32PAIR",
+__all__ = ["Simulation", "Batch", "DDSimulation", "MLP", "pair_eval", "MHError", "build_library", "MH_PREC_FP64", "MH_PREC_FP32PAIR",
            "MH_BETA_MODIFIED", "MH_BETA_STANDARD"]
 
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -305,6 +305,84 @@ class Batch:
         e = np.zeros(self.S)
         check(_capi.lib().mh_batch_energy(self._h, _ptr(e)))
         return e
+
+
+def _dd_host(a, N: int, K: int = 3) -> np.ndarray:
+    """(N, K, 2) double-double pairs from pairs or from plain doubles (lo = 0)."""
+    a = np.asarray(a, dtype=np.float64)
+    if a.ndim >= 1 and a.shape[-1] == 2 and a.size == N * K * 2:
+        return np.ascontiguousarray(a.reshape(N, K, 2))
+    a = a.reshape(N, K)
+    return np.ascontiguousarray(np.stack([a, np.zeros_like(a)], axis=-1))
+
+
+class DDSimulation:
+    """One system integrated in double-double arithmetic (mh_dd_*): the state,
+    the prediction, every pair term and every sum carry ~106 bits, so that the
+    high-order schemes can be run below the round-off of FP64 (Section 3.1;
+    Discussion).  Shared constant steps, orders 4 to 10.
+
+    x, v: (N, 3) doubles or (N, 3, 2) (hi, lo) pairs.  Results come back as
+    (..., 2) pairs; value = hi + lo.
+    """
+
+    def __init__(self, order: int, m, x, v, eps: float, beta: int = MH_BETA_MODIFIED, G: float = 1.0,
+                 stream=None):
+        L = _capi.lib()
+        m = _host(m)
+        N = m.shape[0]
+        x2, v2 = _dd_host(x, N), _dd_host(v, N)
+        cfg = _capi.Config()
+        L.mh_config_default(ctypes.byref(cfg))
+        cfg.order, cfg.beta_mode, cfg.G = order, beta, G
+        h = ctypes.c_void_p()
+        check(L.mh_dd_create(ctypes.byref(h), N, order, _ptr(m), _ptr(x2), _ptr(v2), float(eps),
+                             ctypes.byref(cfg), _stream_handle(stream)))
+        self._h = h
+        self.N, self.order, self.p = N, order, order // 2 - 1
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _capi.lib().mh_dd_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def step(self, dt: float, n_iter: int, nsteps: int = 1) -> None:
+        check(_capi.lib().mh_dd_step(self._h, float(dt), int(n_iter), int(nsteps)))
+
+    def sync(self):
+        """(t2, x2, v2, d2): time (2,), positions and velocities (N, 3, 2), a^(0..2p-1) (N, 2p, 3, 2)."""
+        t2 = np.zeros(2)
+        x2, v2 = np.zeros((self.N, 3, 2)), np.zeros((self.N, 3, 2))
+        d2 = np.zeros((self.N, 2 * self.p, 3, 2))
+        check(_capi.lib().mh_dd_sync(self._h, _ptr(t2), _ptr(x2), _ptr(v2), _ptr(d2)))
+        return t2, x2, v2, d2
+
+    def set_state(self, x, v, derivs=None, t2=None) -> None:
+        x2, v2 = _dd_host(x, self.N), _dd_host(v, self.N)
+        d2 = None if derivs is None else _dd_host(derivs, self.N, 2 * self.p * 3)
+        t2 = None if t2 is None else np.ascontiguousarray(t2, dtype=np.float64).reshape(2)
+        check(_capi.lib().mh_dd_set_state(self._h, None if t2 is None else _ptr(t2), _ptr(x2), _ptr(v2),
+                                          None if d2 is None else _ptr(d2)))
+
+    def diagnostics(self, central: int = 0):
+        """(E2, ecc2): the energy as a (2,) pair and the eccentricity vectors (N, 3, 2)."""
+        E2 = np.zeros(2)
+        e2 = np.zeros((self.N, 3, 2))
+        check(_capi.lib().mh_dd_diagnostics(self._h, _ptr(E2), _ptr(e2), int(central)))
+        return E2, e2
+
+    def counters(self) -> dict:
+        c = _capi.Counters()
+        check(_capi.lib().mh_dd_info(self._h, None, None, ctypes.byref(c)))
+        return {f: getattr(c, f) for f, _ in c._fields_ if f != "pair_tune_ms_x1000"}
 
 
 def _dev_ptr(t) -> int:

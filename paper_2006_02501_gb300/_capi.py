@@ -33,6 +33,8 @@ EXPORTS = [
     "mh_batch_energy", "mh_step_converge", "mh_set_predictor", "mh_collect_samples", "mh_mlp_create",
     "mh_mlp_destroy", "mh_mlp_num_params", "mh_mlp_get_params", "mh_mlp_set_params", "mh_mlp_forward",
     "mh_mlp_loss_grad", "mh_mlp_train", "mh_predict", "mh_step_timesym", "mh_measure_peaks",
+    "mh_dd_create", "mh_dd_destroy", "mh_dd_step", "mh_dd_sync", "mh_dd_set_state", "mh_dd_diagnostics",
+    "mh_dd_info",
 ]
 
 
@@ -119,8 +121,17 @@ def lib() -> ctypes.CDLL:
             L.mh_mlp_forward.argtypes = [P, P, P, I64, P]
             L.mh_mlp_loss_grad.argtypes = [P, P, P, I64, DP, FP, P]
             L.mh_mlp_train.argtypes = [P, P, P, I64, I, I, ctypes.c_float, U64, DP, P]
+            L.mh_dd_create.argtypes = [ctypes.POINTER(P), I64, I, DP, DP, DP, D, ctypes.POINTER(Config), P]
+            L.mh_dd_destroy.argtypes = [P]
+            L.mh_dd_destroy.restype = None
+            L.mh_dd_step.argtypes = [P, D, I, I64]
+            L.mh_dd_sync.argtypes = [P, DP, DP, DP, DP]
+            L.mh_dd_set_state.argtypes = [P, DP, DP, DP, DP]
+            L.mh_dd_diagnostics.argtypes = [P, DP, DP, I]
+            L.mh_dd_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(Counters)]
             for name in EXPORTS:
-                if name not in ("mh_destroy", "mh_config_default", "mh_last_error", "mh_mlp_destroy"):
+                if name not in ("mh_destroy", "mh_config_default", "mh_last_error", "mh_mlp_destroy",
+                                "mh_dd_destroy"):
                     getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib

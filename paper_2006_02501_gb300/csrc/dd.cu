@@ -1,0 +1,790 @@
+// Double-double form: the modified Hermite integrators of Dittmann (2020) with
+// every quantity and every operation in double-double arithmetic (dd.cuh, ~106
+// bits), for few-body systems whose 8th-order (and higher) integration reaches
+// the round-off of FP64 (Section 3.1, the 8th-order Kepler test; the
+// Discussion's case for high-order schemes with extended precision).
+//
+// One step is the P(EC)^n shared step of the FP64 form: Taylor predictor
+// (Section 3 intro), n times { O(N^2) evaluation of a^(0..p) (Section 3 intro),
+// corrector: velocity by Eq. 6, then position by Eq. 7 with beta of Eq. 20 },
+// then a^(p+1..2p-1) from the end-of-step Hermite interpolant (Eqs. 2-5).
+// The state x, v, the derivative stack, the predicted trajectory, the pair
+// terms and every sum are double-double; the corrector and interpolation
+// constants are formed to 106 bits from exact rationals (hermite_consts_dd.cuh).
+//
+// Layout in device memory (each double-double is a double2 {hi, lo}):
+//   x, v   N x 3          d   N x 2p x 3 (a^(0..2p-1))
+//   tr     N x (P+1) x 3  trajectory fed to an evaluation (x, v, a, a-dot, ...)
+//   part   S x N x (P+1) x 3  per-j-chunk partial sums, added by the consumer in
+//                         chunk order, so results do not depend on scheduling.
+// Kernels:
+//   k_dd_pair<P>      one i per thread over one j-chunk, j records staged in
+//                     shared memory; FP64-pipe bound (double-double costs about
+//                     20 FP64 operations per FP64 operation of the plain form).
+//   k_dd_pair_top2<P> the same sums for the initialisation pass P = 7,
+//                     keeping only the two orders such a pass stores.
+//   k_dd_predict<p>   one (body, component) per thread.
+//   k_dd_correct<p>   one (body, component) per thread: adds the S partial
+//                     sums, corrects, and on the last pass commits the step and
+//                     interpolates the higher derivatives.
+//   k_dd_init_*       the explicit initial derivatives in passes of two orders.
+//   k_dd_energy / k_dd_ecc   diagnostics (Appendix A) in double-double.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "dd.cuh"
+#include "hermite_consts_dd.cuh"
+#include "pair_math.cuh"
+
+namespace mh {
+
+namespace {
+
+constexpr int kDDThreads = 128;
+constexpr int kDDJTile = 32;
+constexpr int kDDTargetCtas = 152 * 8;   // evaluation grid: a few waves over the 152 SMs
+constexpr int kDDMinJ = 4;               // fewest j per chunk (bounds the partial-sum traffic)
+
+__device__ __forceinline__ dd ld2(const double2 *p)
+{
+    const double2 v = *p;
+    return dd(v.x, v.y);
+}
+
+__device__ __forceinline__ void st2(double2 *p, dd a) { *p = make_double2(a.hi, a.lo); }
+
+__device__ __forceinline__ dd dot3(const dd *a, const dd *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// 1/y for a double-double y: the double reciprocal of y.hi and one Newton step
+// with the residual 1 - y q formed in double-double.
+__device__ __forceinline__ dd dd_inv(dd y)
+{
+    const double q = __drcp_rn(y.hi);
+    const dd w = y * dd(q);
+    const double e = __dsub_rn(__dsub_rn(1.0, w.hi), w.lo);
+    return fast_two_sum(q, __dmul_rn(q, e));
+}
+
+// ---- constants (exact rationals to double-double) ----
+
+template <int p>
+struct DDTab;
+#define MH_DD_TAB(P, KV, KX, E1, E0)                                                                     \
+    template <>                                                                                          \
+    struct DDTab<P> {                                                                                    \
+        __device__ static dd kv(int k) { const ddc::Ratio r = KV(k); return dd_ratio(r.num, r.den); }     \
+        __device__ static dd kx(int b, int k) { const ddc::Ratio r = KX(b, k); return dd_ratio(r.num, r.den); } \
+        __device__ static dd e1(int n, int k) { const ddc::Ratio r = E1(n, k); return dd_ratio(r.num, r.den); } \
+        __device__ static dd e0(int n, int k) { const ddc::Ratio r = E0(n, k); return dd_ratio(r.num, r.den); } \
+    };
+__host__ __device__ constexpr ddc::Ratio no_ratio(int, int) { return ddc::Ratio{0, 1}; }
+MH_DD_TAB(1, ddc::kv1, ddc::kx1, no_ratio, no_ratio)
+MH_DD_TAB(2, ddc::kv2, ddc::kx2, ddc::e1_2, ddc::e0_2)
+MH_DD_TAB(3, ddc::kv3, ddc::kx3, ddc::e1_3, ddc::e0_3)
+MH_DD_TAB(4, ddc::kv4, ddc::kx4, ddc::e1_4, ddc::e0_4)
+#undef MH_DD_TAB
+
+__device__ __forceinline__ long long factorial_ll(int n)
+{
+    long long f = 1;
+    for (int i = 2; i <= n; ++i) f *= i;
+    return f;
+}
+
+// 1/n! to double-double (n <= 18 keeps n! below 2^53)
+__device__ __forceinline__ dd inv_fact_dd(int n) { return dd_ratio(1, factorial_ll(n)); }
+
+// ---- evaluation ----
+
+// part[split][i] = sum over j in chunk `split`, j != i, of the pair derivatives
+// a^(0..P) of body i (Section 3 intro).  Grid: (ceil(N / 128), S).
+template <int P>
+__global__ void __launch_bounds__(kDDThreads)
+k_dd_pair(const double2 *__restrict__ tr, const double *__restrict__ m, int N, double eps, double G,
+          int jchunk, double2 *__restrict__ part)
+{
+    constexpr int R = (P + 1) * 3;
+    __shared__ double2 sj[kDDJTile * R];
+    __shared__ double sm[kDDJTile];
+    const int i = blockIdx.x * kDDThreads + threadIdx.x;
+    const int j0 = blockIdx.y * jchunk;
+    const int j1 = min(N, j0 + jchunk);
+    const bool live = i < N;
+    const dd eps2 = two_prod(eps, eps);
+    dd acc[P + 1][3];
+#pragma unroll
+    for (int k = 0; k <= P; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[k][c] = dd(0.0);
+    for (int jt = j0; jt < j1; jt += kDDJTile) {
+        const int nt = min(kDDJTile, j1 - jt);
+        __syncthreads();
+        for (int q = threadIdx.x; q < nt * R; q += kDDThreads) sj[q] = tr[(size_t)jt * R + q];
+        for (int q = threadIdx.x; q < nt; q += kDDThreads) sm[q] = m[jt + q];
+        __syncthreads();
+        if (!live) continue;
+        for (int jj = 0; jj < nt; ++jj) {
+            if (jt + jj == i) continue;
+            dd r[P + 1][3];
+#pragma unroll
+            for (int k = 0; k <= P; ++k)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    r[k][c] = ld2(&sj[jj * R + k * 3 + c]) - ld2(&tr[(size_t)i * R + k * 3 + c]);
+            const dd s = eps2 + (r[0][0] * r[0][0] + r[0][1] * r[0][1] + r[0][2] * r[0][2]);
+            const dd y = rsqrt_dd(s);
+            const dd sinv = y * y;
+            const dd mS = two_prod(G, sm[jj]) * (sinv * y);
+            pair_derivs<P, dd>(r, mS, sinv, acc);
+        }
+    }
+    if (!live) return;
+    double2 *o = part + ((size_t)blockIdx.y * N + i) * R;
+#pragma unroll
+    for (int k = 0; k <= P; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) st2(&o[k * 3 + c], acc[k][c]);
+}
+
+// The initialisation pass with many derivatives (P = 7, the 10th-order start)
+// stores only a^(P-1) and a^(P) (the lower orders are known).
+// The full-record kernel above would hold r^(0..P), A^(0..P) and the sums of
+// every order per pair, far beyond the register file; this one keeps the
+// scalars q_k = s^(k)/s and tau_k (the same recursion as pair_terms in
+// pair_math.cuh), forms each r^(k) from shared memory when it is needed, and
+// runs the A recursion one component at a time:
+//   A^(n)_c = G m S r^(n)_c - sum_{k=1..n} C(n,k) tau_k A^(n-k)_c.
+template <int P>
+__global__ void __launch_bounds__(kDDThreads)
+k_dd_pair_top2(const double2 *__restrict__ tr, const double *__restrict__ m, int N, double eps, double G,
+               int jchunk, double2 *__restrict__ part)
+{
+    constexpr int R = (P + 1) * 3;
+    __shared__ double2 sj[kDDJTile * R];
+    __shared__ double sm[kDDJTile];
+    const int i = blockIdx.x * kDDThreads + threadIdx.x;
+    const int j0 = blockIdx.y * jchunk;
+    const int j1 = min(N, j0 + jchunk);
+    const bool live = i < N;
+    const dd eps2 = two_prod(eps, eps);
+    const double2 *ti = tr + (size_t)(live ? i : 0) * R;
+    dd acc[2][3];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[k][c] = dd(0.0);
+    for (int jt = j0; jt < j1; jt += kDDJTile) {
+        const int nt = min(kDDJTile, j1 - jt);
+        __syncthreads();
+        for (int q = threadIdx.x; q < nt * R; q += kDDThreads) sj[q] = tr[(size_t)jt * R + q];
+        for (int q = threadIdx.x; q < nt; q += kDDThreads) sm[q] = m[jt + q];
+        __syncthreads();
+        if (!live) continue;
+        for (int jj = 0; jj < nt; ++jj) {
+            if (jt + jj == i) continue;
+            const double2 *tj = sj + jj * R;
+            auto rk = [&](int k, int c) { return ld2(&tj[k * 3 + c]) - ld2(&ti[k * 3 + c]); };
+            auto rdot = [&](int a, int b) {
+                return rk(a, 0) * rk(b, 0) + rk(a, 1) * rk(b, 1) + rk(a, 2) * rk(b, 2);
+            };
+            const dd s = eps2 + rdot(0, 0);
+            const dd y = rsqrt_dd(s);
+            const dd sinv = y * y;
+            const dd mS = two_prod(G, sm[jj]) * (sinv * y);
+            dd q[P + 1], tau[P + 1];
+#pragma unroll
+            for (int k = 1; k <= P; ++k) {          // q_k = s^(k)/s, s^(k) = sum_j C(k,j) r^(j).r^(k-j)
+                dd sk = dd(0.0);
+#pragma unroll
+                for (int j = 0; 2 * j <= k; ++j)
+                    sk += dd((2 * j == k) ? binom(k, j) : 2.0 * binom(k, j)) * rdot(j, k - j);
+                q[k] = sk * sinv;
+            }
+            tau[0] = dd(1.0);
+#pragma unroll
+            for (int n = 1; n <= P; ++n) {
+                dd t = dd(1.5) * q[n];
+#pragma unroll
+                for (int j = 1; j <= n - 1; ++j) t += dd(1.5 * binom(n - 1, j - 1) - binom(n - 1, j)) * q[j] * tau[n - j];
+                tau[n] = t;
+            }
+#pragma unroll 1
+            for (int c = 0; c < 3; ++c) {
+                dd A[P + 1];
+#pragma unroll
+                for (int n = 0; n <= P; ++n) {
+                    dd a = mS * rk(n, c);
+#pragma unroll
+                    for (int k = 1; k <= n; ++k) a -= (dd(binom(n, k)) * tau[k]) * A[n - k];
+                    A[n] = a;
+                }
+                acc[0][c] += A[P - 1];
+                acc[1][c] += A[P];
+            }
+        }
+    }
+    if (!live) return;
+    double2 *o = part + ((size_t)blockIdx.y * N + i) * R;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        st2(&o[(P - 1) * 3 + c], acc[0][c]);
+        st2(&o[P * 3 + c], acc[1][c]);
+    }
+}
+
+// ---- predictor ----
+
+// Taylor series of x, v and a^(0..p-2) to t0 + dt (Section 3 intro, with every
+// derivative the step holds), written as the trajectory record of the first
+// evaluation.  One thread per (body, component).
+template <int p>
+__global__ void __launch_bounds__(kDDThreads)
+k_dd_predict(const double2 *__restrict__ x, const double2 *__restrict__ v, const double2 *__restrict__ d,
+             int N, double dt, double2 *__restrict__ tr)
+{
+    constexpr int K = 2 * p, R = (p + 1) * 3;
+    const int t = blockIdx.x * kDDThreads + threadIdx.x;
+    if (t >= 3 * N) return;
+    const int i = t / 3, c = t - 3 * i;
+    dd a[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) a[k] = ld2(&d[((size_t)i * K + k) * 3 + c]);
+    dd sx = dd(0.0), sv = dd(0.0);
+#pragma unroll
+    for (int k = K - 1; k >= 0; --k) {
+        sx = mul_d(sx, dt) + a[k] * inv_fact_dd(k + 2);
+        sv = mul_d(sv, dt) + a[k] * inv_fact_dd(k + 1);
+    }
+    const dd x0 = ld2(&x[(size_t)i * 3 + c]), v0 = ld2(&v[(size_t)i * 3 + c]);
+    double2 *o = tr + (size_t)i * R;
+    st2(&o[c], mul_d(mul_d(sx, dt) + v0, dt) + x0);
+    st2(&o[3 + c], mul_d(sv, dt) + v0);
+#pragma unroll
+    for (int q = 0; q + 2 <= p; ++q) {
+        dd sa = dd(0.0);
+#pragma unroll
+        for (int k = K - 1; k >= q; --k) sa = mul_d(sa, dt) + a[k] * inv_fact_dd(k - q);
+        st2(&o[(q + 2) * 3 + c], sa);
+    }
+}
+
+// ---- corrector ----
+
+// One correction pass (Eqs. 6, 7 in dt-power form: velocity first, then the
+// position with the new velocity).  a^(0..p) at t1 are the S partial sums added
+// in chunk order.  Not last: writes the next evaluation's trajectory record
+// (x1, v1 and a^(0..p-2) of this evaluation).  Last: commits x, v and
+// a^(0..p), and a^(p+1..2p-1) from the Hermite interpolant; flags a non-finite
+// state.
+template <int p, bool kLast>
+__global__ void __launch_bounds__(kDDThreads)
+k_dd_correct(double2 *__restrict__ x, double2 *__restrict__ v, double2 *__restrict__ d,
+             const double2 *__restrict__ part, int S, int N, double dt, int bm,
+             double2 *__restrict__ tr, int *__restrict__ flag)
+{
+    constexpr int K = 2 * p, R = (p + 1) * 3;
+    using Tab = DDTab<p>;
+    const int t = blockIdx.x * kDDThreads + threadIdx.x;
+    if (t >= 3 * N) return;
+    const int i = t / 3, c = t - 3 * i;
+    dd a1[p + 1], a0[p + 1];
+#pragma unroll
+    for (int k = 0; k <= p; ++k) {
+        dd s = dd(0.0);
+        for (int q = 0; q < S; ++q) s += ld2(&part[((size_t)q * N + i) * R + k * 3 + c]);
+        a1[k] = s;
+        a0[k] = ld2(&d[((size_t)i * K + k) * 3 + c]);
+    }
+    const dd x0 = ld2(&x[(size_t)i * 3 + c]), v0 = ld2(&v[(size_t)i * 3 + c]);
+    // velocity: sum_k kv(k) (a1^(k) + (-1)^k a0^(k)) dt^(k+1)
+    dd sv = dd(0.0);
+#pragma unroll
+    for (int k = p; k >= 0; --k) {
+        const dd f = (k & 1) ? a1[k] - a0[k] : a1[k] + a0[k];
+        sv = mul_d(sv, dt) + Tab::kv(k) * f;
+    }
+    const dd vn = mul_d(sv, dt) + v0;
+    // position: kx(0) (v1 + v0) dt + sum_{k>=1} kx(k) (a1^(k-1) +- a0^(k-1)) dt^(k+1)
+    dd sx = dd(0.0);
+#pragma unroll
+    for (int k = p + 1; k >= 1; --k) {
+        const dd f = (k & 1) ? a1[k - 1] - a0[k - 1] : a1[k - 1] + a0[k - 1];
+        sx = mul_d(sx, dt) + Tab::kx(bm, k) * f;
+    }
+    sx = mul_d(sx, dt) + Tab::kx(bm, 0) * (vn + v0);
+    const dd xn = mul_d(sx, dt) + x0;
+    if constexpr (!kLast) {
+        double2 *o = tr + (size_t)i * R;
+        st2(&o[c], xn);
+        st2(&o[3 + c], vn);
+#pragma unroll
+        for (int q = 0; q + 2 <= p; ++q) st2(&o[(q + 2) * 3 + c], a1[q]);
+    } else {
+        st2(&x[(size_t)i * 3 + c], xn);
+        st2(&v[(size_t)i * 3 + c], vn);
+        if (!dd_isfinite(xn) || !dd_isfinite(vn)) *flag = 1;
+#pragma unroll
+        for (int k = 0; k <= p; ++k) st2(&d[((size_t)i * K + k) * 3 + c], a1[k]);
+        if constexpr (p >= 2) {
+            // a^(n)(t1) = sum_k (e1(n,k) a1^(k) + e0(n,k) a0^(k)) dt^(k-n)
+            const dd rdt = dd_recip(dt);
+#pragma unroll
+            for (int n = p + 1; n < K; ++n) {
+                dd s = dd(0.0);
+#pragma unroll
+                for (int k = p; k >= 0; --k) s = mul_d(s, dt) + (Tab::e1(n, k) * a1[k] + Tab::e0(n, k) * a0[k]);
+#pragma unroll
+                for (int e = 0; e < n; ++e) s = s * rdt;
+                st2(&d[((size_t)i * K + n) * 3 + c], s);
+            }
+        }
+    }
+}
+
+// ---- initialisation (Section 3 intro) ----
+
+// Trajectory records x, v, a^(0..have-1) (R = have + 2 vectors per body).
+__global__ void k_dd_init_tr(const double2 *__restrict__ x, const double2 *__restrict__ v,
+                             const double2 *__restrict__ d, int N, int K, int have, double2 *__restrict__ tr)
+{
+    const int R = (have + 2) * 3;
+    const int64_t t = (int64_t)blockIdx.x * kDDThreads + threadIdx.x;
+    if (t >= (int64_t)N * R) return;
+    const int i = (int)(t / R), q = (int)(t - (int64_t)i * R);
+    const int k = q / 3, c = q - 3 * k;
+    tr[t] = k == 0 ? x[(size_t)i * 3 + c] : k == 1 ? v[(size_t)i * 3 + c] : d[((size_t)i * K + k - 2) * 3 + c];
+}
+
+// d[i][n] = sum over the S chunks, n = have .. min(P, K-1).
+__global__ void k_dd_init_store(const double2 *__restrict__ part, int S, int N, int P, int K, int have,
+                                double2 *__restrict__ d)
+{
+    const int R = (P + 1) * 3;
+    const int nn = min(P, K - 1) - have + 1;
+    const int64_t t = (int64_t)blockIdx.x * kDDThreads + threadIdx.x;
+    if (t >= (int64_t)N * nn * 3) return;
+    const int i = (int)(t / (nn * 3)), q = (int)(t - (int64_t)i * nn * 3);
+    const int n = have + q / 3, c = q % 3;
+    dd s = dd(0.0);
+    for (int u = 0; u < S; ++u) s += ld2(&part[((size_t)u * N + i) * R + n * 3 + c]);
+    st2(&d[((size_t)i * K + n) * 3 + c], s);
+}
+
+// ---- diagnostics (Appendix A) ----
+
+// Per-CTA partial energies: sum over the CTA's bodies i of m_i |v_i|^2 / 2 -
+// sum_{j > i} G m_i m_j / sqrt(r_ij^2 + eps^2), reduced by a fixed tree.
+__global__ void __launch_bounds__(kDDThreads)
+k_dd_energy(const double *__restrict__ m, const double2 *__restrict__ x, const double2 *__restrict__ v,
+            int N, double eps, double G, double2 *__restrict__ bpart)
+{
+    __shared__ double2 sh[kDDThreads];
+    const int i = blockIdx.x * kDDThreads + threadIdx.x;
+    dd e = dd(0.0);
+    if (i < N) {
+        dd xi[3], vi[3];
+        for (int c = 0; c < 3; ++c) { xi[c] = ld2(&x[(size_t)i * 3 + c]); vi[c] = ld2(&v[(size_t)i * 3 + c]); }
+        const dd eps2 = two_prod(eps, eps);
+        dd pot = dd(0.0);
+        for (int j = i + 1; j < N; ++j) {
+            dd r[3];
+            for (int c = 0; c < 3; ++c) r[c] = ld2(&x[(size_t)j * 3 + c]) - xi[c];
+            pot += dd(m[j]) * rsqrt_dd(eps2 + dot3(r, r));
+        }
+        e = mul_d(mul_d(dot3(vi, vi), m[i]), 0.5) - pot * two_prod(G, m[i]);
+    }
+    st2(&sh[threadIdx.x], e);
+    __syncthreads();
+    for (int s = kDDThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) st2(&sh[threadIdx.x], ld2(&sh[threadIdx.x]) + ld2(&sh[threadIdx.x + s]));
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) bpart[blockIdx.x] = sh[0];
+}
+
+__global__ void k_dd_sum(const double2 *__restrict__ bpart, int nb, double2 *__restrict__ out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    dd s = dd(0.0);
+    for (int b = 0; b < nb; ++b) s += ld2(&bpart[b]);
+    st2(out, s);
+}
+
+// Eccentricity vectors about body `central` (Eq. A1): mu e = (|v|^2 - mu/|r|) r
+// - (r.v) v with r, v relative to the central body and mu = G (m_c + m_i).
+__global__ void k_dd_ecc(const double *__restrict__ m, const double2 *__restrict__ x,
+                         const double2 *__restrict__ v, int N, double G, int central, double2 *__restrict__ e)
+{
+    const int i = blockIdx.x * kDDThreads + threadIdx.x;
+    if (i >= N) return;
+    if (i == central) {
+        for (int c = 0; c < 3; ++c) e[(size_t)i * 3 + c] = make_double2(0.0, 0.0);
+        return;
+    }
+    dd r[3], u[3];
+    for (int c = 0; c < 3; ++c) {
+        r[c] = ld2(&x[(size_t)i * 3 + c]) - ld2(&x[(size_t)central * 3 + c]);
+        u[c] = ld2(&v[(size_t)i * 3 + c]) - ld2(&v[(size_t)central * 3 + c]);
+    }
+    const dd mu = mul_d(two_sum(m[central], m[i]), G);
+    const dd w = dot3(u, u) - mu * rsqrt_dd(dot3(r, r));
+    const dd rv = dot3(r, u);
+    const dd rmu = dd_inv(mu);
+    for (int c = 0; c < 3; ++c) st2(&e[(size_t)i * 3 + c], (w * r[c] - rv * u[c]) * rmu);
+}
+
+// ---- launch helpers ----
+
+struct DDPlan {
+    int iblocks, S, jchunk;
+};
+
+DDPlan dd_plan(int N)
+{
+    DDPlan pl;
+    pl.iblocks = (N + kDDThreads - 1) / kDDThreads;
+    int S = std::max(1, std::min((N + kDDMinJ - 1) / kDDMinJ, kDDTargetCtas / pl.iblocks));
+    pl.jchunk = (N + S - 1) / S;
+    pl.S = (N + pl.jchunk - 1) / pl.jchunk;
+    return pl;
+}
+
+int launch_dd_pair(int P, const double2 *tr, const double *m, int N, double eps, double G, const DDPlan &pl,
+                   double2 *part, cudaStream_t st)
+{
+    const dim3 grid(pl.iblocks, pl.S);
+    switch (P) {
+        case 1: k_dd_pair<1><<<grid, kDDThreads, 0, st>>>(tr, m, N, eps, G, pl.jchunk, part); break;
+        case 2: k_dd_pair<2><<<grid, kDDThreads, 0, st>>>(tr, m, N, eps, G, pl.jchunk, part); break;
+        case 3: k_dd_pair<3><<<grid, kDDThreads, 0, st>>>(tr, m, N, eps, G, pl.jchunk, part); break;
+        case 4: k_dd_pair<4><<<grid, kDDThreads, 0, st>>>(tr, m, N, eps, G, pl.jchunk, part); break;
+        case 5: k_dd_pair<5><<<grid, kDDThreads, 0, st>>>(tr, m, N, eps, G, pl.jchunk, part); break;
+        case 7: k_dd_pair_top2<7><<<grid, kDDThreads, 0, st>>>(tr, m, N, eps, G, pl.jchunk, part); break;
+        default: set_error("double-double evaluation: unsupported derivative count"); return MH_EINVAL;
+    }
+    MH_LAUNCHED("k_dd_pair");
+    return MH_OK;
+}
+
+template <int p>
+int launch_dd_step_p(double2 *x, double2 *v, double2 *d, double2 *tr, double2 *part, const double *m, int N,
+                     double eps, double G, int bm, double dt, int n_iter, int *flag, cudaStream_t st)
+{
+    const DDPlan pl = dd_plan(N);
+    const int nb = (3 * N + kDDThreads - 1) / kDDThreads;
+    k_dd_predict<p><<<nb, kDDThreads, 0, st>>>(x, v, d, N, dt, tr);
+    MH_LAUNCHED("k_dd_predict");
+    for (int it = 0; it < n_iter; ++it) {
+        if (int rc = launch_dd_pair(p, tr, m, N, eps, G, pl, part, st)) return rc;
+        if (it + 1 < n_iter)
+            k_dd_correct<p, false><<<nb, kDDThreads, 0, st>>>(x, v, d, part, pl.S, N, dt, bm, tr, flag);
+        else
+            k_dd_correct<p, true><<<nb, kDDThreads, 0, st>>>(x, v, d, part, pl.S, N, dt, bm, tr, flag);
+        MH_LAUNCHED("k_dd_correct");
+    }
+    return MH_OK;
+}
+
+// host double-double add of a double (the simulation time)
+void host_add(double &hi, double &lo, double b)
+{
+    const double s = hi + b;
+    const double bv = s - hi;
+    const double t = (hi - (s - bv)) + (b - bv);
+    const double l = lo + t;
+    hi = s + l;
+    lo = l - (hi - s);
+}
+
+}  // namespace
+
+}  // namespace mh
+
+using namespace mh;
+
+struct mh_dd {
+    int64_t N = 0;
+    int p = 0, order = 0, bm = 0;
+    double eps = 0.0, G = 1.0;
+    double t_hi = 0.0, t_lo = 0.0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    double *m = nullptr;
+    double2 *x = nullptr, *v = nullptr, *d = nullptr, *tr = nullptr, *part = nullptr, *diag = nullptr;
+    int *flag = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    double graph_dt = 0.0;
+    int graph_n = 0;
+    mh_counters ctr{};
+};
+
+namespace {
+
+int dd_free(mh_dd *s)
+{
+    if (!s) return MH_OK;
+    if (s->graph) cudaGraphExecDestroy(s->graph);
+    cudaFree(s->m); cudaFree(s->x); cudaFree(s->v); cudaFree(s->d);
+    cudaFree(s->tr); cudaFree(s->part); cudaFree(s->diag); cudaFree(s->flag);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+    return MH_OK;
+}
+
+int dd_check(const mh_dd *s, const char *fn)
+{
+    if (!s) {
+        set_error(std::string(fn) + ": handle is NULL");
+        return MH_EINVAL;
+    }
+    return MH_OK;
+}
+
+int dd_initialise(mh_dd *s)
+{
+    const int N = (int)s->N, K = 2 * s->p;
+    const DDPlan pl = dd_plan(N);
+    for (int have = 0; have < K; have += 2) {
+        const int P = have + 1;
+        const int64_t nt = (int64_t)N * (have + 2) * 3;
+        k_dd_init_tr<<<(unsigned)((nt + kDDThreads - 1) / kDDThreads), kDDThreads, 0, s->stream>>>(
+            s->x, s->v, s->d, N, K, have, s->tr);
+        MH_LAUNCHED("k_dd_init_tr");
+        if (int rc = launch_dd_pair(P, s->tr, s->m, N, s->eps, s->G, pl, s->part, s->stream)) return rc;
+        const int nn = std::min(P, K - 1) - have + 1;
+        const int64_t ns = (int64_t)N * nn * 3;
+        k_dd_init_store<<<(unsigned)((ns + kDDThreads - 1) / kDDThreads), kDDThreads, 0, s->stream>>>(
+            s->part, pl.S, N, P, K, have, s->d);
+        MH_LAUNCHED("k_dd_init_store");
+        s->ctr.kernel_launches += 3;
+    }
+    return MH_OK;
+}
+
+int dd_step_once(mh_dd *s, double dt, int n_iter)
+{
+    const int N = (int)s->N;
+    switch (s->p) {
+        case 1: return launch_dd_step_p<1>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream);
+        case 2: return launch_dd_step_p<2>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream);
+        case 3: return launch_dd_step_p<3>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream);
+        case 4: return launch_dd_step_p<4>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream);
+        default: set_error("double-double step: unsupported order"); return MH_EINVAL;
+    }
+}
+
+int dd_check_flag(mh_dd *s)
+{
+    int flag = 0;
+    MH_CUDA(cudaMemcpyAsync(&flag, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    MH_CUDA(cudaStreamSynchronize(s->stream));
+    if (flag) {
+        set_error("non-finite position or velocity produced by a double-double step");
+        return MH_ENONFINITE;
+    }
+    return MH_OK;
+}
+
+bool finite_all(const double *a, size_t n)
+{
+    for (size_t q = 0; q < n; ++q)
+        if (!std::isfinite(a[q])) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mh_dd_create(mh_dd **out, int64_t N, int order, const double *m, const double *x2, const double *v2,
+                 double eps, const mh_config *cfg, void *stream)
+{
+    if (!out) { set_error("mh_dd_create: out is NULL"); return MH_EINVAL; }
+    *out = nullptr;
+    if (N < 1 || N > (1 << 24)) { set_error("mh_dd_create: N must be in [1, 2^24]"); return MH_EINVAL; }
+    if (order != 4 && order != 6 && order != 8 && order != 10) {
+        set_error(order == 12 ? "mh_dd_create: order 12 is not built in double-double (its start needs "
+                                "the P = 9 pair derivatives, whose double-double kernel is not built)"
+                              : "mh_dd_create: order must be 4, 6, 8 or 10");
+        return MH_EINVAL;
+    }
+    if (!m || !x2 || !v2) { set_error("mh_dd_create: m, x2 and v2 are required"); return MH_EINVAL; }
+    if (!(eps >= 0.0) || !std::isfinite(eps)) { set_error("mh_dd_create: eps must be finite and >= 0"); return MH_EINVAL; }
+    mh_config c;
+    mh_config_default(&c);
+    if (cfg) c = *cfg;
+    if (c.beta_mode != MH_BETA_MODIFIED && c.beta_mode != MH_BETA_STANDARD) {
+        set_error("mh_dd_create: beta_mode must be MH_BETA_MODIFIED or MH_BETA_STANDARD");
+        return MH_EINVAL;
+    }
+    if (!std::isfinite(c.G)) { set_error("mh_dd_create: G must be finite"); return MH_EINVAL; }
+    if (!finite_all(m, (size_t)N) || !finite_all(x2, (size_t)N * 6) || !finite_all(v2, (size_t)N * 6)) {
+        set_error("mh_dd_create: non-finite m, x or v");
+        return MH_ENONFINITE;
+    }
+    mh_dd *s = new mh_dd;
+    s->N = N;
+    s->order = order;
+    s->p = order / 2 - 1;
+    s->bm = c.beta_mode;
+    s->eps = eps;
+    s->G = c.G;
+    const int K = 2 * s->p;
+    const DDPlan pl = dd_plan((int)N);
+    const size_t R = (size_t)K * 3;      // widest trajectory record (initialisation, P + 1 <= 2p)
+    const int nb = (int)((N + kDDThreads - 1) / kDDThreads);
+    auto fail = [&](int rc) { dd_free(s); return rc; };
+    if (stream) {
+        s->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(cuda_fail(cudaGetLastError(), "cudaStreamCreate"));
+        s->own_stream = true;
+    }
+    if (cudaMalloc((void **)&s->m, N * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void **)&s->x, N * 3 * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc((void **)&s->v, N * 3 * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc((void **)&s->d, N * K * 3 * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc((void **)&s->tr, N * R * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc((void **)&s->part, (size_t)pl.S * N * R * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc((void **)&s->diag, (nb + 1) * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc((void **)&s->flag, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("mh_dd_create: device allocation failed");
+        return fail(MH_ENOMEM);
+    }
+    int rc = MH_OK;
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        if (!rc && cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+            rc = cuda_fail(cudaGetLastError(), "mh_dd_create: upload");
+    };
+    up(s->m, m, N * sizeof(double));
+    up(s->x, x2, N * 3 * sizeof(double2));
+    up(s->v, v2, N * 3 * sizeof(double2));
+    if (!rc && cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream) != cudaSuccess)
+        rc = cuda_fail(cudaGetLastError(), "mh_dd_create: memset");
+    if (!rc && cudaMemsetAsync(s->d, 0, N * K * 3 * sizeof(double2), s->stream) != cudaSuccess)
+        rc = cuda_fail(cudaGetLastError(), "mh_dd_create: memset");
+    if (!rc) rc = dd_initialise(s);
+    if (!rc && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "mh_dd_create");
+    if (rc) return fail(rc);
+    *out = s;
+    return MH_OK;
+}
+
+void mh_dd_destroy(mh_dd *sim)
+{
+    if (sim && sim->stream) cudaStreamSynchronize(sim->stream);
+    dd_free(sim);
+}
+
+int mh_dd_step(mh_dd *sim, double dt, int n_iter, int64_t nsteps)
+{
+    if (int rc = dd_check(sim, "mh_dd_step")) return rc;
+    if (!std::isfinite(dt) || dt == 0.0) { set_error("mh_dd_step: dt must be finite and non-zero"); return MH_EINVAL; }
+    if (n_iter < 1 || n_iter > 64) { set_error("mh_dd_step: n_iter must be in [1, 64]"); return MH_EINVAL; }
+    if (nsteps < 0) { set_error("mh_dd_step: nsteps must be >= 0"); return MH_EINVAL; }
+    if (nsteps == 0) return MH_OK;
+    const int launches = 1 + 2 * n_iter;
+    if (nsteps == 1) {
+        if (int rc = dd_step_once(sim, dt, n_iter)) return rc;
+    } else {
+        // one step captured as a CUDA graph, replayed nsteps times
+        if (!sim->graph || sim->graph_dt != dt || sim->graph_n != n_iter) {
+            if (sim->graph) { cudaGraphExecDestroy(sim->graph); sim->graph = nullptr; }
+            cudaGraph_t g = nullptr;
+            MH_CUDA(cudaStreamBeginCapture(sim->stream, cudaStreamCaptureModeThreadLocal));
+            int rc = dd_step_once(sim, dt, n_iter);
+            cudaError_t e = cudaStreamEndCapture(sim->stream, &g);
+            if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+            if (e != cudaSuccess) return cuda_fail(e, "mh_dd_step: graph capture");
+            e = cudaGraphInstantiate(&sim->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) { sim->graph = nullptr; return cuda_fail(e, "mh_dd_step: graph instantiate"); }
+            sim->graph_dt = dt;
+            sim->graph_n = n_iter;
+        }
+        for (int64_t k = 0; k < nsteps; ++k) MH_CUDA(cudaGraphLaunch(sim->graph, sim->stream));
+    }
+    for (int64_t k = 0; k < nsteps; ++k) host_add(sim->t_hi, sim->t_lo, dt);
+    sim->ctr.steps += nsteps;
+    sim->ctr.evaluations += nsteps * n_iter;
+    sim->ctr.pair_interactions += (double)nsteps * n_iter * (double)sim->N * (double)(sim->N - 1);
+    sim->ctr.particle_steps += (double)nsteps * (double)sim->N;
+    sim->ctr.kernel_launches += nsteps * launches;
+    return MH_OK;
+}
+
+int mh_dd_sync(mh_dd *sim, double *t2, double *x2, double *v2, double *d2)
+{
+    if (int rc = dd_check(sim, "mh_dd_sync")) return rc;
+    const size_t N = (size_t)sim->N, K = 2 * (size_t)sim->p;
+    if (x2) MH_CUDA(cudaMemcpyAsync(x2, sim->x, N * 3 * sizeof(double2), cudaMemcpyDeviceToHost, sim->stream));
+    if (v2) MH_CUDA(cudaMemcpyAsync(v2, sim->v, N * 3 * sizeof(double2), cudaMemcpyDeviceToHost, sim->stream));
+    if (d2) MH_CUDA(cudaMemcpyAsync(d2, sim->d, N * K * 3 * sizeof(double2), cudaMemcpyDeviceToHost, sim->stream));
+    if (int rc = dd_check_flag(sim)) return rc;
+    if (t2) { t2[0] = sim->t_hi; t2[1] = sim->t_lo; }
+    return MH_OK;
+}
+
+int mh_dd_set_state(mh_dd *sim, const double *t2, const double *x2, const double *v2, const double *d2)
+{
+    if (int rc = dd_check(sim, "mh_dd_set_state")) return rc;
+    if (!x2 || !v2) { set_error("mh_dd_set_state: x2 and v2 are required"); return MH_EINVAL; }
+    const size_t N = (size_t)sim->N, K = 2 * (size_t)sim->p;
+    if (!finite_all(x2, N * 6) || !finite_all(v2, N * 6) || (d2 && !finite_all(d2, N * K * 6))) {
+        set_error("mh_dd_set_state: non-finite state");
+        return MH_ENONFINITE;
+    }
+    MH_CUDA(cudaMemcpyAsync(sim->x, x2, N * 3 * sizeof(double2), cudaMemcpyHostToDevice, sim->stream));
+    MH_CUDA(cudaMemcpyAsync(sim->v, v2, N * 3 * sizeof(double2), cudaMemcpyHostToDevice, sim->stream));
+    MH_CUDA(cudaMemsetAsync(sim->flag, 0, sizeof(int), sim->stream));
+    if (d2) {
+        MH_CUDA(cudaMemcpyAsync(sim->d, d2, N * K * 3 * sizeof(double2), cudaMemcpyHostToDevice, sim->stream));
+    } else if (int rc = dd_initialise(sim)) {
+        return rc;
+    }
+    if (t2) { sim->t_hi = t2[0]; sim->t_lo = t2[1]; }
+    MH_CUDA(cudaStreamSynchronize(sim->stream));
+    return MH_OK;
+}
+
+int mh_dd_diagnostics(mh_dd *sim, double *energy2, double *ecc2, int central)
+{
+    if (int rc = dd_check(sim, "mh_dd_diagnostics")) return rc;
+    const int N = (int)sim->N;
+    if (ecc2 && (central < 0 || central >= N)) { set_error("mh_dd_diagnostics: central out of range"); return MH_EINVAL; }
+    const int nb = (N + kDDThreads - 1) / kDDThreads;
+    if (energy2) {
+        k_dd_energy<<<nb, kDDThreads, 0, sim->stream>>>(sim->m, sim->x, sim->v, N, sim->eps, sim->G, sim->diag);
+        MH_LAUNCHED("k_dd_energy");
+        k_dd_sum<<<1, 32, 0, sim->stream>>>(sim->diag, nb, sim->diag + nb);
+        MH_LAUNCHED("k_dd_sum");
+        MH_CUDA(cudaMemcpyAsync(energy2, sim->diag + nb, sizeof(double2), cudaMemcpyDeviceToHost, sim->stream));
+        sim->ctr.kernel_launches += 2;
+    }
+    if (ecc2) {
+        // the eccentricity vectors are staged in the trajectory buffer (N x 3 fits)
+        k_dd_ecc<<<nb, kDDThreads, 0, sim->stream>>>(sim->m, sim->x, sim->v, N, sim->G, central, sim->tr);
+        MH_LAUNCHED("k_dd_ecc");
+        MH_CUDA(cudaMemcpyAsync(ecc2, sim->tr, (size_t)N * 3 * sizeof(double2), cudaMemcpyDeviceToHost, sim->stream));
+        sim->ctr.kernel_launches += 1;
+    }
+    MH_CUDA(cudaStreamSynchronize(sim->stream));
+    return MH_OK;
+}
+
+int mh_dd_info(mh_dd *sim, int64_t *N, int *order, mh_counters *counters)
+{
+    if (int rc = dd_check(sim, "mh_dd_info")) return rc;
+    if (N) *N = sim->N;
+    if (order) *order = sim->order;
+    if (counters) *counters = sim->ctr;
+    return MH_OK;
+}
+
+}  // extern "C"

@@ -1,6 +1,8 @@
 """Derivation of the rational constants hard-coded in hermite_consts.cuh.
 
 Run:  python derive_constants.py      (needs sympy; prints the constants)
+      python derive_constants.py --dd-header   (writes hermite_consts_dd.cuh: the
+      same constants as exact numerator / denominator pairs)
 
 Method (independent of the quadrature-on-F+- route of Section 2): build the
 two-point Hermite interpolant of f on [t0, t1 = t0 + dt] in the monomial basis
@@ -75,7 +77,59 @@ PRINTED = {   # Section 2.1: Eq. 21 (p = 1), Eq. 22 (p = 2), Eq. 23 (p = 3), on 
 }
 
 
+def rational_tables():
+    """The constants of hermite_consts.cuh as exact rationals, p = 1 .. 5:
+    kv[p][k], kx[p][b][k] (b = 0 modified, 1 standard), e1[p][n][k], e0[p][n][k]."""
+    T = {"kv": {}, "kx": {}, "e1": {}, "e0": {}}
+    for p in range(1, 6):
+        T["kv"][p] = [sp.Rational(c) for c in integral_coeffs(p)[0]]
+        T["kx"][p] = [[sp.Rational(c) for c in modified_position_coeffs(p)[0]],
+                      [sp.Rational(c) for c in integral_coeffs(p + 1)[0]]]
+        d = end_derivs(p, range(p + 1, 2 * p)) if p >= 2 else {}
+        T["e1"][p] = {n: [sp.Rational(c) for c in d[n][0]] for n in d}
+        T["e0"][p] = {n: [sp.Rational(c) for c in d[n][1]] for n in d}
+    return T
+
+
+def dd_header() -> str:
+    """hermite_consts_dd.cuh: the same constants as numerator / denominator pairs,
+    from which the double-double kernels form each value to 106 bits."""
+    T = rational_tables()
+    pair = lambda r: "{%d, %d}" % (r.p, r.q)
+    fn = "__host__ __device__ constexpr Ratio"
+    L = ["// Rational constants of the modified Hermite corrector and end-of-step",
+         "// interpolation (the values of hermite_consts.cuh, same meaning: kv(k),",
+         "// kx(beta_mode, k), e1(n, k), e0(n, k) with n = p+1 .. 2p-1) as exact",
+         "// numerator / denominator pairs, p = 1 .. 5, for the double-double form.",
+         "// Written by `python derive_constants.py --dd-header`.",
+         "#pragma once", "", "namespace mh {", "namespace ddc {", "",
+         "struct Ratio { long long num, den; };", ""]
+    for p in range(1, 6):
+        L.append(f"// p = {p} (order {2 * p + 2})")
+        L.append(f"{fn} kv{p}(int k)")
+        L.append(f"{{ constexpr Ratio t[{p + 1}] = {{{', '.join(pair(r) for r in T['kv'][p])}}}; return t[k]; }}")
+        rows = ", ".join("{" + ", ".join(pair(r) for r in T["kx"][p][b]) + "}" for b in (0, 1))
+        L.append(f"{fn} kx{p}(int b, int k)")
+        L.append(f"{{ constexpr Ratio t[2][{p + 2}] = {{{rows}}}; return t[b][k]; }}")
+        if p >= 2:
+            for nm in ("e1", "e0"):
+                rows = ", ".join("{" + ", ".join(pair(r) for r in T[nm][p][n]) + "}"
+                                 for n in range(p + 1, 2 * p))
+                L.append(f"{fn} {nm}_{p}(int n, int k)")
+                L.append(f"{{ constexpr Ratio t[{p - 1}][{p + 1}] = {{{rows}}}; return t[n - {p + 1}][k]; }}")
+        L.append("")
+    L += ["}  // namespace ddc", "}  // namespace mh", ""]
+    return "\n".join(L)
+
+
 if __name__ == "__main__":
+    import sys
+    if "--dd-header" in sys.argv:
+        import os
+        out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "hermite_consts_dd.cuh")
+        open(out, "w").write(dd_header())
+        print(out)
+        sys.exit(0)
     for p in (1, 2, 3):
         c1, c0 = modified_position_coeffs(p)
         assert c1 == PRINTED[p], (p, c1)

@@ -50,3 +50,23 @@ def kepler_traj(m, x, v, P, central=0):
     if P >= 3:
         out[:, 3] = j
     return out
+
+
+def dd_diff(a2, b2):
+    """(a_hi + a_lo) - (b_hi + b_lo) for double-double arrays (..., 2), keeping
+    the low words: the high words' difference is exact when they are within a
+    factor of two of each other (Sterbenz), which holds wherever the values agree."""
+    a2, b2 = np.asarray(a2), np.asarray(b2)
+    return (a2[..., 0] - b2[..., 0]) + (a2[..., 1] - b2[..., 1])
+
+
+def dd_scaled_stack_err(got2, ref2, dt):
+    """scaled_stack_err for double-double stacks (N, K, 3, 2)."""
+    ref = np.asarray(ref2)[..., 0] + np.asarray(ref2)[..., 1]
+    d = dd_diff(got2, ref2)
+    K = ref.shape[1]
+    h = abs(dt) / 2
+    sc = np.array([h ** k / factorial(k) for k in range(K)])[None, :, None]
+    per = np.linalg.norm(d * sc, axis=-1).max(axis=1)
+    scale = np.linalg.norm(ref * sc, axis=-1).max(axis=1)
+    return float((per / np.maximum(scale, 1e-300)).max())
