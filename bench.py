@@ -70,6 +70,18 @@ TRAFFIC = {"files": ["paper_2006_02501_gb300/csrc/pair_sym.cu", "paper_2006_0250
            "bytes_per_launch": 56.26e6 + 1.61e9}
 
 
+# FP64 instructions per pair interaction of the double-double evaluation kernel
+# k_dd_pair<3>, from one ncu capture (profiles/), valid while its source is
+# the one captured.
+DD_INSTR = {"files": ["paper_2006_02501_gb300/csrc/dd.cu", "paper_2006_02501_gb300/csrc/dd.cuh"],
+            "sha256": ["35d7d70f1b4749e934d42849c13462dadf3b9494eb156506c6fc858751fff82f",
+                       "fc820299535e960effdf3d75b248976e124a70606f221bffac1d8e3395d01bd7"],
+            # profiles/k_dd_pair_disc_N4096_order8.md: 30.19e9 FP64 thread instructions
+            # for 4097 x 4096 ordered pairs
+            "fp64_thread_instr_per_pair": 1799.0}
+FP64_LANE_INSTR_PER_S = N_SM * 2 * SM_MAX_MHZ * 1e6
+
+
 def _sha(path):
     with open(os.path.join(ROOT, path), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()
@@ -371,6 +383,40 @@ def run_ours(args, rank, world, local_rank):
     batch_pairs = float((sizes * (sizes - 1)).sum()) * 2 * 10000
     batch_ps = (g1["particle_steps"] - g0["particle_steps"]) / tb
 
+    # ---- double-double form: the same disc cut to 4096 stars (8th order), and a
+    # 65-body planetesimal ring at 10th order (the few-body regime it is for) ----
+    from paper_2006_02501_gb300 import inputs as _inp2
+    dd_out = {}
+    for tag, (dm, dx, dv), d_order, d_eps, d_steps in (
+            ("disc4096_order8", _inp2.smbh_disc(seed=2, N=4095), 8, EPS, 3),
+            ("ring65_order10", _inp2.planetesimal_ring(seed=1, n=64, m=1e-9), 10, 0.0, 50)):
+        dN = len(dm)
+        with mh.DDSimulation(d_order, dm, dx, dv, d_eps, stream=stream) as dsim:
+            dsim.step(DT, N_ITER, nsteps=2)
+            dsim.sync()
+            q0 = dsim.counters()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dsim.step(DT, N_ITER, nsteps=d_steps)
+            e1.record(stream)
+            e1.synchronize()
+            q1 = dsim.counters()
+        dms = reduce_max(e0.elapsed_time(e1), world)
+        dd_out[tag] = {"bodies": dN, "order": d_order, "steps": d_steps, "ms_per_step": dms / d_steps,
+                       "pair_interactions_per_s": world * d_steps * N_ITER * dN * (dN - 1) / (dms * 1e-3),
+                       "particle_steps_per_s": world * d_steps * dN / (dms * 1e-3),
+                       "gpu_launches": q1["kernel_launches"] - q0["kernel_launches"]}
+    dd_pair_rate = dd_out["disc4096_order8"]["pair_interactions_per_s"] / world
+    dd_src = all(_sha(f) == h for f, h in zip(DD_INSTR["files"], DD_INSTR["sha256"]))
+    dd_instr = DD_INSTR["fp64_thread_instr_per_pair"] if dd_src else None
+    dd_out["pair_kernel"] = "k_dd_pair<3>"
+    dd_out["fp64_thread_instr_per_pair"] = dd_instr
+    dd_out["fp64_pipe_frac"] = (dd_pair_rate * dd_instr / FP64_LANE_INSTR_PER_S) if dd_instr else None
+    dd_out["fp64_pipe_frac_basis"] = ("pair-interactions/s of the 4096-body step x FP64 thread "
+                                      "instructions per pair (ncu, profiles/) / (152 SMs x 2 FP64 lanes "
+                                      "x 2070 MHz); null once dd.cu or dd.cuh changes")
+
     peaks = mh.measure_peaks()       # measured ALU rates of this GPU, reported beside the unit-count peaks
     if rank != 0:
         return
@@ -416,6 +462,7 @@ def run_ours(args, rank, world, local_rank):
             "value": world * kp * units / (elp * 1e-3), "unit": UNIT, "ms_per_step": elp / kp, "steps": kp,
             "pair_kernel": "k_pair_fp32x2<3>", "launch_ms": pairp_ms, "achieved_tflops": achp / 1e12,
             "peak_tflops": PEAK_FP32 / 1e12, "frac": achp / PEAK_FP32, "flops_per_pair": FLOPS_PER_PAIR[ORDER]},
+            "double_double": dd_out,
             "batched": {
             "workload": "4096 planetary systems (3..64 bodies), 6th order FP64, P(EC)^2, dt_s = P_min/128, "
                         "10^4 steps in one launch",

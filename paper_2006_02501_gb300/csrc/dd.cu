@@ -34,6 +34,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "dd.cuh"
@@ -95,8 +96,46 @@ __device__ __forceinline__ long long factorial_ll(int n)
     return f;
 }
 
-// 1/n! to double-double (n <= 18 keeps n! below 2^53)
-__device__ __forceinline__ dd inv_fact_dd(int n) { return dd_ratio(1, factorial_ll(n)); }
+// The constants of every order, formed once per process by k_dd_consts (each
+// a division pair, so forming them per thread would put ~50 FP64 divisions on
+// every predictor and corrector thread) and read with warp-uniform indices.
+constexpr int kDDMaxP = 4;
+struct DDConsts {
+    double2 kv[kDDMaxP + 1][kDDMaxP + 2];                 // [p][k]
+    double2 kx[kDDMaxP + 1][2][kDDMaxP + 3];              // [p][beta_mode][k]
+    double2 e1[kDDMaxP + 1][kDDMaxP][kDDMaxP + 2];        // [p][n - p - 1][k]
+    double2 e0[kDDMaxP + 1][kDDMaxP][kDDMaxP + 2];
+    double2 inv_fact[2 * kDDMaxP + 4];                   // 1/n!
+};
+__constant__ DDConsts c_ddc;
+__device__ DDConsts g_ddc_stage;
+
+template <int p>
+__device__ void fill_consts(DDConsts &t)
+{
+    using Tab = DDTab<p>;
+    for (int k = 0; k <= p; ++k) st2(&t.kv[p][k], Tab::kv(k));
+    for (int b = 0; b < 2; ++b)
+        for (int k = 0; k <= p + 1; ++k) st2(&t.kx[p][b][k], Tab::kx(b, k));
+    for (int n = p + 1; n < 2 * p; ++n)
+        for (int k = 0; k <= p; ++k) {
+            st2(&t.e1[p][n - p - 1][k], Tab::e1(n, k));
+            st2(&t.e0[p][n - p - 1][k], Tab::e0(n, k));
+        }
+}
+
+__global__ void k_dd_consts()
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    fill_consts<1>(g_ddc_stage);
+    fill_consts<2>(g_ddc_stage);
+    fill_consts<3>(g_ddc_stage);
+    fill_consts<4>(g_ddc_stage);
+    for (int n = 0; n < 2 * kDDMaxP + 4; ++n) st2(&g_ddc_stage.inv_fact[n], dd_ratio(1, factorial_ll(n)));
+}
+
+__device__ __forceinline__ dd cget(const double2 &c) { return dd(c.x, c.y); }
+__device__ __forceinline__ dd inv_fact_dd(int n) { return cget(c_ddc.inv_fact[n]); }
 
 // ---- evaluation ----
 
@@ -287,7 +326,6 @@ k_dd_correct(double2 *__restrict__ x, double2 *__restrict__ v, double2 *__restri
              double2 *__restrict__ tr, int *__restrict__ flag)
 {
     constexpr int K = 2 * p, R = (p + 1) * 3;
-    using Tab = DDTab<p>;
     const int t = blockIdx.x * kDDThreads + threadIdx.x;
     if (t >= 3 * N) return;
     const int i = t / 3, c = t - 3 * i;
@@ -305,7 +343,7 @@ k_dd_correct(double2 *__restrict__ x, double2 *__restrict__ v, double2 *__restri
 #pragma unroll
     for (int k = p; k >= 0; --k) {
         const dd f = (k & 1) ? a1[k] - a0[k] : a1[k] + a0[k];
-        sv = mul_d(sv, dt) + Tab::kv(k) * f;
+        sv = mul_d(sv, dt) + cget(c_ddc.kv[p][k]) * f;
     }
     const dd vn = mul_d(sv, dt) + v0;
     // position: kx(0) (v1 + v0) dt + sum_{k>=1} kx(k) (a1^(k-1) +- a0^(k-1)) dt^(k+1)
@@ -313,9 +351,9 @@ k_dd_correct(double2 *__restrict__ x, double2 *__restrict__ v, double2 *__restri
 #pragma unroll
     for (int k = p + 1; k >= 1; --k) {
         const dd f = (k & 1) ? a1[k - 1] - a0[k - 1] : a1[k - 1] + a0[k - 1];
-        sx = mul_d(sx, dt) + Tab::kx(bm, k) * f;
+        sx = mul_d(sx, dt) + cget(c_ddc.kx[p][bm][k]) * f;
     }
-    sx = mul_d(sx, dt) + Tab::kx(bm, 0) * (vn + v0);
+    sx = mul_d(sx, dt) + cget(c_ddc.kx[p][bm][0]) * (vn + v0);
     const dd xn = mul_d(sx, dt) + x0;
     if constexpr (!kLast) {
         double2 *o = tr + (size_t)i * R;
@@ -336,7 +374,8 @@ k_dd_correct(double2 *__restrict__ x, double2 *__restrict__ v, double2 *__restri
             for (int n = p + 1; n < K; ++n) {
                 dd s = dd(0.0);
 #pragma unroll
-                for (int k = p; k >= 0; --k) s = mul_d(s, dt) + (Tab::e1(n, k) * a1[k] + Tab::e0(n, k) * a0[k]);
+                for (int k = p; k >= 0; --k)
+                    s = mul_d(s, dt) + (cget(c_ddc.e1[p][n - p - 1][k]) * a1[k] + cget(c_ddc.e0[p][n - p - 1][k]) * a0[k]);
 #pragma unroll
                 for (int e = 0; e < n; ++e) s = s * rdt;
                 st2(&d[((size_t)i * K + n) * 3 + c], s);
@@ -544,6 +583,24 @@ int dd_check(const mh_dd *s, const char *fn)
     return MH_OK;
 }
 
+// Forms the constant table (k_dd_consts) and copies it to constant memory, once
+// per process.
+int dd_consts_once(cudaStream_t st)
+{
+    static std::mutex mu;
+    static bool done = false;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done) return MH_OK;
+    k_dd_consts<<<1, 32, 0, st>>>();
+    MH_LAUNCHED("k_dd_consts");
+    void *stage = nullptr;
+    MH_CUDA(cudaGetSymbolAddress(&stage, g_ddc_stage));
+    MH_CUDA(cudaMemcpyToSymbolAsync(c_ddc, stage, sizeof(DDConsts), 0, cudaMemcpyDeviceToDevice, st));
+    MH_CUDA(cudaStreamSynchronize(st));
+    done = true;
+    return MH_OK;
+}
+
 int dd_initialise(mh_dd *s)
 {
     const int N = (int)s->N, K = 2 * s->p;
@@ -669,6 +726,7 @@ int mh_dd_create(mh_dd **out, int64_t N, int order, const double *m, const doubl
         rc = cuda_fail(cudaGetLastError(), "mh_dd_create: memset");
     if (!rc && cudaMemsetAsync(s->d, 0, N * K * 3 * sizeof(double2), s->stream) != cudaSuccess)
         rc = cuda_fail(cudaGetLastError(), "mh_dd_create: memset");
+    if (!rc) rc = dd_consts_once(s->stream);
     if (!rc) rc = dd_initialise(s);
     if (!rc && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "mh_dd_create");
     if (rc) return fail(rc);

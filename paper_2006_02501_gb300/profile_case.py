@@ -8,6 +8,8 @@ initialisation launches one evaluation per pass (p passes), so a profiler that
 wants the first step's evaluation skips those.  FP64 evaluations use the
 pair-symmetric kernel (k_pair_fp64_sym) for P <= 3 unless --ordered is given;
 the 8th-order initialisation's last pass (P = 5) always runs k_pair_fp64.
+--precision dd runs the double-double form (mh_dd_*) on the same disc; its
+initialisation also launches one evaluation (k_dd_pair) per pass.
 """
 import argparse
 import os
@@ -19,7 +21,7 @@ import numpy as np
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--N", type=int, default=16384)
-    ap.add_argument("--precision", choices=["fp64", "fp32pair"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "fp32pair", "dd"], default="fp64")
     ap.add_argument("--order", type=int, default=8)
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--n-iter", type=int, default=3)
@@ -31,6 +33,13 @@ def main():
     from paper_2006_02501_gb300 import inputs
     mh.build_library()
     m, x, v = inputs.smbh_disc(seed=2, N=a.N)
+    if a.precision == "dd":
+        with mh.DDSimulation(a.order, m, x, v, 1e-4) as sim:
+            sim.step(2 * np.pi * 1e-3, a.n_iter, nsteps=a.steps)
+            t2, x2, v2, d2 = sim.sync()
+        print(f"ok N={len(m)} dd order {a.order} steps {a.steps} t={t2[0]:.6f} "
+              f"finite={bool(np.isfinite(x2).all())}")
+        return
     prec = mh.MH_PREC_FP64 if a.precision == "fp64" else mh.MH_PREC_FP32PAIR
     with mh.Simulation(a.order, m, x, v, 1e-4, precision=prec, symmetric=not a.ordered) as sim:
         sim.step(2 * np.pi * 1e-3, a.n_iter, nsteps=a.steps)
