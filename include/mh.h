@@ -238,8 +238,7 @@ int mh_batch_energy(mh_sim *sim, double *energy);
 typedef struct mh_dd mh_dd;
 
 /* Create a double-double simulation of N bodies (1 <= N <= 2^24) of order 4, 6,
- * 8 or 10 (order 12 is refused with MH_EINVAL: its start needs the P = 9 pair
- * derivatives, whose double-double kernel is not built).  m: N masses; x2, v2: N x 3 x 2 positions and velocities (a
+ * 8, 10 or 12.  m: N masses; x2, v2: N x 3 x 2 positions and velocities (a
  * plain double state has lo = 0); eps >= 0; cfg: NULL for defaults, only
  * beta_mode and G are read; stream as for mh_create.  Computes a^(0..2p-1) at
  * t = 0 by explicit pair derivatives in double-double (Section 3 intro).  On

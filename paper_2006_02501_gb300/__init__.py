@@ -320,7 +320,7 @@ class DDSimulation:
     """One system integrated in double-double arithmetic (mh_dd_*): the state,
     the prediction, every pair term and every sum carry ~106 bits, so that the
     high-order schemes can be run below the round-off of FP64 (Section 3.1;
-    Discussion).  Shared constant steps, orders 4 to 10.
+    Discussion).  Shared constant steps, orders 4 to 12.
 
     x, v: (N, 3) doubles or (N, 3, 2) (hi, lo) pairs.  Results come back as
     (..., 2) pairs; value = hi + lo.

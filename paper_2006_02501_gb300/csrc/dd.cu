@@ -21,7 +21,7 @@
 //   k_dd_pair<P>      one i per thread over one j-chunk, j records staged in
 //                     shared memory; FP64-pipe bound (double-double costs about
 //                     20 FP64 operations per FP64 operation of the plain form).
-//   k_dd_pair_top2<P> the same sums for the initialisation pass P = 7,
+//   k_dd_pair_top2<P> the same sums for the initialisation passes P = 7, 9,
 //                     keeping only the two orders such a pass stores.
 //   k_dd_predict<p>   one (body, component) per thread.
 //   k_dd_correct<p>   one (body, component) per thread: adds the S partial
@@ -87,6 +87,7 @@ MH_DD_TAB(1, ddc::kv1, ddc::kx1, no_ratio, no_ratio)
 MH_DD_TAB(2, ddc::kv2, ddc::kx2, ddc::e1_2, ddc::e0_2)
 MH_DD_TAB(3, ddc::kv3, ddc::kx3, ddc::e1_3, ddc::e0_3)
 MH_DD_TAB(4, ddc::kv4, ddc::kx4, ddc::e1_4, ddc::e0_4)
+MH_DD_TAB(5, ddc::kv5, ddc::kx5, ddc::e1_5, ddc::e0_5)
 #undef MH_DD_TAB
 
 __device__ __forceinline__ long long factorial_ll(int n)
@@ -99,7 +100,7 @@ __device__ __forceinline__ long long factorial_ll(int n)
 // The constants of every order, formed once per process by k_dd_consts (each
 // a division pair, so forming them per thread would put ~50 FP64 divisions on
 // every predictor and corrector thread) and read with warp-uniform indices.
-constexpr int kDDMaxP = 4;
+constexpr int kDDMaxP = 5;
 struct DDConsts {
     double2 kv[kDDMaxP + 1][kDDMaxP + 2];                 // [p][k]
     double2 kx[kDDMaxP + 1][2][kDDMaxP + 3];              // [p][beta_mode][k]
@@ -131,6 +132,7 @@ __global__ void k_dd_consts()
     fill_consts<2>(g_ddc_stage);
     fill_consts<3>(g_ddc_stage);
     fill_consts<4>(g_ddc_stage);
+    fill_consts<5>(g_ddc_stage);
     for (int n = 0; n < 2 * kDDMaxP + 4; ++n) st2(&g_ddc_stage.inv_fact[n], dd_ratio(1, factorial_ll(n)));
 }
 
@@ -189,8 +191,8 @@ k_dd_pair(const double2 *__restrict__ tr, const double *__restrict__ m, int N, d
         for (int c = 0; c < 3; ++c) st2(&o[k * 3 + c], acc[k][c]);
 }
 
-// The initialisation pass with many derivatives (P = 7, the 10th-order start)
-// stores only a^(P-1) and a^(P) (the lower orders are known).
+// The initialisation passes with many derivatives (P = 7, 9: the 10th- and
+// 12th-order starts) store only a^(P-1) and a^(P) (the lower orders are known).
 // The full-record kernel above would hold r^(0..P), A^(0..P) and the sums of
 // every order per pair, far beyond the register file; this one keeps the
 // scalars q_k = s^(k)/s and tau_k (the same recursion as pair_terms in
@@ -503,6 +505,7 @@ int launch_dd_pair(int P, const double2 *tr, const double *m, int N, double eps,
         case 4: k_dd_pair<4><<<grid, kDDThreads, 0, st>>>(tr, m, N, eps, G, pl.jchunk, part); break;
         case 5: k_dd_pair<5><<<grid, kDDThreads, 0, st>>>(tr, m, N, eps, G, pl.jchunk, part); break;
         case 7: k_dd_pair_top2<7><<<grid, kDDThreads, 0, st>>>(tr, m, N, eps, G, pl.jchunk, part); break;
+        case 9: k_dd_pair_top2<9><<<grid, kDDThreads, 0, st>>>(tr, m, N, eps, G, pl.jchunk, part); break;
         default: set_error("double-double evaluation: unsupported derivative count"); return MH_EINVAL;
     }
     MH_LAUNCHED("k_dd_pair");
@@ -630,6 +633,7 @@ int dd_step_once(mh_dd *s, double dt, int n_iter)
         case 2: return launch_dd_step_p<2>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream);
         case 3: return launch_dd_step_p<3>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream);
         case 4: return launch_dd_step_p<4>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream);
+        case 5: return launch_dd_step_p<5>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream);
         default: set_error("double-double step: unsupported order"); return MH_EINVAL;
     }
 }
@@ -663,10 +667,8 @@ int mh_dd_create(mh_dd **out, int64_t N, int order, const double *m, const doubl
     if (!out) { set_error("mh_dd_create: out is NULL"); return MH_EINVAL; }
     *out = nullptr;
     if (N < 1 || N > (1 << 24)) { set_error("mh_dd_create: N must be in [1, 2^24]"); return MH_EINVAL; }
-    if (order != 4 && order != 6 && order != 8 && order != 10) {
-        set_error(order == 12 ? "mh_dd_create: order 12 is not built in double-double (its start needs "
-                                "the P = 9 pair derivatives, whose double-double kernel is not built)"
-                              : "mh_dd_create: order must be 4, 6, 8 or 10");
+    if (order != 4 && order != 6 && order != 8 && order != 10 && order != 12) {
+        set_error("mh_dd_create: order must be 4, 6, 8, 10 or 12");
         return MH_EINVAL;
     }
     if (!m || !x2 || !v2) { set_error("mh_dd_create: m, x2 and v2 are required"); return MH_EINVAL; }

@@ -258,15 +258,24 @@ template <> __host__ __device__ constexpr double e0<5>(int n, int k)
     return 0.0;
 }
 
-// Binomial coefficient as a compile-time constant.
+// Binomial coefficient C(n, k) (exact: after step i the product is C(n-k+i, i)).
+// Written as a loop, not a recursion: where a call is not folded at compile
+// time it must not become a recursive device function, whose stack depth the
+// compiler cannot bound.
 __host__ __device__ constexpr double binom(int n, int k)
 {
-    return (k < 0 || k > n) ? 0.0 : (k == 0 || k == n) ? 1.0 : binom(n - 1, k - 1) + binom(n - 1, k);
+    if (k < 0 || k > n) return 0.0;
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
 }
 
+// 1/n!, divided out in the order 1/2, /3, ..., /n.
 __host__ __device__ constexpr double inv_fact(int n)
 {
-    return n <= 1 ? 1.0 : inv_fact(n - 1) / n;
+    double r = 1.0;
+    for (int i = 2; i <= n; ++i) r /= i;
+    return r;
 }
 
 }  // namespace mh

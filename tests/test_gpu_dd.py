@@ -39,7 +39,7 @@ def _rel(got2, ref2):
     return float(np.abs(dd_diff(got2, ref2)).max() / np.abs(ref).max())
 
 
-@pytest.mark.parametrize("order", [4, 6, 8, 10])
+@pytest.mark.parametrize("order", [4, 6, 8, 10, 12])
 def test_dd_initialisation_parity(mh, orc, order):
     m, x, v, pmin = _planets()
     dt = pmin / 64
@@ -51,7 +51,7 @@ def test_dd_initialisation_parity(mh, orc, order):
     assert err < 1e-27, err
 
 
-@pytest.mark.parametrize("order", [4, 6, 8, 10])
+@pytest.mark.parametrize("order", [4, 6, 8, 10, 12])
 @pytest.mark.parametrize("modified", [True, False])
 def test_dd_steps_parity(mh, orc, order, modified):
     m, x, v, pmin = _planets()
@@ -95,11 +95,12 @@ def test_dd_single_body(mh, orc):
     assert _rel(x2, xr) < 1e-30
 
 
-def test_dd_kepler_pair(mh, orc):
-    """Two bodies: the Kepler pair of Section 3.1 at 10th order."""
+@pytest.mark.parametrize("order", [10, 12])
+def test_dd_kepler_pair(mh, orc, order):
+    """Two bodies: the Kepler pair of Section 3.1 at 10th and 12th order."""
     m, x, v = I.kepler_pair(a=1.0, e=0.1, M=1.0, m=1e-3)
-    xr, vr, _ = orc.dd_run(10, m, x, v, 0.0, 2.0 ** -4, 3, 20)
-    with mh.DDSimulation(10, m, x, v, 0.0) as sim:
+    xr, vr, _ = orc.dd_run(order, m, x, v, 0.0, 2.0 ** -4, 3, 20)
+    with mh.DDSimulation(order, m, x, v, 0.0) as sim:
         sim.step(2.0 ** -4, 3, nsteps=20)
         _, x2, v2, _ = sim.sync()
     assert _rel(x2, xr) < 1e-27 and _rel(v2, vr) < 1e-27
@@ -146,15 +147,17 @@ def test_dd_set_state_round_trip(mh):
             assert np.array_equal(qa, qb)
 
 
-def test_dd_section31_energy_below_fp64(mh, orc):
-    """a = 1, e = 0.1, dt = 2^-4, n = 3, ten orbits: the 10th-order double-double
-    run keeps the energy error below 1e-17, the FP64 form's stays at round-off."""
+@pytest.mark.parametrize("order,bound", [(10, 1e-17), (12, 1e-21)])
+def test_dd_section31_energy_below_fp64(mh, orc, order, bound):
+    """a = 1, e = 0.1, dt = 2^-4, n = 3, ten orbits: the 10th- and 12th-order
+    double-double runs keep the energy error below 1e-17 and 1e-21 (the binary128
+    oracle gives 9e-19 and 2.5e-22), the FP64 form's stays at round-off."""
     m, x, v = I.kepler_pair(a=1.0, e=0.1, M=1.0, m=1e-3)
     dt = 2.0 ** -4
     from fractions import Fraction
     val = lambda E2: Fraction(float(E2[0])) + Fraction(float(E2[1]))
     worst, worst64 = 0.0, 0.0
-    with mh.DDSimulation(10, m, x, v, 0.0) as sim, mh.Simulation(10, m, x, v, 0.0) as ref:
+    with mh.DDSimulation(order, m, x, v, 0.0) as sim, mh.Simulation(order, m, x, v, 0.0) as ref:
         E0 = val(sim.diagnostics()[0])
         E0f = ref.diagnostics(central=0)[0]
         for _ in range(20):
@@ -163,16 +166,16 @@ def test_dd_section31_energy_below_fp64(mh, orc):
             worst = max(worst, float(abs((val(sim.diagnostics()[0]) - E0) / E0)))
             worst64 = max(worst64, abs(ref.diagnostics(central=0)[0] / E0f - 1))
         _, x2, v2, _ = sim.sync()
-    assert worst < 1e-17, worst
+    assert worst < bound, worst
     assert worst64 > 3e-16 and worst < worst64 / 1e3, (worst, worst64)
-    xr, vr, _ = orc.dd_run(10, m, x, v, 0.0, dt, 3, 1000)
+    xr, vr, _ = orc.dd_run(order, m, x, v, 0.0, dt, 3, 1000)
     assert _rel(x2, xr) < 1e-25 and _rel(v2, vr) < 1e-25
 
 
 def test_dd_argument_errors(mh):
     from paper_2006_02501_gb300 import _capi
     m, x, v, pmin = _planets()
-    for order in (7, 12):
+    for order in (2, 7, 14):
         with pytest.raises(mh.MHError) as e:
             mh.DDSimulation(order, m, x, v, 0.0)
         assert e.value.code == _capi.MH_EINVAL
