@@ -71,10 +71,10 @@ TRAFFIC = {"files": ["paper_2006_02501_gb300/csrc/pair_sym.cu", "paper_2006_0250
 
 
 # FP64 instructions per pair interaction of the double-double evaluation kernel
-# k_dd_pair<3>, from one ncu capture (profiles/), valid while its source is
+# k_dd_pair<3, false>, from one ncu capture (profiles/), valid while its source is
 # the one captured.
 DD_INSTR = {"files": ["paper_2006_02501_gb300/csrc/dd.cu", "paper_2006_02501_gb300/csrc/dd.cuh"],
-            "sha256": ["35d7d70f1b4749e934d42849c13462dadf3b9494eb156506c6fc858751fff82f",
+            "sha256": ["3f25358f26b2b05f48ec2f31fb14dee2c5aedcade09c2db4f52a809b1c623def",
                        "fc820299535e960effdf3d75b248976e124a70606f221bffac1d8e3395d01bd7"],
             # profiles/k_dd_pair_disc_N4096_order8.md: 30.19e9 FP64 thread instructions
             # for 4097 x 4096 ordered pairs
@@ -407,10 +407,33 @@ def run_ours(args, rank, world, local_rank):
                        "pair_interactions_per_s": world * d_steps * N_ITER * dN * (dN - 1) / (dms * 1e-3),
                        "particle_steps_per_s": world * d_steps * dN / (dms * 1e-3),
                        "gpu_launches": q1["kernel_launches"] - q0["kernel_launches"]}
+    # batched double-double: the 4096 planetary systems of the batched form, 6th order
+    from paper_2006_02501_gb300 import inputs as _inp3
+    boff, bbm, bbx, bbv, bpmin = _inp3.planetary_systems(seed=4, S=4096)
+    with mh.DDBatch(6, boff, bbm, bbx, bbv, bpmin / 128.0, 1e-8, stream=stream) as db:
+        db.step(2, 2)
+        db.sync()
+        r0 = db.counters()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        db.step(20, 2)
+        e1.record(stream)
+        e1.synchronize()
+        r1 = db.counters()
+    bms = reduce_max(e0.elapsed_time(e1), world)
+    bsz = np.diff(boff)
+    dd_out["batched4096_order6"] = {
+        "workload": "the batched form's 4096 planetary systems (3..64 bodies), 6th order, P(EC)^2, "
+                    "dt_s = P_min/128, 20 steps replayed from a CUDA graph",
+        "ms_per_step": bms / 20,
+        "particle_steps_per_s": world * 20 * int(boff[-1]) / (bms * 1e-3),
+        "pair_interactions_per_s": world * 20 * 2 * float((bsz * (bsz - 1)).sum()) / (bms * 1e-3),
+        "gpu_launches": r1["kernel_launches"] - r0["kernel_launches"]}
     dd_pair_rate = dd_out["disc4096_order8"]["pair_interactions_per_s"] / world
     dd_src = all(_sha(f) == h for f, h in zip(DD_INSTR["files"], DD_INSTR["sha256"]))
     dd_instr = DD_INSTR["fp64_thread_instr_per_pair"] if dd_src else None
-    dd_out["pair_kernel"] = "k_dd_pair<3>"
+    dd_out["pair_kernel"] = "k_dd_pair<3, false>"
     dd_out["fp64_thread_instr_per_pair"] = dd_instr
     dd_out["fp64_pipe_frac"] = (dd_pair_rate * dd_instr / FP64_LANE_INSTR_PER_S) if dd_instr else None
     dd_out["fp64_pipe_frac_basis"] = ("pair-interactions/s of the 4096-body step x FP64 thread "

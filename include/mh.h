@@ -275,6 +275,25 @@ int mh_dd_diagnostics(mh_dd *sim, double *energy2, double *ecc2, int central);
 /* Size, order and counters of a double-double simulation (outputs may be NULL). */
 int mh_dd_info(mh_dd *sim, int64_t *N, int *order, mh_counters *counters);
 
+/* Batched double-double form: S independent systems of 1 to 64 bodies each,
+ * advanced together with shared steps of each system's own dt, one CTA per
+ * system per evaluation.  offsets: S+1 body offsets (offsets[0] = 0); m, x2, v2:
+ * the systems' bodies back to back (offsets[S] <= 2^24 bodies, x2 and v2 as for
+ * mh_dd_create); dt: S non-zero steps; eps, order, cfg, stream as for
+ * mh_dd_create.  mh_dd_sync and mh_dd_set_state see the concatenated bodies,
+ * with t2 = (number of steps taken, 0); mh_dd_step and mh_dd_diagnostics are
+ * rejected (use mh_dd_step_batch, mh_dd_batch_energy). */
+int mh_dd_create_batch(mh_dd **out, int64_t S, const int64_t *offsets, const double *m, const double *x2,
+                       const double *v2, const double *dt, double eps, int order, const mh_config *cfg,
+                       void *stream);
+
+/* nsteps >= 0 steps of every system, P(EC)^n_iter each (1 <= n_iter <= 64);
+ * more than one step is replayed from a CUDA graph of one step.  Stream-ordered. */
+int mh_dd_step_batch(mh_dd *sim, int64_t nsteps, int n_iter);
+
+/* The energy of every system as S (hi, lo) pairs (double-double; waits). */
+int mh_dd_batch_energy(mh_dd *sim, double *energy2);
+
 /* ------------------------------------------------------------------------- */
 /* Convergence-controlled stepping and the learned predictor residual.        */
 /* The paper has no learned component; it iterates P(EC)^n (Section 2.1, end)  */

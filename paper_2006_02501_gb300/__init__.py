@@ -20,7 +20,7 @@ from . import _capi
 from ._capi import (MH_BETA_MODIFIED, MH_BETA_STANDARD, MH_PREC_FP32PAIR, MH_PREC_FP64,  # noqa: F401
                     MHError, check)
 
-__all__ = ["Simulation", "Batch", "DDSimulation", "MLP", "pair_eval", "MHError", "build_library", "MH_PREC_FP64", "MH_PREC_FP32PAIR",
+__all__ = ["Simulation", "Batch", "DDSimulation", "DDBatch", "MLP", "pair_eval", "MHError", "build_library", "MH_PREC_FP64", "MH_PREC_FP32PAIR",
            "MH_BETA_MODIFIED", "MH_BETA_STANDARD"]
 
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -383,6 +383,44 @@ class DDSimulation:
         c = _capi.Counters()
         check(_capi.lib().mh_dd_info(self._h, None, None, ctypes.byref(c)))
         return {f: getattr(c, f) for f, _ in c._fields_ if f != "pair_tune_ms_x1000"}
+
+
+class DDBatch(DDSimulation):
+    """Many independent systems (1..64 bodies each) in double-double, advanced
+    together with shared steps of each system's own dt (mh_dd_create_batch).
+
+    offsets: (S+1,) int64 body offsets; m, x, v: the concatenated bodies (x, v as
+    doubles or (hi, lo) pairs); dt: (S,) steps.
+    """
+
+    def __init__(self, order: int, offsets, m, x, v, dt, eps: float, beta: int = MH_BETA_MODIFIED,
+                 G: float = 1.0, stream=None):
+        L = _capi.lib()
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        S = offsets.shape[0] - 1
+        m = _host(m)
+        N = m.shape[0]
+        x2, v2 = _dd_host(x, N), _dd_host(v, N)
+        dt = _host(dt, (S,))
+        cfg = _capi.Config()
+        L.mh_config_default(ctypes.byref(cfg))
+        cfg.order, cfg.beta_mode, cfg.G = order, beta, G
+        h = ctypes.c_void_p()
+        check(L.mh_dd_create_batch(ctypes.byref(h), S, offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                   _ptr(m), _ptr(x2), _ptr(v2), _ptr(dt), float(eps), order,
+                                   ctypes.byref(cfg), _stream_handle(stream)))
+        self._h = h
+        self.S, self.N, self.order, self.p = S, N, order, order // 2 - 1
+        self.offsets = offsets
+
+    def step(self, nsteps: int, n_iter: int) -> None:          # noqa: D401 (batched signature)
+        check(_capi.lib().mh_dd_step_batch(self._h, int(nsteps), int(n_iter)))
+
+    def energies(self) -> np.ndarray:
+        """(S, 2) energies of the systems as (hi, lo) pairs."""
+        e = np.zeros((self.S, 2))
+        check(_capi.lib().mh_dd_batch_energy(self._h, _ptr(e)))
+        return e
 
 
 def _dev_ptr(t) -> int:

@@ -18,10 +18,11 @@
 //   part   S x N x (P+1) x 3  per-j-chunk partial sums, added by the consumer in
 //                         chunk order, so results do not depend on scheduling.
 // Kernels:
-//   k_dd_pair<P>      one i per thread over one j-chunk, j records staged in
-//                     shared memory; FP64-pipe bound (double-double costs about
-//                     20 FP64 operations per FP64 operation of the plain form).
-//   k_dd_pair_top2<P> the same sums for the initialisation passes P = 7, 9,
+//   k_dd_pair<P, false>  one i per thread over one j-chunk, j records staged
+//                     in shared memory; FP64-pipe bound (double-double costs
+//                     about 20 FP64 operations per FP64 operation of the plain
+//                     form).
+//   k_dd_pair<P, true>   the same sums for the initialisation passes P = 7, 9,
 //                     keeping only the two orders such a pass stores.
 //   k_dd_predict<p>   one (body, component) per thread.
 //   k_dd_correct<p>   one (body, component) per thread: adds the S partial
@@ -29,12 +30,18 @@
 //                     interpolates the higher derivatives.
 //   k_dd_init_*       the explicit initial derivatives in passes of two orders.
 //   k_dd_energy / k_dd_ecc   diagnostics (Appendix A) in double-double.
+// Batched form (mh_dd_create_batch): many independent systems of up to 64
+// bodies, each with its own dt.  k_dd_pair_sys gives system s one CTA holding
+// its records in shared memory; the predictor and corrector read each body's
+// dt through its system index; k_dd_energy_sys reduces each system's energy.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <string>
+#include <vector>
 
 #include "common.cuh"
 #include "dd.cuh"
@@ -49,6 +56,7 @@ constexpr int kDDThreads = 128;
 constexpr int kDDJTile = 32;
 constexpr int kDDTargetCtas = 152 * 8;   // evaluation grid: a few waves over the 152 SMs
 constexpr int kDDMinJ = 4;               // fewest j per chunk (bounds the partial-sum traffic)
+constexpr int kDDSysMax = 64;            // batched form: bodies per system (one CTA each)
 
 __device__ __forceinline__ dd ld2(const double2 *p)
 {
@@ -141,9 +149,101 @@ __device__ __forceinline__ dd inv_fact_dd(int n) { return cget(c_ddc.inv_fact[n]
 
 // ---- evaluation ----
 
-// part[split][i] = sum over j in chunk `split`, j != i, of the pair derivatives
-// a^(0..P) of body i (Section 3 intro).  Grid: (ceil(N / 128), S).
+// One pair's a^(0..P) of body i due to body j (Section 3 intro), added to acc:
+// ti, tj the trajectory records x, v, a, ... (P + 1 vectors) of i and j.
 template <int P>
+__device__ __forceinline__ void dd_pair_full(const double2 *tj, const double2 *ti, double mj, dd eps2,
+                                             double G, dd (&acc)[P + 1][3])
+{
+    dd r[P + 1][3];
+#pragma unroll
+    for (int k = 0; k <= P; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r[k][c] = ld2(&tj[k * 3 + c]) - ld2(&ti[k * 3 + c]);
+    const dd s = eps2 + (r[0][0] * r[0][0] + r[0][1] * r[0][1] + r[0][2] * r[0][2]);
+    const dd y = rsqrt_dd(s);
+    const dd sinv = y * y;
+    const dd mS = two_prod(G, mj) * (sinv * y);
+    pair_derivs<P, dd>(r, mS, sinv, acc);
+}
+
+// The initialisation passes with many derivatives (P = 7, 9: the 10th- and
+// 12th-order starts) store only a^(P-1) and a^(P) (the lower orders are known).
+// Holding r^(0..P), A^(0..P) and the sums of every order per pair would go far
+// beyond the register file, so this form keeps the scalars q_k = s^(k)/s and
+// tau_k (the recursion of pair_terms in pair_math.cuh), forms each r^(k) from
+// the records when it is needed, and runs the A recursion one component at a
+// time:  A^(n)_c = G m S r^(n)_c - sum_{k=1..n} C(n,k) tau_k A^(n-k)_c.
+template <int P>
+__device__ __forceinline__ void dd_pair_top2(const double2 *tj, const double2 *ti, double mj, dd eps2,
+                                             double G, dd (&acc)[2][3])
+{
+    auto rk = [&](int k, int c) { return ld2(&tj[k * 3 + c]) - ld2(&ti[k * 3 + c]); };
+    auto rdot = [&](int a, int b) { return rk(a, 0) * rk(b, 0) + rk(a, 1) * rk(b, 1) + rk(a, 2) * rk(b, 2); };
+    const dd s = eps2 + rdot(0, 0);
+    const dd y = rsqrt_dd(s);
+    const dd sinv = y * y;
+    const dd mS = two_prod(G, mj) * (sinv * y);
+    dd q[P + 1], tau[P + 1];
+#pragma unroll
+    for (int k = 1; k <= P; ++k) {          // q_k = s^(k)/s, s^(k) = sum_j C(k,j) r^(j).r^(k-j)
+        dd sk = dd(0.0);
+#pragma unroll
+        for (int j = 0; 2 * j <= k; ++j) sk += dd((2 * j == k) ? binom(k, j) : 2.0 * binom(k, j)) * rdot(j, k - j);
+        q[k] = sk * sinv;
+    }
+    tau[0] = dd(1.0);
+#pragma unroll
+    for (int n = 1; n <= P; ++n) {
+        dd t = dd(1.5) * q[n];
+#pragma unroll
+        for (int j = 1; j <= n - 1; ++j) t += dd(1.5 * binom(n - 1, j - 1) - binom(n - 1, j)) * q[j] * tau[n - j];
+        tau[n] = t;
+    }
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        dd A[P + 1];
+#pragma unroll
+        for (int n = 0; n <= P; ++n) {
+            dd a = mS * rk(n, c);
+#pragma unroll
+            for (int k = 1; k <= n; ++k) a -= (dd(binom(n, k)) * tau[k]) * A[n - k];
+            A[n] = a;
+        }
+        acc[0][c] += A[P - 1];
+        acc[1][c] += A[P];
+    }
+}
+
+// Sums of either form for body i over the records sj[0..n) (skipping jself),
+// written to o: all orders, or (kTop2) orders P-1 and P at their places.
+template <int P, bool kTop2>
+__device__ __forceinline__ void dd_pair_sum(const double2 *sj, const double *smj, int n, int jself,
+                                            const double2 *ti, dd eps2, double G, dd (&acc)[kTop2 ? 2 : P + 1][3])
+{
+    constexpr int R = (P + 1) * 3;
+    for (int jj = 0; jj < n; ++jj) {
+        if (jj == jself) continue;
+        if constexpr (kTop2)
+            dd_pair_top2<P>(sj + jj * R, ti, smj[jj], eps2, G, acc);
+        else
+            dd_pair_full<P>(sj + jj * R, ti, smj[jj], eps2, G, acc);
+    }
+}
+
+template <int P, bool kTop2>
+__device__ __forceinline__ void dd_store_sums(double2 *o, const dd (&acc)[kTop2 ? 2 : P + 1][3])
+{
+    constexpr int K0 = kTop2 ? P - 1 : 0;
+#pragma unroll
+    for (int k = 0; k < (kTop2 ? 2 : P + 1); ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) st2(&o[(K0 + k) * 3 + c], acc[k][c]);
+}
+
+// One system: part[split][i] = sum over j in chunk `split`, j != i.  Grid:
+// (ceil(N / 128), S); j records staged in shared memory 32 at a time.
+template <int P, bool kTop2>
 __global__ void __launch_bounds__(kDDThreads)
 k_dd_pair(const double2 *__restrict__ tr, const double *__restrict__ m, int N, double eps, double G,
           int jchunk, double2 *__restrict__ part)
@@ -156,9 +256,10 @@ k_dd_pair(const double2 *__restrict__ tr, const double *__restrict__ m, int N, d
     const int j1 = min(N, j0 + jchunk);
     const bool live = i < N;
     const dd eps2 = two_prod(eps, eps);
-    dd acc[P + 1][3];
+    const double2 *ti = tr + (size_t)(live ? i : 0) * R;
+    dd acc[kTop2 ? 2 : P + 1][3];
 #pragma unroll
-    for (int k = 0; k <= P; ++k)
+    for (int k = 0; k < (kTop2 ? 2 : P + 1); ++k)
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[k][c] = dd(0.0);
     for (int jt = j0; jt < j1; jt += kDDJTile) {
@@ -167,114 +268,37 @@ k_dd_pair(const double2 *__restrict__ tr, const double *__restrict__ m, int N, d
         for (int q = threadIdx.x; q < nt * R; q += kDDThreads) sj[q] = tr[(size_t)jt * R + q];
         for (int q = threadIdx.x; q < nt; q += kDDThreads) sm[q] = m[jt + q];
         __syncthreads();
-        if (!live) continue;
-        for (int jj = 0; jj < nt; ++jj) {
-            if (jt + jj == i) continue;
-            dd r[P + 1][3];
-#pragma unroll
-            for (int k = 0; k <= P; ++k)
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    r[k][c] = ld2(&sj[jj * R + k * 3 + c]) - ld2(&tr[(size_t)i * R + k * 3 + c]);
-            const dd s = eps2 + (r[0][0] * r[0][0] + r[0][1] * r[0][1] + r[0][2] * r[0][2]);
-            const dd y = rsqrt_dd(s);
-            const dd sinv = y * y;
-            const dd mS = two_prod(G, sm[jj]) * (sinv * y);
-            pair_derivs<P, dd>(r, mS, sinv, acc);
-        }
+        if (live) dd_pair_sum<P, kTop2>(sj, sm, nt, i - jt, ti, eps2, G, acc);
     }
-    if (!live) return;
-    double2 *o = part + ((size_t)blockIdx.y * N + i) * R;
-#pragma unroll
-    for (int k = 0; k <= P; ++k)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) st2(&o[k * 3 + c], acc[k][c]);
+    if (live) dd_store_sums<P, kTop2>(part + ((size_t)blockIdx.y * N + i) * R, acc);
 }
 
-// The initialisation passes with many derivatives (P = 7, 9: the 10th- and
-// 12th-order starts) store only a^(P-1) and a^(P) (the lower orders are known).
-// The full-record kernel above would hold r^(0..P), A^(0..P) and the sums of
-// every order per pair, far beyond the register file; this one keeps the
-// scalars q_k = s^(k)/s and tau_k (the same recursion as pair_terms in
-// pair_math.cuh), forms each r^(k) from shared memory when it is needed, and
-// runs the A recursion one component at a time:
-//   A^(n)_c = G m S r^(n)_c - sum_{k=1..n} C(n,k) tau_k A^(n-k)_c.
-template <int P>
-__global__ void __launch_bounds__(kDDThreads)
-k_dd_pair_top2(const double2 *__restrict__ tr, const double *__restrict__ m, int N, double eps, double G,
-               int jchunk, double2 *__restrict__ part)
+// Many independent systems (batched form): CTA s holds system s (at most
+// kDDSysMax bodies, records off[s] .. off[s+1]-1) in shared memory; thread t
+// sums body off[s] + t over the system, into a single partial-sum slot.
+template <int P, bool kTop2>
+__global__ void __launch_bounds__(kDDSysMax)
+k_dd_pair_sys(const double2 *__restrict__ tr, const double *__restrict__ m, const int64_t *__restrict__ off,
+              double eps, double G, double2 *__restrict__ part)
 {
     constexpr int R = (P + 1) * 3;
-    __shared__ double2 sj[kDDJTile * R];
-    __shared__ double sm[kDDJTile];
-    const int i = blockIdx.x * kDDThreads + threadIdx.x;
-    const int j0 = blockIdx.y * jchunk;
-    const int j1 = min(N, j0 + jchunk);
-    const bool live = i < N;
+    __shared__ double2 sj[kDDSysMax * R];
+    __shared__ double sm[kDDSysMax];
+    const int64_t b0 = off[blockIdx.x];
+    const int n = (int)(off[blockIdx.x + 1] - b0);
+    for (int q = threadIdx.x; q < n * R; q += kDDSysMax) sj[q] = tr[(size_t)b0 * R + q];
+    for (int q = threadIdx.x; q < n; q += kDDSysMax) sm[q] = m[b0 + q];
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t >= n) return;
     const dd eps2 = two_prod(eps, eps);
-    const double2 *ti = tr + (size_t)(live ? i : 0) * R;
-    dd acc[2][3];
+    dd acc[kTop2 ? 2 : P + 1][3];
 #pragma unroll
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < (kTop2 ? 2 : P + 1); ++k)
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[k][c] = dd(0.0);
-    for (int jt = j0; jt < j1; jt += kDDJTile) {
-        const int nt = min(kDDJTile, j1 - jt);
-        __syncthreads();
-        for (int q = threadIdx.x; q < nt * R; q += kDDThreads) sj[q] = tr[(size_t)jt * R + q];
-        for (int q = threadIdx.x; q < nt; q += kDDThreads) sm[q] = m[jt + q];
-        __syncthreads();
-        if (!live) continue;
-        for (int jj = 0; jj < nt; ++jj) {
-            if (jt + jj == i) continue;
-            const double2 *tj = sj + jj * R;
-            auto rk = [&](int k, int c) { return ld2(&tj[k * 3 + c]) - ld2(&ti[k * 3 + c]); };
-            auto rdot = [&](int a, int b) {
-                return rk(a, 0) * rk(b, 0) + rk(a, 1) * rk(b, 1) + rk(a, 2) * rk(b, 2);
-            };
-            const dd s = eps2 + rdot(0, 0);
-            const dd y = rsqrt_dd(s);
-            const dd sinv = y * y;
-            const dd mS = two_prod(G, sm[jj]) * (sinv * y);
-            dd q[P + 1], tau[P + 1];
-#pragma unroll
-            for (int k = 1; k <= P; ++k) {          // q_k = s^(k)/s, s^(k) = sum_j C(k,j) r^(j).r^(k-j)
-                dd sk = dd(0.0);
-#pragma unroll
-                for (int j = 0; 2 * j <= k; ++j)
-                    sk += dd((2 * j == k) ? binom(k, j) : 2.0 * binom(k, j)) * rdot(j, k - j);
-                q[k] = sk * sinv;
-            }
-            tau[0] = dd(1.0);
-#pragma unroll
-            for (int n = 1; n <= P; ++n) {
-                dd t = dd(1.5) * q[n];
-#pragma unroll
-                for (int j = 1; j <= n - 1; ++j) t += dd(1.5 * binom(n - 1, j - 1) - binom(n - 1, j)) * q[j] * tau[n - j];
-                tau[n] = t;
-            }
-#pragma unroll 1
-            for (int c = 0; c < 3; ++c) {
-                dd A[P + 1];
-#pragma unroll
-                for (int n = 0; n <= P; ++n) {
-                    dd a = mS * rk(n, c);
-#pragma unroll
-                    for (int k = 1; k <= n; ++k) a -= (dd(binom(n, k)) * tau[k]) * A[n - k];
-                    A[n] = a;
-                }
-                acc[0][c] += A[P - 1];
-                acc[1][c] += A[P];
-            }
-        }
-    }
-    if (!live) return;
-    double2 *o = part + ((size_t)blockIdx.y * N + i) * R;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        st2(&o[(P - 1) * 3 + c], acc[0][c]);
-        st2(&o[P * 3 + c], acc[1][c]);
-    }
+    dd_pair_sum<P, kTop2>(sj, sm, n, t, sj + t * R, eps2, G, acc);
+    dd_store_sums<P, kTop2>(part + (size_t)(b0 + t) * R, acc);
 }
 
 // ---- predictor ----
@@ -285,12 +309,14 @@ k_dd_pair_top2(const double2 *__restrict__ tr, const double *__restrict__ m, int
 template <int p>
 __global__ void __launch_bounds__(kDDThreads)
 k_dd_predict(const double2 *__restrict__ x, const double2 *__restrict__ v, const double2 *__restrict__ d,
-             int N, double dt, double2 *__restrict__ tr)
+             int N, double dt0, const double *__restrict__ dts, const int *__restrict__ sys,
+             double2 *__restrict__ tr)
 {
     constexpr int K = 2 * p, R = (p + 1) * 3;
     const int t = blockIdx.x * kDDThreads + threadIdx.x;
     if (t >= 3 * N) return;
     const int i = t / 3, c = t - 3 * i;
+    const double dt = dts ? dts[sys[i]] : dt0;      // batched form: each system its own step
     dd a[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) a[k] = ld2(&d[((size_t)i * K + k) * 3 + c]);
@@ -324,13 +350,14 @@ k_dd_predict(const double2 *__restrict__ x, const double2 *__restrict__ v, const
 template <int p, bool kLast>
 __global__ void __launch_bounds__(kDDThreads)
 k_dd_correct(double2 *__restrict__ x, double2 *__restrict__ v, double2 *__restrict__ d,
-             const double2 *__restrict__ part, int S, int N, double dt, int bm,
-             double2 *__restrict__ tr, int *__restrict__ flag)
+             const double2 *__restrict__ part, int S, int N, double dt0, const double *__restrict__ dts,
+             const int *__restrict__ sys, int bm, double2 *__restrict__ tr, int *__restrict__ flag)
 {
     constexpr int K = 2 * p, R = (p + 1) * 3;
     const int t = blockIdx.x * kDDThreads + threadIdx.x;
     if (t >= 3 * N) return;
     const int i = t / 3, c = t - 3 * i;
+    const double dt = dts ? dts[sys[i]] : dt0;
     dd a1[p + 1], a0[p + 1];
 #pragma unroll
     for (int k = 0; k <= p; ++k) {
@@ -447,6 +474,39 @@ k_dd_energy(const double *__restrict__ m, const double2 *__restrict__ x, const d
     if (threadIdx.x == 0) bpart[blockIdx.x] = sh[0];
 }
 
+// Batched form: the energy of system s (CTA s), reduced over its bodies by a
+// fixed tree.
+__global__ void __launch_bounds__(kDDSysMax)
+k_dd_energy_sys(const double *__restrict__ m, const double2 *__restrict__ x, const double2 *__restrict__ v,
+                const int64_t *__restrict__ off, double eps, double G, double2 *__restrict__ out)
+{
+    __shared__ double2 sh[kDDSysMax];
+    const int64_t b0 = off[blockIdx.x];
+    const int n = (int)(off[blockIdx.x + 1] - b0);
+    const int t = threadIdx.x;
+    dd e = dd(0.0);
+    if (t < n) {
+        const int64_t i = b0 + t;
+        dd xi[3], vi[3];
+        for (int c = 0; c < 3; ++c) { xi[c] = ld2(&x[i * 3 + c]); vi[c] = ld2(&v[i * 3 + c]); }
+        const dd eps2 = two_prod(eps, eps);
+        dd pot = dd(0.0);
+        for (int64_t j = i + 1; j < b0 + n; ++j) {
+            dd r[3];
+            for (int c = 0; c < 3; ++c) r[c] = ld2(&x[j * 3 + c]) - xi[c];
+            pot += dd(m[j]) * rsqrt_dd(eps2 + dot3(r, r));
+        }
+        e = mul_d(mul_d(dot3(vi, vi), m[i]), 0.5) - pot * two_prod(G, m[i]);
+    }
+    st2(&sh[t], e);
+    __syncthreads();
+    for (int h = kDDSysMax / 2; h > 0; h >>= 1) {
+        if (t < h) st2(&sh[t], ld2(&sh[t]) + ld2(&sh[t + h]));
+        __syncthreads();
+    }
+    if (t == 0) out[blockIdx.x] = sh[0];
+}
+
 __global__ void k_dd_sum(const double2 *__restrict__ bpart, int nb, double2 *__restrict__ out)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -494,18 +554,36 @@ DDPlan dd_plan(int N)
     return pl;
 }
 
-int launch_dd_pair(int P, const double2 *tr, const double *m, int N, double eps, double G, const DDPlan &pl,
-                   double2 *part, cudaStream_t st)
+// Batched form on the device: system offsets, the system of every body, and
+// the per-system steps.
+struct DDBatchDev {
+    const int64_t *off = nullptr;
+    const int *sys = nullptr;
+    const double *dts = nullptr;
+    int S = 0;
+};
+
+template <int P, bool kTop2>
+void launch_pair_kernel(const double2 *tr, const double *m, int N, double eps, double G, const DDPlan &pl,
+                        double2 *part, cudaStream_t st, const DDBatchDev *b)
 {
-    const dim3 grid(pl.iblocks, pl.S);
+    if (b)
+        k_dd_pair_sys<P, kTop2><<<b->S, kDDSysMax, 0, st>>>(tr, m, b->off, eps, G, part);
+    else
+        k_dd_pair<P, kTop2><<<dim3(pl.iblocks, pl.S), kDDThreads, 0, st>>>(tr, m, N, eps, G, pl.jchunk, part);
+}
+
+int launch_dd_pair(int P, const double2 *tr, const double *m, int N, double eps, double G, const DDPlan &pl,
+                   double2 *part, cudaStream_t st, const DDBatchDev *b)
+{
     switch (P) {
-        case 1: k_dd_pair<1><<<grid, kDDThreads, 0, st>>>(tr, m, N, eps, G, pl.jchunk, part); break;
-        case 2: k_dd_pair<2><<<grid, kDDThreads, 0, st>>>(tr, m, N, eps, G, pl.jchunk, part); break;
-        case 3: k_dd_pair<3><<<grid, kDDThreads, 0, st>>>(tr, m, N, eps, G, pl.jchunk, part); break;
-        case 4: k_dd_pair<4><<<grid, kDDThreads, 0, st>>>(tr, m, N, eps, G, pl.jchunk, part); break;
-        case 5: k_dd_pair<5><<<grid, kDDThreads, 0, st>>>(tr, m, N, eps, G, pl.jchunk, part); break;
-        case 7: k_dd_pair_top2<7><<<grid, kDDThreads, 0, st>>>(tr, m, N, eps, G, pl.jchunk, part); break;
-        case 9: k_dd_pair_top2<9><<<grid, kDDThreads, 0, st>>>(tr, m, N, eps, G, pl.jchunk, part); break;
+        case 1: launch_pair_kernel<1, false>(tr, m, N, eps, G, pl, part, st, b); break;
+        case 2: launch_pair_kernel<2, false>(tr, m, N, eps, G, pl, part, st, b); break;
+        case 3: launch_pair_kernel<3, false>(tr, m, N, eps, G, pl, part, st, b); break;
+        case 4: launch_pair_kernel<4, false>(tr, m, N, eps, G, pl, part, st, b); break;
+        case 5: launch_pair_kernel<5, false>(tr, m, N, eps, G, pl, part, st, b); break;
+        case 7: launch_pair_kernel<7, true>(tr, m, N, eps, G, pl, part, st, b); break;
+        case 9: launch_pair_kernel<9, true>(tr, m, N, eps, G, pl, part, st, b); break;
         default: set_error("double-double evaluation: unsupported derivative count"); return MH_EINVAL;
     }
     MH_LAUNCHED("k_dd_pair");
@@ -514,18 +592,22 @@ int launch_dd_pair(int P, const double2 *tr, const double *m, int N, double eps,
 
 template <int p>
 int launch_dd_step_p(double2 *x, double2 *v, double2 *d, double2 *tr, double2 *part, const double *m, int N,
-                     double eps, double G, int bm, double dt, int n_iter, int *flag, cudaStream_t st)
+                     double eps, double G, int bm, double dt, int n_iter, int *flag, cudaStream_t st,
+                     const DDBatchDev *b)
 {
     const DDPlan pl = dd_plan(N);
+    const int slots = b ? 1 : pl.S;
+    const double *dts = b ? b->dts : nullptr;
+    const int *sys = b ? b->sys : nullptr;
     const int nb = (3 * N + kDDThreads - 1) / kDDThreads;
-    k_dd_predict<p><<<nb, kDDThreads, 0, st>>>(x, v, d, N, dt, tr);
+    k_dd_predict<p><<<nb, kDDThreads, 0, st>>>(x, v, d, N, dt, dts, sys, tr);
     MH_LAUNCHED("k_dd_predict");
     for (int it = 0; it < n_iter; ++it) {
-        if (int rc = launch_dd_pair(p, tr, m, N, eps, G, pl, part, st)) return rc;
+        if (int rc = launch_dd_pair(p, tr, m, N, eps, G, pl, part, st, b)) return rc;
         if (it + 1 < n_iter)
-            k_dd_correct<p, false><<<nb, kDDThreads, 0, st>>>(x, v, d, part, pl.S, N, dt, bm, tr, flag);
+            k_dd_correct<p, false><<<nb, kDDThreads, 0, st>>>(x, v, d, part, slots, N, dt, dts, sys, bm, tr, flag);
         else
-            k_dd_correct<p, true><<<nb, kDDThreads, 0, st>>>(x, v, d, part, pl.S, N, dt, bm, tr, flag);
+            k_dd_correct<p, true><<<nb, kDDThreads, 0, st>>>(x, v, d, part, slots, N, dt, dts, sys, bm, tr, flag);
         MH_LAUNCHED("k_dd_correct");
     }
     return MH_OK;
@@ -558,10 +640,27 @@ struct mh_dd {
     double *m = nullptr;
     double2 *x = nullptr, *v = nullptr, *d = nullptr, *tr = nullptr, *part = nullptr, *diag = nullptr;
     int *flag = nullptr;
+    // batched form (S > 0): system offsets, system of each body, per-system steps
+    int64_t S = 0;
+    int64_t *off = nullptr;
+    int *sys = nullptr;
+    double *dts = nullptr;
+    int64_t batch_steps = 0;
+    double batch_pairs = 0.0;     // sum over systems of n_s (n_s - 1)
     cudaGraphExec_t graph = nullptr;
     double graph_dt = 0.0;
     int graph_n = 0;
     mh_counters ctr{};
+
+    DDBatchDev batch() const
+    {
+        DDBatchDev b;
+        b.off = off;
+        b.sys = sys;
+        b.dts = dts;
+        b.S = (int)S;
+        return b;
+    }
 };
 
 namespace {
@@ -572,6 +671,7 @@ int dd_free(mh_dd *s)
     if (s->graph) cudaGraphExecDestroy(s->graph);
     cudaFree(s->m); cudaFree(s->x); cudaFree(s->v); cudaFree(s->d);
     cudaFree(s->tr); cudaFree(s->part); cudaFree(s->diag); cudaFree(s->flag);
+    cudaFree(s->off); cudaFree(s->sys); cudaFree(s->dts);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return MH_OK;
@@ -608,17 +708,20 @@ int dd_initialise(mh_dd *s)
 {
     const int N = (int)s->N, K = 2 * s->p;
     const DDPlan pl = dd_plan(N);
+    const DDBatchDev b = s->batch();
+    const DDBatchDev *bp = s->S ? &b : nullptr;
+    const int slots = s->S ? 1 : pl.S;
     for (int have = 0; have < K; have += 2) {
         const int P = have + 1;
         const int64_t nt = (int64_t)N * (have + 2) * 3;
         k_dd_init_tr<<<(unsigned)((nt + kDDThreads - 1) / kDDThreads), kDDThreads, 0, s->stream>>>(
             s->x, s->v, s->d, N, K, have, s->tr);
         MH_LAUNCHED("k_dd_init_tr");
-        if (int rc = launch_dd_pair(P, s->tr, s->m, N, s->eps, s->G, pl, s->part, s->stream)) return rc;
+        if (int rc = launch_dd_pair(P, s->tr, s->m, N, s->eps, s->G, pl, s->part, s->stream, bp)) return rc;
         const int nn = std::min(P, K - 1) - have + 1;
         const int64_t ns = (int64_t)N * nn * 3;
         k_dd_init_store<<<(unsigned)((ns + kDDThreads - 1) / kDDThreads), kDDThreads, 0, s->stream>>>(
-            s->part, pl.S, N, P, K, have, s->d);
+            s->part, slots, N, P, K, have, s->d);
         MH_LAUNCHED("k_dd_init_store");
         s->ctr.kernel_launches += 3;
     }
@@ -628,14 +731,48 @@ int dd_initialise(mh_dd *s)
 int dd_step_once(mh_dd *s, double dt, int n_iter)
 {
     const int N = (int)s->N;
+    const DDBatchDev b = s->batch();
+    const DDBatchDev *bp = s->S ? &b : nullptr;
     switch (s->p) {
-        case 1: return launch_dd_step_p<1>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream);
-        case 2: return launch_dd_step_p<2>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream);
-        case 3: return launch_dd_step_p<3>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream);
-        case 4: return launch_dd_step_p<4>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream);
-        case 5: return launch_dd_step_p<5>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream);
+        case 1: return launch_dd_step_p<1>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream, bp);
+        case 2: return launch_dd_step_p<2>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream, bp);
+        case 3: return launch_dd_step_p<3>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream, bp);
+        case 4: return launch_dd_step_p<4>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream, bp);
+        case 5: return launch_dd_step_p<5>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream, bp);
         default: set_error("double-double step: unsupported order"); return MH_EINVAL;
     }
+}
+
+// nsteps steps: one launched directly, more replayed from a CUDA graph of one
+// step (kept while dt and n_iter stay the same).
+int dd_advance(mh_dd *sim, double dt, int n_iter, int64_t nsteps)
+{
+    if (nsteps == 1) return dd_step_once(sim, dt, n_iter);
+    if (!sim->graph || sim->graph_dt != dt || sim->graph_n != n_iter) {
+        if (sim->graph) { cudaGraphExecDestroy(sim->graph); sim->graph = nullptr; }
+        cudaGraph_t g = nullptr;
+        MH_CUDA(cudaStreamBeginCapture(sim->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = dd_step_once(sim, dt, n_iter);
+        cudaError_t e = cudaStreamEndCapture(sim->stream, &g);
+        if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+        if (e != cudaSuccess) return cuda_fail(e, "double-double step: graph capture");
+        e = cudaGraphInstantiate(&sim->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { sim->graph = nullptr; return cuda_fail(e, "double-double step: graph instantiate"); }
+        sim->graph_dt = dt;
+        sim->graph_n = n_iter;
+    }
+    for (int64_t k = 0; k < nsteps; ++k) MH_CUDA(cudaGraphLaunch(sim->graph, sim->stream));
+    return MH_OK;
+}
+
+void dd_count(mh_dd *sim, int n_iter, int64_t nsteps, double pairs_per_eval)
+{
+    sim->ctr.steps += nsteps;
+    sim->ctr.evaluations += nsteps * n_iter;
+    sim->ctr.pair_interactions += (double)nsteps * n_iter * pairs_per_eval;
+    sim->ctr.particle_steps += (double)nsteps * (double)sim->N;
+    sim->ctr.kernel_launches += nsteps * (1 + 2 * n_iter);
 }
 
 int dd_check_flag(mh_dd *s)
@@ -657,6 +794,102 @@ bool finite_all(const double *a, size_t n)
     return true;
 }
 
+// Shared by mh_dd_create and mh_dd_create_batch (offsets, dt: the batch's, or
+// null for one system).
+int dd_create(mh_dd **out, const char *fn, int64_t N, int order, const double *m, const double *x2,
+              const double *v2, double eps, const mh_config *cfg, void *stream, int64_t S,
+              const int64_t *offsets, const double *dt)
+{
+    const std::string f(fn);
+    if (order != 4 && order != 6 && order != 8 && order != 10 && order != 12) {
+        set_error(f + ": order must be 4, 6, 8, 10 or 12");
+        return MH_EINVAL;
+    }
+    if (!m || !x2 || !v2) { set_error(f + ": m, x2 and v2 are required"); return MH_EINVAL; }
+    if (!(eps >= 0.0) || !std::isfinite(eps)) { set_error(f + ": eps must be finite and >= 0"); return MH_EINVAL; }
+    mh_config c;
+    mh_config_default(&c);
+    if (cfg) c = *cfg;
+    if (c.beta_mode != MH_BETA_MODIFIED && c.beta_mode != MH_BETA_STANDARD) {
+        set_error(f + ": beta_mode must be MH_BETA_MODIFIED or MH_BETA_STANDARD");
+        return MH_EINVAL;
+    }
+    if (!std::isfinite(c.G)) { set_error(f + ": G must be finite"); return MH_EINVAL; }
+    if (!finite_all(m, (size_t)N) || !finite_all(x2, (size_t)N * 6) || !finite_all(v2, (size_t)N * 6)) {
+        set_error(f + ": non-finite m, x or v");
+        return MH_ENONFINITE;
+    }
+    mh_dd *s = new mh_dd;
+    s->N = N;
+    s->order = order;
+    s->p = order / 2 - 1;
+    s->bm = c.beta_mode;
+    s->eps = eps;
+    s->G = c.G;
+    s->S = S;
+    const int K = 2 * s->p;
+    const DDPlan pl = dd_plan((int)N);
+    const size_t slots = S ? 1 : (size_t)pl.S;
+    const size_t R = (size_t)K * 3;      // widest trajectory record (initialisation, P + 1 <= 2p)
+    const int nb = (int)((N + kDDThreads - 1) / kDDThreads);
+    const size_t ndiag = std::max<size_t>((size_t)nb + 1, (size_t)S);
+    auto fail = [&](int rc) { dd_free(s); return rc; };
+    if (stream) {
+        s->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(cuda_fail(cudaGetLastError(), "cudaStreamCreate"));
+        s->own_stream = true;
+    }
+    bool ok = cudaMalloc((void **)&s->m, N * sizeof(double)) == cudaSuccess &&
+              cudaMalloc((void **)&s->x, N * 3 * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc((void **)&s->v, N * 3 * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc((void **)&s->d, N * K * 3 * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc((void **)&s->tr, N * R * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc((void **)&s->part, slots * N * R * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc((void **)&s->diag, ndiag * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc((void **)&s->flag, sizeof(int)) == cudaSuccess;
+    if (ok && S)
+        ok = cudaMalloc((void **)&s->off, (S + 1) * sizeof(int64_t)) == cudaSuccess &&
+             cudaMalloc((void **)&s->sys, N * sizeof(int)) == cudaSuccess &&
+             cudaMalloc((void **)&s->dts, S * sizeof(double)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        set_error(f + ": device allocation failed");
+        return fail(MH_ENOMEM);
+    }
+    int rc = MH_OK;
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        if (!rc && cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+            rc = cuda_fail(cudaGetLastError(), (f + ": upload").c_str());
+    };
+    std::vector<int> sys_h;
+    if (S) {
+        sys_h.resize((size_t)N);
+        for (int64_t q = 0; q < S; ++q) {
+            for (int64_t i = offsets[q]; i < offsets[q + 1]; ++i) sys_h[(size_t)i] = (int)q;
+            const double n = (double)(offsets[q + 1] - offsets[q]);
+            s->batch_pairs += n * (n - 1.0);
+        }
+        up(s->off, offsets, (S + 1) * sizeof(int64_t));
+        up(s->sys, sys_h.data(), N * sizeof(int));
+        up(s->dts, dt, S * sizeof(double));
+    }
+    up(s->m, m, N * sizeof(double));
+    up(s->x, x2, N * 3 * sizeof(double2));
+    up(s->v, v2, N * 3 * sizeof(double2));
+    if (!rc && cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream) != cudaSuccess)
+        rc = cuda_fail(cudaGetLastError(), (f + ": memset").c_str());
+    if (!rc && cudaMemsetAsync(s->d, 0, N * K * 3 * sizeof(double2), s->stream) != cudaSuccess)
+        rc = cuda_fail(cudaGetLastError(), (f + ": memset").c_str());
+    if (!rc) rc = dd_consts_once(s->stream);
+    if (!rc) rc = dd_initialise(s);
+    if (!rc && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), fn);
+    if (rc) return fail(rc);
+    *out = s;
+    return MH_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -667,73 +900,34 @@ int mh_dd_create(mh_dd **out, int64_t N, int order, const double *m, const doubl
     if (!out) { set_error("mh_dd_create: out is NULL"); return MH_EINVAL; }
     *out = nullptr;
     if (N < 1 || N > (1 << 24)) { set_error("mh_dd_create: N must be in [1, 2^24]"); return MH_EINVAL; }
-    if (order != 4 && order != 6 && order != 8 && order != 10 && order != 12) {
-        set_error("mh_dd_create: order must be 4, 6, 8, 10 or 12");
+    return dd_create(out, "mh_dd_create", N, order, m, x2, v2, eps, cfg, stream, 0, nullptr, nullptr);
+}
+
+int mh_dd_create_batch(mh_dd **out, int64_t S, const int64_t *offsets, const double *m, const double *x2,
+                       const double *v2, const double *dt, double eps, int order, const mh_config *cfg,
+                       void *stream)
+{
+    if (!out) { set_error("mh_dd_create_batch: out is NULL"); return MH_EINVAL; }
+    *out = nullptr;
+    if (S < 1 || S > (1 << 22) || !offsets || !dt) {
+        set_error("mh_dd_create_batch: need 1 <= S <= 2^22, offsets and dt");
         return MH_EINVAL;
     }
-    if (!m || !x2 || !v2) { set_error("mh_dd_create: m, x2 and v2 are required"); return MH_EINVAL; }
-    if (!(eps >= 0.0) || !std::isfinite(eps)) { set_error("mh_dd_create: eps must be finite and >= 0"); return MH_EINVAL; }
-    mh_config c;
-    mh_config_default(&c);
-    if (cfg) c = *cfg;
-    if (c.beta_mode != MH_BETA_MODIFIED && c.beta_mode != MH_BETA_STANDARD) {
-        set_error("mh_dd_create: beta_mode must be MH_BETA_MODIFIED or MH_BETA_STANDARD");
-        return MH_EINVAL;
+    if (offsets[0] != 0) { set_error("mh_dd_create_batch: offsets[0] must be 0"); return MH_EINVAL; }
+    for (int64_t q = 0; q < S; ++q) {
+        const int64_t n = offsets[q + 1] - offsets[q];
+        if (n < 1 || n > kDDSysMax) {
+            set_error("mh_dd_create_batch: every system needs 1 to 64 bodies");
+            return MH_EINVAL;
+        }
+        if (!std::isfinite(dt[q]) || dt[q] == 0.0) {
+            set_error("mh_dd_create_batch: every dt must be finite and non-zero");
+            return MH_EINVAL;
+        }
     }
-    if (!std::isfinite(c.G)) { set_error("mh_dd_create: G must be finite"); return MH_EINVAL; }
-    if (!finite_all(m, (size_t)N) || !finite_all(x2, (size_t)N * 6) || !finite_all(v2, (size_t)N * 6)) {
-        set_error("mh_dd_create: non-finite m, x or v");
-        return MH_ENONFINITE;
-    }
-    mh_dd *s = new mh_dd;
-    s->N = N;
-    s->order = order;
-    s->p = order / 2 - 1;
-    s->bm = c.beta_mode;
-    s->eps = eps;
-    s->G = c.G;
-    const int K = 2 * s->p;
-    const DDPlan pl = dd_plan((int)N);
-    const size_t R = (size_t)K * 3;      // widest trajectory record (initialisation, P + 1 <= 2p)
-    const int nb = (int)((N + kDDThreads - 1) / kDDThreads);
-    auto fail = [&](int rc) { dd_free(s); return rc; };
-    if (stream) {
-        s->stream = (cudaStream_t)stream;
-    } else {
-        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess)
-            return fail(cuda_fail(cudaGetLastError(), "cudaStreamCreate"));
-        s->own_stream = true;
-    }
-    if (cudaMalloc((void **)&s->m, N * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void **)&s->x, N * 3 * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc((void **)&s->v, N * 3 * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc((void **)&s->d, N * K * 3 * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc((void **)&s->tr, N * R * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc((void **)&s->part, (size_t)pl.S * N * R * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc((void **)&s->diag, (nb + 1) * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc((void **)&s->flag, sizeof(int)) != cudaSuccess) {
-        cudaGetLastError();
-        set_error("mh_dd_create: device allocation failed");
-        return fail(MH_ENOMEM);
-    }
-    int rc = MH_OK;
-    auto up = [&](void *dst, const void *src, size_t bytes) {
-        if (!rc && cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
-            rc = cuda_fail(cudaGetLastError(), "mh_dd_create: upload");
-    };
-    up(s->m, m, N * sizeof(double));
-    up(s->x, x2, N * 3 * sizeof(double2));
-    up(s->v, v2, N * 3 * sizeof(double2));
-    if (!rc && cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream) != cudaSuccess)
-        rc = cuda_fail(cudaGetLastError(), "mh_dd_create: memset");
-    if (!rc && cudaMemsetAsync(s->d, 0, N * K * 3 * sizeof(double2), s->stream) != cudaSuccess)
-        rc = cuda_fail(cudaGetLastError(), "mh_dd_create: memset");
-    if (!rc) rc = dd_consts_once(s->stream);
-    if (!rc) rc = dd_initialise(s);
-    if (!rc && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "mh_dd_create");
-    if (rc) return fail(rc);
-    *out = s;
-    return MH_OK;
+    const int64_t N = offsets[S];
+    if (N > (1 << 24)) { set_error("mh_dd_create_batch: at most 2^24 bodies in all"); return MH_EINVAL; }
+    return dd_create(out, "mh_dd_create_batch", N, order, m, x2, v2, eps, cfg, stream, S, offsets, dt);
 }
 
 void mh_dd_destroy(mh_dd *sim)
@@ -745,37 +939,27 @@ void mh_dd_destroy(mh_dd *sim)
 int mh_dd_step(mh_dd *sim, double dt, int n_iter, int64_t nsteps)
 {
     if (int rc = dd_check(sim, "mh_dd_step")) return rc;
+    if (sim->S) { set_error("mh_dd_step: a batch advances with mh_dd_step_batch"); return MH_EINVAL; }
     if (!std::isfinite(dt) || dt == 0.0) { set_error("mh_dd_step: dt must be finite and non-zero"); return MH_EINVAL; }
     if (n_iter < 1 || n_iter > 64) { set_error("mh_dd_step: n_iter must be in [1, 64]"); return MH_EINVAL; }
     if (nsteps < 0) { set_error("mh_dd_step: nsteps must be >= 0"); return MH_EINVAL; }
     if (nsteps == 0) return MH_OK;
-    const int launches = 1 + 2 * n_iter;
-    if (nsteps == 1) {
-        if (int rc = dd_step_once(sim, dt, n_iter)) return rc;
-    } else {
-        // one step captured as a CUDA graph, replayed nsteps times
-        if (!sim->graph || sim->graph_dt != dt || sim->graph_n != n_iter) {
-            if (sim->graph) { cudaGraphExecDestroy(sim->graph); sim->graph = nullptr; }
-            cudaGraph_t g = nullptr;
-            MH_CUDA(cudaStreamBeginCapture(sim->stream, cudaStreamCaptureModeThreadLocal));
-            int rc = dd_step_once(sim, dt, n_iter);
-            cudaError_t e = cudaStreamEndCapture(sim->stream, &g);
-            if (rc) { if (g) cudaGraphDestroy(g); return rc; }
-            if (e != cudaSuccess) return cuda_fail(e, "mh_dd_step: graph capture");
-            e = cudaGraphInstantiate(&sim->graph, g, 0);
-            cudaGraphDestroy(g);
-            if (e != cudaSuccess) { sim->graph = nullptr; return cuda_fail(e, "mh_dd_step: graph instantiate"); }
-            sim->graph_dt = dt;
-            sim->graph_n = n_iter;
-        }
-        for (int64_t k = 0; k < nsteps; ++k) MH_CUDA(cudaGraphLaunch(sim->graph, sim->stream));
-    }
+    if (int rc = dd_advance(sim, dt, n_iter, nsteps)) return rc;
     for (int64_t k = 0; k < nsteps; ++k) host_add(sim->t_hi, sim->t_lo, dt);
-    sim->ctr.steps += nsteps;
-    sim->ctr.evaluations += nsteps * n_iter;
-    sim->ctr.pair_interactions += (double)nsteps * n_iter * (double)sim->N * (double)(sim->N - 1);
-    sim->ctr.particle_steps += (double)nsteps * (double)sim->N;
-    sim->ctr.kernel_launches += nsteps * launches;
+    dd_count(sim, n_iter, nsteps, (double)sim->N * (double)(sim->N - 1));
+    return MH_OK;
+}
+
+int mh_dd_step_batch(mh_dd *sim, int64_t nsteps, int n_iter)
+{
+    if (int rc = dd_check(sim, "mh_dd_step_batch")) return rc;
+    if (!sim->S) { set_error("mh_dd_step_batch: the handle is not a batch"); return MH_EINVAL; }
+    if (n_iter < 1 || n_iter > 64) { set_error("mh_dd_step_batch: n_iter must be in [1, 64]"); return MH_EINVAL; }
+    if (nsteps < 0) { set_error("mh_dd_step_batch: nsteps must be >= 0"); return MH_EINVAL; }
+    if (nsteps == 0) return MH_OK;
+    if (int rc = dd_advance(sim, 0.0, n_iter, nsteps)) return rc;     // the steps come from dts
+    sim->batch_steps += nsteps;
+    dd_count(sim, n_iter, nsteps, sim->batch_pairs);
     return MH_OK;
 }
 
@@ -787,7 +971,10 @@ int mh_dd_sync(mh_dd *sim, double *t2, double *x2, double *v2, double *d2)
     if (v2) MH_CUDA(cudaMemcpyAsync(v2, sim->v, N * 3 * sizeof(double2), cudaMemcpyDeviceToHost, sim->stream));
     if (d2) MH_CUDA(cudaMemcpyAsync(d2, sim->d, N * K * 3 * sizeof(double2), cudaMemcpyDeviceToHost, sim->stream));
     if (int rc = dd_check_flag(sim)) return rc;
-    if (t2) { t2[0] = sim->t_hi; t2[1] = sim->t_lo; }
+    if (t2) {
+        t2[0] = sim->S ? (double)sim->batch_steps : sim->t_hi;
+        t2[1] = sim->S ? 0.0 : sim->t_lo;
+    }
     return MH_OK;
 }
 
@@ -808,7 +995,14 @@ int mh_dd_set_state(mh_dd *sim, const double *t2, const double *x2, const double
     } else if (int rc = dd_initialise(sim)) {
         return rc;
     }
-    if (t2) { sim->t_hi = t2[0]; sim->t_lo = t2[1]; }
+    if (t2) {
+        if (sim->S) {
+            sim->batch_steps = (int64_t)t2[0];
+        } else {
+            sim->t_hi = t2[0];
+            sim->t_lo = t2[1];
+        }
+    }
     MH_CUDA(cudaStreamSynchronize(sim->stream));
     return MH_OK;
 }
@@ -816,6 +1010,7 @@ int mh_dd_set_state(mh_dd *sim, const double *t2, const double *x2, const double
 int mh_dd_diagnostics(mh_dd *sim, double *energy2, double *ecc2, int central)
 {
     if (int rc = dd_check(sim, "mh_dd_diagnostics")) return rc;
+    if (sim->S) { set_error("mh_dd_diagnostics: a batch reports energies with mh_dd_batch_energy"); return MH_EINVAL; }
     const int N = (int)sim->N;
     if (ecc2 && (central < 0 || central >= N)) { set_error("mh_dd_diagnostics: central out of range"); return MH_EINVAL; }
     const int nb = (N + kDDThreads - 1) / kDDThreads;
@@ -834,6 +1029,20 @@ int mh_dd_diagnostics(mh_dd *sim, double *energy2, double *ecc2, int central)
         MH_CUDA(cudaMemcpyAsync(ecc2, sim->tr, (size_t)N * 3 * sizeof(double2), cudaMemcpyDeviceToHost, sim->stream));
         sim->ctr.kernel_launches += 1;
     }
+    MH_CUDA(cudaStreamSynchronize(sim->stream));
+    return MH_OK;
+}
+
+int mh_dd_batch_energy(mh_dd *sim, double *energy2)
+{
+    if (int rc = dd_check(sim, "mh_dd_batch_energy")) return rc;
+    if (!sim->S) { set_error("mh_dd_batch_energy: the handle is not a batch"); return MH_EINVAL; }
+    if (!energy2) { set_error("mh_dd_batch_energy: energy2 is NULL"); return MH_EINVAL; }
+    k_dd_energy_sys<<<(unsigned)sim->S, kDDSysMax, 0, sim->stream>>>(sim->m, sim->x, sim->v, sim->off, sim->eps,
+                                                                    sim->G, sim->diag);
+    MH_LAUNCHED("k_dd_energy_sys");
+    sim->ctr.kernel_launches += 1;
+    MH_CUDA(cudaMemcpyAsync(energy2, sim->diag, (size_t)sim->S * sizeof(double2), cudaMemcpyDeviceToHost, sim->stream));
     MH_CUDA(cudaStreamSynchronize(sim->stream));
     return MH_OK;
 }
