@@ -15,9 +15,9 @@
  *   - energy and Laplace-Runge-Lenz (eccentricity) vectors (Appendix A, Eq. A1).
  * The integrator order is 2(p+1) where p is the number of acceleration
  * derivatives evaluated (Section 2): order 4, 6, 8, 10, 12 <-> p = 1 .. 5.
- * Orders 10 and 12 run in the FP64 form with shared or time-symmetric steps;
- * the FP32-pair form, block steps, the learned residual and the batched form
- * are built for orders 4 to 8.
+ * Orders 10 and 12 run in the FP64 form with shared or time-symmetric steps and
+ * in the double-double form (mh_dd_*); the FP32-pair form, block steps, the
+ * learned residual and the FP64 batched form are built for orders 4 to 8.
  *
  * Conventions shared by every entry point
  *   - Return value: an mh_status; 0 is success, negative values are errors.
@@ -365,7 +365,7 @@ int mh_mlp_train(mh_mlp *net, const float *x, const float *t, int64_t rows, int 
  * FP64 fused multiply-add TFLOP/s, FP32 fused multiply-add TFLOP/s, packed
  * FP32x2 multiply-add TFLOP/s, single-precision reciprocal square roots in
  * 10^12 per second.  Every SM runs independent chains; each rate is one
- * CUDA-event timed launch after a warm-up launch (about 2 s in all).  Waits. */
+ * CUDA-event timed launch after a warm-up launch (about 0.2 s in all).  Waits. */
 int mh_measure_peaks(double *out4);
 
 /* Number of bodies, order and counters of a handle. */

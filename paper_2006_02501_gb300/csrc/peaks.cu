@@ -101,8 +101,9 @@ extern "C" int mh_measure_peaks(double *out4)
     cudaStream_t st = 0;
     float ms = 0.0f;
     int rc = MH_OK;
-    // about 0.3-0.5 s per launch at 2.07 GHz (FP64 has 2 lanes per SM, FP32 128)
-    const int it64 = 128, it32 = 4096, itr = 1024;
+    // 20-40 ms per launch at 2.07 GHz (FP64 has 2 lanes per SM, FP32 128): long
+    // against the event resolution and the launch latency
+    const int it64 = 8192, it32 = 131072, itr = 65536;
     if (!rc) rc = time_launch([&] { k_peak_fma<double><<<grid, kPeakThreads, 0, st>>>((double *)sink, it64, 0.999999, 1e-7); }, st, &ms);
     if (!rc) out4[0] = 2.0 * kChains * it64 * threads / (ms * 1e-3) / 1e12;
     if (!rc) rc = time_launch([&] { k_peak_fma<float><<<grid, kPeakThreads, 0, st>>>(sink, it32, 0.999999f, 1e-7f); }, st, &ms);
