@@ -351,10 +351,8 @@ def _lib_q_handle():
 
 
 def as_dd(a) -> np.ndarray:
-    """A double-double array (..., 2): doubles get lo = 0, pairs pass through."""
+    """Doubles as a double-double array (..., 2) with lo = 0."""
     a = np.asarray(a, dtype=np.float64)
-    if a.ndim >= 1 and a.shape[-1] == 2 and getattr(a, "_is_dd", False):
-        return np.ascontiguousarray(a)
     return np.ascontiguousarray(np.stack([a, np.zeros_like(a)], axis=-1))
 
 
