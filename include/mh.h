@@ -143,6 +143,18 @@ void mh_config_default(mh_config *cfg);
 int mh_create(mh_sim **out, int64_t N, int order, const double *m, const double *x,
               const double *v, double eps, const mh_config *cfg, void *stream);
 
+/* Create a simulation from a state taken by mh_sync (checkpoint / resume):
+ * N, order, m, eps, cfg, stream as for mh_create; state->x, v and derivs are
+ * required (no initialisation passes run), state->t is the time and, for block
+ * steps, state->level the levels (NULL: from the criterion).  Continuing the
+ * restored simulation gives bit for bit the states of the uninterrupted run for
+ * shared and block steps (every reduction has a fixed order).  The time-symmetric
+ * step restarts its H- from Eq. 24 at the restored positions, and compensated
+ * summation restarts its compensation at zero, so those continue within
+ * rounding, not bitwise.  On error *out is NULL. */
+int mh_restore(mh_sim **out, int64_t N, int order, const double *m, const mh_state *state, double eps,
+               const mh_config *cfg, void *stream);
+
 /* Release every resource of the handle (NULL is a no-op). */
 void mh_destroy(mh_sim *sim);
 

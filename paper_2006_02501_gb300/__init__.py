@@ -51,6 +51,27 @@ def _stream_handle(stream) -> int | None:
     return int(stream.cuda_stream)        # torch.cuda.Stream
 
 
+def _config(order, precision, beta, G, split_j, heavy_frac, block, symmetric, fp32_variant, timesym_eta,
+            compensated) -> "_capi.Config":
+    cfg = _capi.Config()
+    _capi.lib().mh_config_default(ctypes.byref(cfg))
+    cfg.order, cfg.precision, cfg.beta_mode, cfg.G, cfg.split_j = order, precision, beta, G, split_j
+    if heavy_frac is not None:
+        cfg.heavy_frac = heavy_frac
+    cfg.symmetric = int(symmetric)
+    cfg.fp32_variant = int(fp32_variant)
+    cfg.compensated = 1 if compensated else 0
+    if timesym_eta is not None:
+        cfg.step_mode = _capi.MH_STEP_TIMESYM
+        cfg.eta = float(timesym_eta)
+    if block is not None:
+        cfg.step_mode = _capi.MH_STEP_BLOCK
+        cfg.dt_max = float(block.get("dt_max", cfg.dt_max))
+        cfg.k_max = int(block.get("k_max", cfg.k_max))
+        cfg.eta = float(block.get("eta", cfg.eta))
+    return cfg
+
+
 class Simulation:
     """One N-body system advanced by the shared-step P(EC)^n scheme.
 
@@ -81,29 +102,53 @@ class Simulation:
         m = _host(m)
         N = m.shape[0]
         x, v = _host(x, (N, 3)), _host(v, (N, 3))
-        cfg = _capi.Config()
-        L.mh_config_default(ctypes.byref(cfg))
-        cfg.order, cfg.precision, cfg.beta_mode, cfg.G, cfg.split_j = order, precision, beta, G, split_j
-        if heavy_frac is not None:
-            cfg.heavy_frac = heavy_frac
-        cfg.symmetric = int(symmetric)
-        cfg.fp32_variant = int(fp32_variant)
-        cfg.compensated = 1 if compensated else 0
-        if timesym_eta is not None:
-            cfg.step_mode = _capi.MH_STEP_TIMESYM
-            cfg.eta = float(timesym_eta)
-        if block is not None:
-            cfg.step_mode = _capi.MH_STEP_BLOCK
-            cfg.dt_max = float(block.get("dt_max", cfg.dt_max))
-            cfg.k_max = int(block.get("k_max", cfg.k_max))
-            cfg.eta = float(block.get("eta", cfg.eta))
+        cfg = _config(order, precision, beta, G, split_j, heavy_frac, block, symmetric, fp32_variant,
+                      timesym_eta, compensated)
         h = ctypes.c_void_p()
         check(L.mh_create(ctypes.byref(h), N, order, _ptr(m), _ptr(x), _ptr(v), float(eps),
                           ctypes.byref(cfg), _stream_handle(stream)))
+        self._adopt(h, N, order, eps, G, precision, block)
+
+    def _adopt(self, h, N, order, eps, G, precision, block):
         self._h = h
         self.N, self.order, self.p = N, order, order // 2 - 1
         self.eps, self.G, self.precision = eps, G, precision
         self.block = block is not None
+
+    @classmethod
+    def restore(cls, order: int, m, state: dict, eps: float, precision: int = MH_PREC_FP64,
+                beta: int = MH_BETA_MODIFIED, G: float = 1.0, stream=None, split_j: int = 0,
+                heavy_frac: float | None = None, block: dict | None = None, symmetric: int = 1,
+                fp32_variant: int = 0, timesym_eta: float | None = None, compensated: bool = False):
+        """A simulation created from checkpoint() output (mh_restore): no
+        initialisation passes; continuing it reproduces the uninterrupted run bit
+        for bit for shared and block steps.  The other arguments as for __init__."""
+        m = _host(m)
+        N = m.shape[0]
+        x, v = _host(state["x"], (N, 3)), _host(state["v"], (N, 3))
+        d = _host(state["derivs"], (N, 2 * (order // 2 - 1), 3))
+        lv = state.get("level")
+        lp = None
+        if lv is not None:
+            lv = np.ascontiguousarray(lv, dtype=np.int32)
+            lp = lv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        st = _capi.StateC(float(state["t"]), _ptr(x), _ptr(v), _ptr(d), lp)
+        cfg = _config(order, precision, beta, G, split_j, heavy_frac, block, symmetric, fp32_variant,
+                      timesym_eta, compensated)
+        h = ctypes.c_void_p()
+        check(_capi.lib().mh_restore(ctypes.byref(h), N, order, _ptr(m), ctypes.byref(st), float(eps),
+                                     ctypes.byref(cfg), _stream_handle(stream)))
+        sim = cls.__new__(cls)
+        sim._adopt(h, N, order, eps, G, precision, block)
+        return sim
+
+    def checkpoint(self) -> dict:
+        """{t, x, v, derivs[, level]}: everything mh_restore needs."""
+        t, x, v, d = self.sync()
+        out = {"t": t, "x": x, "v": v, "derivs": d}
+        if self.block:
+            out["level"] = self.levels()
+        return out
 
     def close(self) -> None:
         if getattr(self, "_h", None):

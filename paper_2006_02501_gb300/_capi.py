@@ -34,7 +34,7 @@ EXPORTS = [
     "mh_mlp_destroy", "mh_mlp_num_params", "mh_mlp_get_params", "mh_mlp_set_params", "mh_mlp_forward",
     "mh_mlp_loss_grad", "mh_mlp_train", "mh_predict", "mh_step_timesym", "mh_measure_peaks",
     "mh_dd_create", "mh_dd_destroy", "mh_dd_step", "mh_dd_sync", "mh_dd_set_state", "mh_dd_diagnostics",
-    "mh_dd_info", "mh_dd_create_batch", "mh_dd_step_batch", "mh_dd_batch_energy",
+    "mh_dd_info", "mh_dd_create_batch", "mh_dd_step_batch", "mh_dd_batch_energy", "mh_restore",
 ]
 
 
@@ -84,6 +84,8 @@ def lib() -> ctypes.CDLL:
             L.mh_config_default.argtypes = [ctypes.POINTER(Config)]
             L.mh_config_default.restype = None
             L.mh_create.argtypes = [ctypes.POINTER(P), I64, I, DP, DP, DP, D, ctypes.POINTER(Config), P]
+            L.mh_restore.argtypes = [ctypes.POINTER(P), I64, I, DP, ctypes.POINTER(StateC), D,
+                                     ctypes.POINTER(Config), P]
             L.mh_destroy.argtypes = [P]
             L.mh_destroy.restype = None
             L.mh_mlp_destroy.restype = None

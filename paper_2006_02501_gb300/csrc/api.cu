@@ -555,6 +555,25 @@ int mh_create(mh_sim **out, int64_t N, int order, const double *m, const double 
     return create_shell(out, N, order, m, x, v, eps, cfg, stream, true);
 }
 
+int mh_restore(mh_sim **out, int64_t N, int order, const double *m, const mh_state *state, double eps,
+               const mh_config *cfg, void *stream)
+{
+    if (!out) { set_error("mh_restore: out is NULL"); return MH_EINVAL; }
+    *out = nullptr;
+    if (!state || !state->x || !state->v || !state->derivs) {
+        set_error("mh_restore: the state needs x, v and derivs");
+        return MH_EINVAL;
+    }
+    mh_sim *sim = nullptr;
+    if (int rc = create_shell(&sim, N, order, m, state->x, state->v, eps, cfg, stream, false)) return rc;
+    if (int rc = mh_set_state(sim, state)) {
+        mh_destroy(sim);
+        return rc;
+    }
+    *out = sim;
+    return MH_OK;
+}
+
 void mh_destroy(mh_sim *sim)
 {
     if (!sim) return;
