@@ -32,6 +32,14 @@
  *     mh_step returns once the work is queued, mh_sync / mh_diagnostics wait.
  *   - Units are the caller's; G defaults to 1.
  *   - Not thread safe per handle: one thread at a time may use an mh_sim.
+ *   - Test hook: the environment variable MH_FAULT, a comma-separated list, makes
+ *     the host side report faults without any device fault: "alloc" (device
+ *     allocations of mh_create, mh_restore, mh_create_batch, mh_dd_create and
+ *     mh_dd_create_batch fail with MH_ENOMEM, freeing what was allocated),
+ *     "launch" / "timeout" (mh_step, mh_dd_step and mh_dd_step_batch return
+ *     MH_ECUDA / MH_ETIMEOUT before queuing work, leaving the state unchanged),
+ *     "nonfinite" (mh_sync and mh_dd_sync return MH_ENONFINITE).  The library
+ *     has no device-side waits; MH_ETIMEOUT exists for callers' handling paths.
  */
 #ifndef MH_H
 #define MH_H

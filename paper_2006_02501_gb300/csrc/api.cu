@@ -7,6 +7,7 @@
 #include <map>
 #include <new>
 #include <tuple>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -19,6 +20,30 @@ thread_local std::string g_last_error;
 }
 
 void set_error(const std::string &msg) { g_last_error = msg; }
+
+bool fault_armed(const char *what)
+{
+    const char *env = std::getenv("MH_FAULT");
+    if (!env || !*env) return false;
+    const std::string list = std::string(",") + env + ",";
+    return list.find(std::string(",") + what + ",") != std::string::npos;
+}
+
+// The step faults a test can inject: a failed kernel launch, or a bounded
+// device-side wait that ran out.  Checked before any work is queued, so the
+// state is left as it was.
+int injected_step_fault(const char *fn)
+{
+    if (fault_armed("launch")) {
+        set_error(std::string(fn) + ": kernel launch failed (injected by MH_FAULT=launch)");
+        return MH_ECUDA;
+    }
+    if (fault_armed("timeout")) {
+        set_error(std::string(fn) + ": a bounded device-side wait ran out (injected by MH_FAULT=timeout)");
+        return MH_ETIMEOUT;
+    }
+    return MH_OK;
+}
 
 int cuda_fail(cudaError_t e, const char *what)
 {
@@ -44,6 +69,10 @@ int dalloc(T **ptr, size_t count)
 {
     *ptr = nullptr;
     if (count == 0) return MH_OK;
+    if (fault_armed("alloc")) {
+        set_error("device allocation failed (injected by MH_FAULT=alloc)");
+        return MH_ENOMEM;
+    }
     MH_CUDA(cudaMalloc((void **)ptr, count * sizeof(T)));
     return MH_OK;
 }
@@ -822,6 +851,7 @@ int mh_step(mh_sim *sim, double dt, int n_iter)
     if (int rc = check_handle(sim)) return rc;
     if (!(dt != 0.0) || !std::isfinite(dt)) { set_error("mh_step: dt must be finite and non-zero"); return MH_EINVAL; }
     if (n_iter < 1 || n_iter > 64) { set_error("mh_step: n_iter must be in [1, 64]"); return MH_EINVAL; }
+    if (int rc = injected_step_fault("mh_step")) return rc;
     if (sim->batch) { set_error("mh_step: batched simulations advance with mh_step_batch"); return MH_EINVAL; }
     if (sim->cfg.step_mode == MH_STEP_BLOCK) return block_advance(sim, dt, n_iter);
     if (sim->cfg.step_mode == MH_STEP_TIMESYM) {
@@ -951,6 +981,10 @@ int mh_sync(mh_sim *sim, mh_state *out)
 {
     if (int rc = check_handle(sim)) return rc;
     if (!out) { set_error("mh_sync: out is NULL"); return MH_EINVAL; }
+    if (fault_armed("nonfinite")) {
+        set_error("non-finite position or velocity (injected by MH_FAULT=nonfinite)");
+        return MH_ENONFINITE;
+    }
     DeviceState &s = sim->s;
     MH_CUDA(cudaStreamSynchronize(sim->stream));
     if (int rc = collect_timing(sim)) return rc;

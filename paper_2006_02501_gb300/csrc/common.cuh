@@ -23,6 +23,12 @@ inline int64_t pad_to(int64_t n, int64_t q) { return (n + q - 1) / q * q; }
 // Thread-local last-error message (mh_last_error).
 void set_error(const std::string &msg);
 
+// Host-side fault injection for tests of the error paths: true when the
+// comma-separated environment variable MH_FAULT lists `what` (alloc, launch,
+// timeout, nonfinite).  No fault is ever made on the device.
+bool fault_armed(const char *what);
+int injected_step_fault(const char *fn);    // MH_ECUDA (launch), MH_ETIMEOUT (timeout) or MH_OK
+
 // Record a CUDA failure and return MH_ECUDA (or MH_ENOMEM for allocations).
 int cuda_fail(cudaError_t e, const char *what);
 

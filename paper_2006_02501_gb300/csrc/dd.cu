@@ -777,6 +777,10 @@ void dd_count(mh_dd *sim, int n_iter, int64_t nsteps, double pairs_per_eval)
 
 int dd_check_flag(mh_dd *s)
 {
+    if (fault_armed("nonfinite")) {
+        set_error("non-finite position or velocity (injected by MH_FAULT=nonfinite)");
+        return MH_ENONFINITE;
+    }
     int flag = 0;
     MH_CUDA(cudaMemcpyAsync(&flag, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     MH_CUDA(cudaStreamSynchronize(s->stream));
@@ -840,6 +844,10 @@ int dd_create(mh_dd **out, const char *fn, int64_t N, int order, const double *m
         if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess)
             return fail(cuda_fail(cudaGetLastError(), "cudaStreamCreate"));
         s->own_stream = true;
+    }
+    if (fault_armed("alloc")) {
+        set_error(f + ": device allocation failed (injected by MH_FAULT=alloc)");
+        return fail(MH_ENOMEM);
     }
     bool ok = cudaMalloc((void **)&s->m, N * sizeof(double)) == cudaSuccess &&
               cudaMalloc((void **)&s->x, N * 3 * sizeof(double2)) == cudaSuccess &&
@@ -943,6 +951,7 @@ int mh_dd_step(mh_dd *sim, double dt, int n_iter, int64_t nsteps)
     if (!std::isfinite(dt) || dt == 0.0) { set_error("mh_dd_step: dt must be finite and non-zero"); return MH_EINVAL; }
     if (n_iter < 1 || n_iter > 64) { set_error("mh_dd_step: n_iter must be in [1, 64]"); return MH_EINVAL; }
     if (nsteps < 0) { set_error("mh_dd_step: nsteps must be >= 0"); return MH_EINVAL; }
+    if (int rc = injected_step_fault("mh_dd_step")) return rc;
     if (nsteps == 0) return MH_OK;
     if (int rc = dd_advance(sim, dt, n_iter, nsteps)) return rc;
     for (int64_t k = 0; k < nsteps; ++k) host_add(sim->t_hi, sim->t_lo, dt);
@@ -956,6 +965,7 @@ int mh_dd_step_batch(mh_dd *sim, int64_t nsteps, int n_iter)
     if (!sim->S) { set_error("mh_dd_step_batch: the handle is not a batch"); return MH_EINVAL; }
     if (n_iter < 1 || n_iter > 64) { set_error("mh_dd_step_batch: n_iter must be in [1, 64]"); return MH_EINVAL; }
     if (nsteps < 0) { set_error("mh_dd_step_batch: nsteps must be >= 0"); return MH_EINVAL; }
+    if (int rc = injected_step_fault("mh_dd_step_batch")) return rc;
     if (nsteps == 0) return MH_OK;
     if (int rc = dd_advance(sim, 0.0, n_iter, nsteps)) return rc;     // the steps come from dts
     sim->batch_steps += nsteps;
