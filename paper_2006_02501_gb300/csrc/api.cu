@@ -702,7 +702,11 @@ static int shared_step(mh_sim *sim, double dt, int n_iter, double tol, int *n_us
 {
     DeviceState &s = sim->s;
     const int prec = sim->cfg.precision;
-    int rc = launch_step_phase(s, sim->cfg, dt, 0, false, 0, sim->stream);
+    int rc;
+    {
+        NvtxScope r("mh:predict");
+        rc = launch_step_phase(s, sim->cfg, dt, 0, false, 0, sim->stream);
+    }
     if (rc) return rc;
     s.flip ^= 1;                        // the predictor raised the other bound slot
     sim->ctr.kernel_launches += 1;
@@ -717,7 +721,12 @@ static int shared_step(mh_sim *sim, double dt, int n_iter, double tol, int *n_us
     int used = n_iter;
     for (int it = 0; it < n_iter; ++it) {
         int split = 0;
-        if ((rc = evaluate(sim, s.p, prec, &split))) return rc;
+        {
+            NvtxScope r("mh:evaluate");
+            rc = evaluate(sim, s.p, prec, &split);
+        }
+        if (rc) return rc;
+        NvtxScope rc_scope("mh:correct");
         bool last = it == n_iter - 1;
         if (adaptive) {
             MH_CUDA(cudaMemsetAsync(sim->conv, 0, 2 * sizeof(unsigned long long), sim->stream));
@@ -794,6 +803,7 @@ int mh_step_timesym(mh_sim *sim, int64_t nsteps, int n_iter, int backward)
         set_error("mh_step_timesym: nsteps >= 0 and 1 <= n_iter <= 64 required");
         return MH_EINVAL;
     }
+    NvtxScope range("mh_step_timesym");
     const double dir = backward ? -1.0 : 1.0;
     const std::pair<int, int> key(n_iter, backward ? 1 : 0);
     int64_t k = 0;
@@ -852,6 +862,7 @@ int mh_step(mh_sim *sim, double dt, int n_iter)
     if (!(dt != 0.0) || !std::isfinite(dt)) { set_error("mh_step: dt must be finite and non-zero"); return MH_EINVAL; }
     if (n_iter < 1 || n_iter > 64) { set_error("mh_step: n_iter must be in [1, 64]"); return MH_EINVAL; }
     if (int rc = injected_step_fault("mh_step")) return rc;
+    NvtxScope range("mh_step");
     if (sim->batch) { set_error("mh_step: batched simulations advance with mh_step_batch"); return MH_EINVAL; }
     if (sim->cfg.step_mode == MH_STEP_BLOCK) return block_advance(sim, dt, n_iter);
     if (sim->cfg.step_mode == MH_STEP_TIMESYM) {

@@ -503,6 +503,7 @@ int mh_step_batch(mh_sim *sim, int64_t n_steps, int n_iter)
         set_error("mh_step_batch: need 1 <= n_steps <= 2^30 and 1 <= n_iter <= 64");
         return MH_EINVAL;
     }
+    NvtxScope range("mh_step_batch");
     BatchState &b = *static_cast<BatchState *>(sim->batch);
     if (!b.tuned)
         if (int rc = batch_tune(sim, b, (int)std::min<int64_t>(n_steps, 8), n_iter)) return rc;

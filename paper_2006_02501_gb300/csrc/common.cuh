@@ -9,6 +9,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mh.h"
 
 struct mh_mlp;
@@ -22,6 +24,17 @@ inline int64_t pad_to(int64_t n, int64_t q) { return (n + q - 1) / q * q; }
 
 // Thread-local last-error message (mh_last_error).
 void set_error(const std::string &msg);
+
+// NVTX range over the host-side issue of one phase of a step ("mh_step",
+// "mh:predict", "mh:evaluate", "mh:correct", ...), so that a profiler can
+// select kernels by phase (ncu --nvtx --nvtx-include "mh:evaluate/").  Without
+// an attached tool a range costs a few nanoseconds.
+struct NvtxScope {
+    explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope &) = delete;
+    NvtxScope &operator=(const NvtxScope &) = delete;
+};
 
 // Host-side fault injection for tests of the error paths: true when the
 // comma-separated environment variable MH_FAULT lists `what` (alloc, launch,

@@ -952,6 +952,7 @@ int mh_dd_step(mh_dd *sim, double dt, int n_iter, int64_t nsteps)
     if (n_iter < 1 || n_iter > 64) { set_error("mh_dd_step: n_iter must be in [1, 64]"); return MH_EINVAL; }
     if (nsteps < 0) { set_error("mh_dd_step: nsteps must be >= 0"); return MH_EINVAL; }
     if (int rc = injected_step_fault("mh_dd_step")) return rc;
+    NvtxScope range("mh_dd_step");
     if (nsteps == 0) return MH_OK;
     if (int rc = dd_advance(sim, dt, n_iter, nsteps)) return rc;
     for (int64_t k = 0; k < nsteps; ++k) host_add(sim->t_hi, sim->t_lo, dt);
@@ -966,6 +967,7 @@ int mh_dd_step_batch(mh_dd *sim, int64_t nsteps, int n_iter)
     if (n_iter < 1 || n_iter > 64) { set_error("mh_dd_step_batch: n_iter must be in [1, 64]"); return MH_EINVAL; }
     if (nsteps < 0) { set_error("mh_dd_step_batch: nsteps must be >= 0"); return MH_EINVAL; }
     if (int rc = injected_step_fault("mh_dd_step_batch")) return rc;
+    NvtxScope range("mh_dd_step_batch");
     if (nsteps == 0) return MH_OK;
     if (int rc = dd_advance(sim, 0.0, n_iter, nsteps)) return rc;     // the steps come from dts
     sim->batch_steps += nsteps;
