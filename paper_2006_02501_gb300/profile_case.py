@@ -10,6 +10,10 @@ pair-symmetric kernel (k_pair_fp64_sym) for P <= 3 unless --ordered is given;
 the 8th-order initialisation's last pass (P = 5) always runs k_pair_fp64.
 --precision dd runs the double-double form (mh_dd_*) on the same disc; its
 initialisation also launches one evaluation (k_dd_pair) per pass.
+--precision all runs one step of every form on the same small disc (for a
+memory checker): FP64 with the pair-symmetric and the ordered kernel, the
+FP32-pair form with both (orders up to 8), the double-double form, and a
+double-double batch of three systems cut from the disc.
 """
 import argparse
 import os
@@ -21,7 +25,7 @@ import numpy as np
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--N", type=int, default=16384)
-    ap.add_argument("--precision", choices=["fp64", "fp32pair", "dd"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "fp32pair", "dd", "all"], default="fp64")
     ap.add_argument("--order", type=int, default=8)
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--n-iter", type=int, default=3)
@@ -33,6 +37,28 @@ def main():
     from paper_2006_02501_gb300 import inputs
     mh.build_library()
     m, x, v = inputs.smbh_disc(seed=2, N=a.N)
+    dt = 2 * np.pi * 1e-3
+    if a.precision == "all":
+        runs = [("fp64 pair-symmetric", mh.MH_PREC_FP64, 2), ("fp64 ordered", mh.MH_PREC_FP64, 0)]
+        if a.order <= 8:
+            runs += [("fp32pair pair-symmetric", mh.MH_PREC_FP32PAIR, 2), ("fp32pair ordered", mh.MH_PREC_FP32PAIR, 0)]
+        for name, prec, sym in runs:
+            with mh.Simulation(a.order, m, x, v, 1e-4, precision=prec, symmetric=sym) as sim:
+                sim.step(dt, a.n_iter, nsteps=a.steps)
+                sim.diagnostics(central=0)
+                ok = bool(np.isfinite(sim.sync()[1]).all())
+            print(f"ok {name} N={len(m)} order {a.order} finite={ok}")
+        with mh.DDSimulation(a.order, m, x, v, 1e-4) as sim:
+            sim.step(dt, a.n_iter, nsteps=a.steps)
+            sim.diagnostics(central=0)
+            print(f"ok dd N={len(m)} order {a.order} finite={bool(np.isfinite(sim.sync()[1]).all())}")
+        off = np.array([0, 1, 3, min(len(m), 64)], dtype=np.int64)
+        k = int(off[-1])
+        with mh.DDBatch(a.order, off, m[:k], x[:k], v[:k], np.full(3, dt), 1e-4) as b:
+            b.step(a.steps, a.n_iter)
+            b.energies()
+            print(f"ok dd batch systems {np.diff(off).tolist()} finite={bool(np.isfinite(b.sync()[1]).all())}")
+        return
     if a.precision == "dd":
         with mh.DDSimulation(a.order, m, x, v, 1e-4) as sim:
             sim.step(2 * np.pi * 1e-3, a.n_iter, nsteps=a.steps)
