@@ -242,3 +242,15 @@ def test_dd_header_constants_exact(orc, p):
                 got = H[("e", p, n, k)][0 if side else 1]
                 want = _frac(out[n, 0])
                 assert abs(got - want) <= Fraction(1, 10 ** 20) * max(1, abs(want)), (p, n, k, side)
+
+
+def test_dd_header_is_the_derivation_scripts_output():
+    """The committed hermite_consts_dd.cuh is exactly what
+    `derive_constants.py --dd-header` writes."""
+    pytest.importorskip("sympy")
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("derive_constants", os.path.join(CSRC, "derive_constants.py"))
+    D = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(D)
+    with open(os.path.join(CSRC, "hermite_consts_dd.cuh")) as f:
+        assert f.read() == D.dd_header()
