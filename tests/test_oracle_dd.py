@@ -11,6 +11,7 @@ binary128.  It is pinned to things other than itself:
   - Kepler's equation, solved to 45 digits with mpmath: the position error
     after one e = 0.5 orbit keeps falling at the scheme's order (8 and 12) to
     1e-16 and 1e-21, where the FP64 oracle has stalled at its round-off;
+  - time symmetry: 100 steps forward and back return to the start to 1e-30;
   - Section 3.1's Kepler test (a = 1, e = 0.1, dt = 2^-4, n = 3): the 10th- and
     12th-order schemes keep the energy error 1e-3 to 1e-7 times below the FP64
     run's round-off level, the extended-precision case of the Discussion.
@@ -254,3 +255,19 @@ def test_dd_header_is_the_derivation_scripts_output():
     spec.loader.exec_module(D)
     with open(os.path.join(CSRC, "hermite_consts_dd.cuh")) as f:
         assert f.read() == D.dd_header()
+
+
+@pytest.mark.parametrize("order", [8, 12])
+def test_time_symmetric_to_binary128(orc, order):
+    """The modified Hermite step with converged iterations is time symmetric
+    (Section 2: the corrector's F+ terms are even, the F- terms odd in dt): 100
+    steps forward and 100 back return to the start to ~1e-32, the rounding of
+    the state to a double-double pair between the two runs."""
+    m, x, v = I.kepler_pair(a=1.0, e=0.5, M=1.0, m=1e-3)
+    dt = 2.0 ** -6
+    x2, v2, d2 = orc.dd_run(order, m, x, v, 0.0, dt, 10, 100)
+    xb, vb, _ = orc.dd_run(order, m, x2, v2, 0.0, -dt, 10, 100, d2=d2)
+    assert np.abs((xb[..., 0] - x) + xb[..., 1]).max() < 1e-30
+    assert np.abs((vb[..., 0] - v) + vb[..., 1]).max() < 1e-30
+    # and the run went somewhere: 100 steps are a quarter orbit
+    assert np.abs(orc.dd_value(x2) - x).max() > 0.1
