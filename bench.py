@@ -74,7 +74,7 @@ TRAFFIC = {"files": ["paper_2006_02501_gb300/csrc/pair_sym.cu", "paper_2006_0250
 # k_dd_pair<3, false>, from one ncu capture (profiles/), valid while its source is
 # the one captured.
 DD_INSTR = {"files": ["paper_2006_02501_gb300/csrc/dd.cu", "paper_2006_02501_gb300/csrc/dd.cuh"],
-            "sha256": ["ed83fc0fb1169f1c8504bf1b5f8b961dad72e69cdd19dec63ba1621dc974c196",
+            "sha256": ["484799a2627abe3b09e9f8f0f2bed35222b21dc59113afc036cbd166be9ade2a",
                        "fc820299535e960effdf3d75b248976e124a70606f221bffac1d8e3395d01bd7"],
             # profiles/k_dd_pair_disc_N4096_order8.md: 30.19e9 FP64 thread instructions
             # for 4097 x 4096 ordered pairs

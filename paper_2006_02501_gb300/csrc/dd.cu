@@ -25,9 +25,11 @@
 //   k_dd_pair<P, true>   the same sums for the initialisation passes P = 7, 9,
 //                     keeping only the two orders such a pass stores.
 //   k_dd_predict<p>   one (body, component) per thread.
-//   k_dd_correct<p>   one (body, component) per thread: adds the S partial
-//                     sums, corrects, and on the last pass commits the step and
-//                     interpolates the higher derivatives.
+//   k_dd_reduce_slots<p>  adds the S partial sums in slot order, one thread
+//                     per (body, order, component).
+//   k_dd_correct<p>   one (body, component) per thread: corrects, and on the
+//                     last pass commits the step and interpolates the higher
+//                     derivatives.
 //   k_dd_init_*       the explicit initial derivatives in passes of two orders.
 //   k_dd_energy / k_dd_ecc   diagnostics (Appendix A) in double-double.
 // Batched form (mh_dd_create_batch): many independent systems of up to 64
@@ -55,7 +57,7 @@ namespace {
 constexpr int kDDThreads = 128;
 constexpr int kDDJTile = 32;
 constexpr int kDDTargetCtas = 152 * 8;   // evaluation grid: a few waves over the 152 SMs
-constexpr int kDDMinJ = 4;               // fewest j per chunk (bounds the partial-sum traffic)
+constexpr int kDDMinJ = 1;               // fewest j per chunk: small systems spread one pair per thread
 constexpr int kDDSysMax = 64;            // batched form: bodies per system (one CTA each)
 
 __device__ __forceinline__ dd ld2(const double2 *p)
@@ -299,6 +301,23 @@ k_dd_pair_sys(const double2 *__restrict__ tr, const double *__restrict__ m, cons
         for (int c = 0; c < 3; ++c) acc[k][c] = dd(0.0);
     dd_pair_sum<P, kTop2>(sj, sm, n, t, sj + t * R, eps2, G, acc);
     dd_store_sums<P, kTop2>(part + (size_t)(b0 + t) * R, acc);
+}
+
+// Adds the S partial-sum slots of a^(0..p) in slot order into slot 0, one
+// thread per (body, order, component), so that the corrector reads one slot.
+// (A serial sum of S slots for all p + 1 orders in every corrector thread is a
+// chain of S (p + 1) double-double additions, each ~20 FP64 instructions of
+// ~64 cycles per warp on GB300: the latency of small systems.)
+template <int p>
+__global__ void __launch_bounds__(kDDThreads)
+k_dd_reduce_slots(double2 *__restrict__ part, int S, int N)
+{
+    constexpr int R = (p + 1) * 3;
+    const int64_t t = (int64_t)blockIdx.x * kDDThreads + threadIdx.x;
+    if (t >= (int64_t)N * R) return;
+    dd s = ld2(&part[t]);
+    for (int q = 1; q < S; ++q) s += ld2(&part[(size_t)q * N * R + t]);
+    st2(&part[t], s);
 }
 
 // ---- predictor ----
@@ -596,14 +615,20 @@ int launch_dd_step_p(double2 *x, double2 *v, double2 *d, double2 *tr, double2 *p
                      const DDBatchDev *b)
 {
     const DDPlan pl = dd_plan(N);
-    const int slots = b ? 1 : pl.S;
+    const bool reduce = !b && pl.S > 1;
+    const int slots = 1;                       // the corrector reads slot 0 (pre-summed when S > 1)
     const double *dts = b ? b->dts : nullptr;
     const int *sys = b ? b->sys : nullptr;
     const int nb = (3 * N + kDDThreads - 1) / kDDThreads;
+    const int nr = (int)(((int64_t)N * (p + 1) * 3 + kDDThreads - 1) / kDDThreads);
     k_dd_predict<p><<<nb, kDDThreads, 0, st>>>(x, v, d, N, dt, dts, sys, tr);
     MH_LAUNCHED("k_dd_predict");
     for (int it = 0; it < n_iter; ++it) {
         if (int rc = launch_dd_pair(p, tr, m, N, eps, G, pl, part, st, b)) return rc;
+        if (reduce) {
+            k_dd_reduce_slots<p><<<nr, kDDThreads, 0, st>>>(part, pl.S, N);
+            MH_LAUNCHED("k_dd_reduce_slots");
+        }
         if (it + 1 < n_iter)
             k_dd_correct<p, false><<<nb, kDDThreads, 0, st>>>(x, v, d, part, slots, N, dt, dts, sys, bm, tr, flag);
         else
@@ -772,7 +797,8 @@ void dd_count(mh_dd *sim, int n_iter, int64_t nsteps, double pairs_per_eval)
     sim->ctr.evaluations += nsteps * n_iter;
     sim->ctr.pair_interactions += (double)nsteps * n_iter * pairs_per_eval;
     sim->ctr.particle_steps += (double)nsteps * (double)sim->N;
-    sim->ctr.kernel_launches += nsteps * (1 + 2 * n_iter);
+    const bool reduce = !sim->S && dd_plan((int)sim->N).S > 1;
+    sim->ctr.kernel_launches += nsteps * (1 + (reduce ? 3 : 2) * n_iter);
 }
 
 int dd_check_flag(mh_dd *s)
