@@ -391,7 +391,11 @@ class DDSimulation:
             _capi.lib().mh_dd_destroy(self._h)
             self._h = None
 
-    __del__ = close
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
     def __enter__(self):
         return self
