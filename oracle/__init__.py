@@ -345,6 +345,7 @@ def _lib_q_handle():
             lib.orq_hermite_interp.argtypes = [i, d, _D, _D, i, _D]
             lib.orq_run.argtypes = [i, i, i, i, d, i, _D, d, d, i, _D, _D, _D]
             lib.orq_energy.argtypes = [i, _D, _D, _D, d, d, _D]
+            lib.orq_evaluate.argtypes = [i, i, _D, _D, d, d, i, i, _D]
             lib.orq_ecc.argtypes = [i, _D, _D, _D, d, i, _D]
             _lib_q = lib
     return _lib_q
@@ -394,6 +395,17 @@ def dd_run(order: int, m, x2, v2, eps: float, dt: float, n_iter: int, nsteps: in
     _lib_q_handle().orq_run(N, p, 0 if modified else 1, n_iter, dt, nsteps, _p(m), eps, G,
                             1 if init else 0, _p(x2), _p(v2), _p(d2))
     return x2, v2, d2
+
+
+def dd_evaluate(m, traj2, eps: float, G: float = 1.0, i0: int = 0, i1: int | None = None) -> np.ndarray:
+    """Direct-summation a^(0..P) in binary128 for bodies i0..i1-1 (pairs out):
+    traj2 (N, P+1, 3, 2) trajectory pairs x, v, a, ...; returns (i1-i0, P+1, 3, 2)."""
+    m, traj2 = _f64(m), _f64(traj2)
+    N, K = traj2.shape[0], traj2.shape[1]
+    i1 = N if i1 is None else i1
+    out = np.zeros((i1 - i0, K, 3, 2))
+    _lib_q_handle().orq_evaluate(N, K - 1, _p(m), _p(traj2), eps, G, i0, i1, _p(out))
+    return out
 
 
 def dd_energy(m, x2, v2, eps: float, G: float = 1.0) -> np.ndarray:

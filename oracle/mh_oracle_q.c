@@ -241,6 +241,31 @@ static void qevaluate(int N, int P, const double *m, const Q *tr, Q eps2, Q G, Q
     }
 }
 
+/* out_i^(n) = sum_{j != i} pair derivatives for i in [i0, i1) only (sampled
+ * checks at sizes where every i would be too slow).  tr2: N x (P+1) x 3 x 2
+ * trajectory pairs; out2: (i1-i0) x (P+1) x 3 x 2. */
+void orq_evaluate(int N, int P, const double *m, const double *tr2, double eps, double G, int i0, int i1,
+                  double *out2)
+{
+    const int K = P + 1;
+    Q *tr = (Q *)malloc((size_t)N * K * 3 * sizeof(Q));
+    for (size_t q = 0; q < (size_t)N * K * 3; ++q) tr[q] = q_in(tr2 + 2 * q);
+    const Q eps2 = (Q)eps * (Q)eps;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = i0; i < i1; ++i) {
+        Q acc[(ORQ_MAXP + 1) * 3], r[(ORQ_MAXP + 1) * 3], d[(ORQ_MAXP + 1) * 3];
+        for (int q = 0; q < K * 3; ++q) acc[q] = 0;
+        for (int j = 0; j < N; ++j) {
+            if (j == i) continue;
+            for (int q = 0; q < K * 3; ++q) r[q] = tr[(size_t)j * K * 3 + q] - tr[(size_t)i * K * 3 + q];
+            qpair_derivs(P, r, eps2, (Q)G * (Q)m[j], d);
+            for (int q = 0; q < K * 3; ++q) acc[q] += d[q];
+        }
+        for (int q = 0; q < K * 3; ++q) q_out(acc[q], out2 + 2 * ((size_t)(i - i0) * K * 3 + q));
+    }
+    free(tr);
+}
+
 /* a^(0..2p-1) at the start from x, v in passes of two orders (Section 3 intro). */
 static void qinitialise(int N, int p, const double *m, const Q *x, const Q *v, Q eps2, Q G, Q *derivs)
 {

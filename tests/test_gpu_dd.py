@@ -198,3 +198,22 @@ def test_dd_argument_errors(mh):
         assert L.mh_dd_sync(None, None, None, None, None) == _capi.MH_EINVAL
         n = ctypes.c_int64()
         assert L.mh_dd_info(sim._h, ctypes.byref(n), None, None) == 0 and n.value == 7
+
+
+def test_dd_bench_size_sampled_start(mh, orc):
+    """The double-double form at the size bench.py times (the SMBH disc cut to
+    4096 bodies, 8th order, eps = 1e-4; 32 i-blocks x 38 j-chunks): a and a-dot
+    of the start (the first initialisation pass, from x and v alone) for sampled
+    bodies, including the SMBH and the last i-block's tail, against binary128 sums
+    over all 4096 bodies.  Tolerance 1e-26 of each row: the SMBH's acceleration
+    is a ~30-fold cancelling sum of 4095 star terms."""
+    m, x, v = I.smbh_disc(seed=2, N=4095)
+    with mh.DDSimulation(8, m, x, v, 1e-4) as sim:
+        _, _, _, d2 = sim.sync()
+    tr = np.stack([orc.as_dd(x), orc.as_dd(v)], axis=1)
+    for i0, i1 in ((0, 3), (1000, 1001), (2047, 2049), (4093, 4096)):
+        ref = orc.dd_evaluate(m, tr, 1e-4, 1.0, i0, i1)
+        for k in range(2):
+            diff = np.linalg.norm(dd_diff(d2[i0:i1, k], ref[:, k]), axis=-1)
+            scale = np.linalg.norm(ref[:, k, :, 0], axis=-1)
+            assert (diff <= 1e-26 * scale).all(), (i0, k, diff / scale)
