@@ -12,6 +12,8 @@ binary128.  It is pinned to things other than itself:
     after one e = 0.5 orbit keeps falling at the scheme's order (8 and 12) to
     1e-16 and 1e-21, where the FP64 oracle has stalled at its round-off;
   - time symmetry: 100 steps forward and back return to the start to 1e-30;
+  - closed forms on exact Kepler states: energy -G M m / (2a) and the
+    eccentricity vector (e, 0, 0), to 1e-30;
   - Section 3.1's Kepler test (a = 1, e = 0.1, dt = 2^-4, n = 3): the 10th- and
     12th-order schemes keep the energy error 1e-3 to 1e-7 times below the FP64
     run's round-off level, the extended-precision case of the Discussion.
@@ -271,3 +273,37 @@ def test_time_symmetric_to_binary128(orc, order):
     assert np.abs((vb[..., 0] - v) + vb[..., 1]).max() < 1e-30
     # and the run went somewhere: 100 steps are a quarter orbit
     assert np.abs(orc.dd_value(x2) - x).max() > 0.1
+
+
+def _dd_of(q):
+    hi = float(q)
+    return [hi, float(q - mp.mpf(hi))]
+
+
+@pytest.mark.parametrize("e,M_anom", [(0.5, 1.0), (0.1, 2.5), (0.9, 0.3)])
+def test_energy_and_ecc_closed_forms(orc, e, M_anom):
+    """A two-body state on an exact Kepler orbit (built at 45 digits, rounded to
+    double-double pairs): the barycentric energy is -G M m / (2a) and the
+    eccentricity vector of the companion is (e, 0, 0) (Appendix A, periapsis on
+    the x axis), both to ~1e-30."""
+    M, m_, a, G = 1.0, 1e-3, 1.0, 1.0
+    with mp.workdps(45):
+        mu = mp.mpf(G) * (mp.mpf(M) + mp.mpf(m_))
+        E = mp.mpf(M_anom)
+        for _ in range(100):
+            E -= (E - e * mp.sin(E) - M_anom) / (1 - e * mp.cos(E))
+        b = mp.sqrt(1 - mp.mpf(e) ** 2)
+        r = [a * (mp.cos(E) - e), a * b * mp.sin(E), mp.mpf(0)]
+        w = mp.sqrt(mu / a) / (1 - e * mp.cos(E))
+        u = [-w * mp.sin(E), w * b * mp.cos(E), mp.mpf(0)]
+        Mt = mp.mpf(M) + mp.mpf(m_)
+        f0, f1 = -mp.mpf(m_) / Mt, mp.mpf(M) / Mt
+        x2 = np.array([[_dd_of(f0 * q) for q in r], [_dd_of(f1 * q) for q in r]])
+        v2 = np.array([[_dd_of(f0 * q) for q in u], [_dd_of(f1 * q) for q in u]])
+        E_exact = -mp.mpf(G) * mp.mpf(M) * mp.mpf(m_) / (2 * a)
+        E2 = orc.dd_energy(np.array([M, m_]), x2, v2, 0.0, G)
+        assert abs((mp.mpf(E2[0]) + mp.mpf(E2[1]) - E_exact) / E_exact) < 1e-30
+        e2 = orc.dd_ecc(np.array([M, m_]), x2, v2, G, 0)
+        got = [mp.mpf(e2[1, c, 0]) + mp.mpf(e2[1, c, 1]) for c in range(3)]
+        assert abs(got[0] - e) < 1e-30 and abs(got[1]) < 1e-30 and got[2] == 0
+        assert not e2[0].any()
