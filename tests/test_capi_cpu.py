@@ -114,3 +114,52 @@ def test_create_batch_argument_checks(L):
                            ptr(m), ptr(x), ptr(x), ptr(dt), 1e-3, 6, None, None)
     assert rc == -1
     assert L.mh_step_batch(None, 10, 2) == -1
+
+
+def test_double_double_and_restore_arguments_rejected_before_device_use(L):
+    from paper_2006_02501_gb300 import _capi
+    dp = ctypes.POINTER(ctypes.c_double)
+    ptr = lambda a: None if a is None else a.ctypes.data_as(dp)
+    m = np.ones(3)
+    x2 = np.zeros((3, 3, 2))
+    x2[:, 0, 0] = [0.0, 1.0, 2.0]
+    v2 = np.zeros((3, 3, 2))
+    h = ctypes.c_void_p()
+    assert L.mh_dd_create(ctypes.byref(h), 3, 7, ptr(m), ptr(x2), ptr(v2), 0.0, None, None) == _capi.MH_EINVAL
+    assert L.mh_dd_create(ctypes.byref(h), 3, 8, ptr(m), None, ptr(v2), 0.0, None, None) == _capi.MH_EINVAL
+    assert L.mh_dd_create(ctypes.byref(h), 3, 8, ptr(m), ptr(x2), ptr(v2), -1.0, None, None) == _capi.MH_EINVAL
+    bad = x2.copy()
+    bad[1, 2, 1] = np.inf                       # a non-finite low word
+    assert L.mh_dd_create(ctypes.byref(h), 3, 8, ptr(m), ptr(bad), ptr(v2), 0.0, None, None) == _capi.MH_ENONFINITE
+    assert not h.value
+    i64 = ctypes.POINTER(ctypes.c_int64)
+    off = np.array([0, 65], dtype=np.int64)      # one system of 65 bodies
+    mm, xx, vv = np.ones(65), np.zeros((65, 3, 2)), np.zeros((65, 3, 2))
+    dt = np.array([0.01])
+    assert L.mh_dd_create_batch(ctypes.byref(h), 1, off.ctypes.data_as(i64), ptr(mm), ptr(xx), ptr(vv), ptr(dt),
+                                0.0, 8, None, None) == _capi.MH_EINVAL
+    off = np.array([0, 2, 3], dtype=np.int64)
+    dt = np.array([0.01, 0.0])                   # a zero step
+    assert L.mh_dd_create_batch(ctypes.byref(h), 2, off.ctypes.data_as(i64), ptr(m), ptr(x2), ptr(v2), ptr(dt),
+                                0.0, 8, None, None) == _capi.MH_EINVAL
+    assert L.mh_dd_step(None, 0.01, 3, 1) == _capi.MH_EINVAL
+    assert L.mh_dd_step_batch(None, 1, 3) == _capi.MH_EINVAL
+    assert L.mh_dd_batch_energy(None, None) == _capi.MH_EINVAL
+    L.mh_dd_destroy(None)
+    # mh_restore needs x, v and derivs before anything is created
+    st = _capi.StateC(0.0, ptr(np.zeros((3, 3))), ptr(np.zeros((3, 3))), None, None)
+    assert L.mh_restore(ctypes.byref(h), 3, 8, ptr(m), ctypes.byref(st), 0.0, None, None) == _capi.MH_EINVAL
+    assert not h.value
+
+
+def test_double_double_marshalling():
+    from paper_2006_02501_gb300 import _dd_host
+    x = np.arange(12.0).reshape(4, 3)
+    x2 = _dd_host(x, 4)
+    assert x2.shape == (4, 3, 2) and np.array_equal(x2[..., 0], x) and not x2[..., 1].any()
+    assert x2.flags.c_contiguous
+    pairs = np.random.default_rng(0).normal(size=(4, 3, 2))
+    assert np.array_equal(_dd_host(pairs, 4), pairs)
+    d = np.arange(4 * 6 * 3, dtype=float).reshape(4, 6, 3)
+    d2 = _dd_host(d, 4, 18)
+    assert d2.shape == (4, 18, 2) and np.array_equal(d2[..., 0].reshape(4, 6, 3), d)
