@@ -400,6 +400,18 @@ int mh_set_timing(mh_sim *sim, int on);
 /* Message describing the calling thread's most recent error ("" if none). */
 const char *mh_last_error(void);
 
+/* Host-side check of the pair-symmetric evaluation's schedule (not part of the
+ * paper's method; no device is used).  The shared-step evaluation of N bodies
+ * (padded to a multiple of 256) adds every block's j-side sums into one slot per
+ * row chunk, row after row in a fixed order, each row waiting for its turn.
+ * For `slots` resident CTAs this rebuilds the plan the library would use and
+ * checks that every slot's writers hold the turns 0 .. n-1 once each and that no
+ * turn waits on a writer that could be waiting on it.  Returns MH_OK, a positive
+ * code naming the violated property, or MH_EINVAL; info (6 ints, NULL ok)
+ * receives blocks, row chunks, distances per chunk, 1 for the all-resident
+ * distance order (else 0), the grid and the accumulation chains per chunk. */
+int mh_sym_schedule_check(int64_t N, int slots, int *info);
+
 /* ------------------------------------------------------------------------- */
 /* Kernel-level entry points on caller-owned DEVICE memory.                   */
 /* ------------------------------------------------------------------------- */
@@ -409,7 +421,8 @@ const char *mh_last_error(void);
  *   traj: device, SoA, (P+1)*3 rows of N doubles: row 3k+c holds component c of
  *         the k-th trajectory derivative (x, v, a, a-dot) of every body;
  *   m:    device, N masses;  out: device, (P+1)*3 rows of (i1-i0) doubles.
- *   P = 1, 2 or 3; precision as in mh_config.  Uses scratch memory that the
+ *   P = 1 .. 5 in the FP64 form (MH_PREC_FP64), 1 .. 3 in the precision form
+ *   (MH_PREC_FP32PAIR); precision as in mh_config.  Uses scratch memory that the
  *   library allocates and caches per device (freed by mh_release_scratch).
  *   Stream-ordered on `stream` (a cudaStream_t, NULL = legacy default stream). */
 int mh_pair_eval(int P, int precision, int64_t N, const double *m, const double *traj,
@@ -431,7 +444,9 @@ int mh_release_scratch(void);
  *   a message naming the bytes it needed; nothing is launched then.
  *   The first call on each device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.
+ *   before any stream capture.  The address is kept for the rest of the
+ *   process: a device reset (cudaDeviceReset) is not supported without
+ *   unloading and reloading the library, as the array may move.
  *   All calls on a device share the one array and it keeps the previous call's
  *   contents; the entry point clears what must start at zero.  Calls whose
  *   work overlaps on the GPU (different streams, or several host threads) race

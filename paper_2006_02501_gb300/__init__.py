@@ -503,3 +503,13 @@ def measure_peaks() -> dict:
     out = (ctypes.c_double * 4)()
     check(_capi.lib().mh_measure_peaks(out))
     return {"fp64_tflops": out[0], "fp32_tflops": out[1], "fp32x2_tflops": out[2], "rsqrt_tera_per_s": out[3]}
+
+
+def sym_schedule_check(N: int, slots: int) -> dict:
+    """Host-side check of the pair-symmetric evaluation's ordered accumulation
+    for N bodies and `slots` resident CTAs (mh_sym_schedule_check; no device
+    needed).  Raises MHError when a property fails; returns the plan."""
+    info = (ctypes.c_int * 6)()
+    check(_capi.lib().mh_sym_schedule_check(int(N), int(slots), info))
+    return {"blocks": info[0], "chunks": info[1], "distances_per_chunk": info[2], "cyclic": bool(info[3]),
+            "grid": info[4], "chains": info[5]}

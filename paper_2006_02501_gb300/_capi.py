@@ -35,6 +35,7 @@ EXPORTS = [
     "mh_mlp_loss_grad", "mh_mlp_train", "mh_predict", "mh_step_timesym", "mh_measure_peaks",
     "mh_dd_create", "mh_dd_destroy", "mh_dd_step", "mh_dd_sync", "mh_dd_set_state", "mh_dd_diagnostics",
     "mh_dd_info", "mh_dd_create_batch", "mh_dd_step_batch", "mh_dd_batch_energy", "mh_restore",
+    "mh_sym_schedule_check",
 ]
 
 
@@ -104,6 +105,7 @@ def lib() -> ctypes.CDLL:
             L.mh_pair_eval_noalloc.argtypes = [I, I, I64, P, P, D, D, I64, I64, P, P]
             I64P = ctypes.POINTER(ctypes.c_int64)
             IP = ctypes.POINTER(ctypes.c_int)
+            L.mh_sym_schedule_check.argtypes = [I64, I, IP]
             L.mh_create_batch.argtypes = [ctypes.POINTER(P), I64, I64P, DP, DP, DP, DP, D, I,
                                           ctypes.POINTER(Config), P]
             L.mh_step_batch.argtypes = [P, I64, I]

@@ -80,7 +80,7 @@ int dalloc(T **ptr, size_t count)
 void free_state(DeviceState &s)
 {
     void *ptrs[] = {s.m, s.x0, s.v0, s.d0, s.x1, s.v1, s.jrec, s.jrec32, s.part, s.diag, s.flag, s.bound,
-                    s.heavy, s.T, s.level, s.act, s.blk, s.tsw, s.tst, s.comp};
+                    s.heavy, s.T, s.level, s.act, s.blk, s.tsw, s.tst, s.comp, s.symsync};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (s.blk_host) cudaFreeHost(s.blk_host);
@@ -116,6 +116,40 @@ int ensure_part(DeviceState &s, size_t need, cudaStream_t st)
     int rc = dalloc(&s.part, need);
     if (rc) return rc;
     s.part_doubles = need;
+    return MH_OK;
+}
+
+// Make sure the ordered-accumulation counters of the pair-symmetric evaluation
+// hold `words` words; new words start at 0 (the state between launches).
+int ensure_symsync(DeviceState &s, size_t words, cudaStream_t st)
+{
+    if (words <= s.symsync_words) return MH_OK;
+    if (s.symsync) {
+        MH_CUDA(cudaStreamSynchronize(st));
+        cudaFree(s.symsync);
+        s.symsync = nullptr;
+        s.symsync_words = 0;
+    }
+    if (int rc = dalloc(&s.symsync, words)) return rc;
+    MH_CUDA(cudaMemsetAsync(s.symsync, 0, words * sizeof(unsigned), st));
+    s.symsync_words = words;
+    return MH_OK;
+}
+
+// Partial sums and counters of one pair-symmetric launch.  MH_FAULT=symwait
+// (tests of the timeout path) makes every wait of the launch unsatisfiable and
+// its limit 20 ms, so the launch ends with kFlagSymWait set.
+int prepare_sym(mh_sim *sim, const SymPlan &sp, int extra_slots, int P, SymSync *sy)
+{
+    DeviceState &s = sim->s;
+    if (int rc = ensure_part(s, (size_t)(sp.slots + extra_slots) * (P + 1) * 3 * s.Np, sim->stream)) return rc;
+    if (int rc = ensure_symsync(s, (size_t)sp.sync_words, sim->stream)) return rc;
+    sy->words = s.symsync;
+    sy->flag = s.flag;
+    if (fault_armed("symwait")) {
+        sy->bias = 0x40000000u;
+        sy->wait_ns = 20000000ull;
+    }
     return MH_OK;
 }
 
@@ -215,16 +249,17 @@ int evaluate(mh_sim *sim, int P, int precision, int *split, unsigned long long *
     const int sym_mode = sim->cfg.symmetric;
     if (precision == MH_PREC_FP64 && P <= 5 && (sym_mode == 2 || (sym_mode == 1 && s.Np >= kSymMinNp))) {
         const SymPlan sp = plan_sym(P, s.Np, sim->device);
-        const size_t need = (size_t)sp.slots * (P + 1) * 3 * s.Np;
-        if (sp.nB > 0 && need * sizeof(double) <= kSymMaxPartBytes) {
-            int rc = ensure_part(s, need, sim->stream);
+        if (sp.nB > 0) {
+            SymSync sy;
+            int rc = prepare_sym(sim, sp, 0, P, &sy);
             if (rc) return rc;
             std::pair<cudaEvent_t, cudaEvent_t> ev{};
             if (sim->timing) {
                 if ((rc = timed_event_pair(sim, &ev))) return rc;
                 MH_CUDA(cudaEventRecord(ev.first, sim->stream));
             }
-            rc = launch_pair_sym(P, sp, s.jrec, s.m, s.Np, s.N, sim->eps, sim->cfg.G, s.part, sim->stream, wslot);
+            rc = launch_pair_sym(P, sp, sy, s.jrec, s.m, s.Np, s.N, sim->eps, sim->cfg.G, s.part, sim->stream,
+                                 wslot);
             if (rc) return rc;
             if (sim->timing) {
                 MH_CUDA(cudaEventRecord(ev.second, sim->stream));
@@ -243,16 +278,16 @@ int evaluate(mh_sim *sim, int P, int precision, int *split, unsigned long long *
         const SymPlan sp = plan_sym(P, s.Np, sim->device, true);
         const bool heavy = s.n_heavy > 0;
         const int slots = sp.slots + (heavy ? 1 : 0);
-        const size_t need = (size_t)slots * (P + 1) * 3 * s.Np;
-        if (sp.nB > 0 && need * sizeof(double) <= kSymMaxPartBytes) {
-            int rc = ensure_part(s, need, sim->stream);
+        if (sp.nB > 0) {
+            SymSync sy;
+            int rc = prepare_sym(sim, sp, heavy ? 1 : 0, P, &sy);
             if (rc) return rc;
             std::pair<cudaEvent_t, cudaEvent_t> ev{};
             if (sim->timing) {
                 if ((rc = timed_event_pair(sim, &ev))) return rc;
                 MH_CUDA(cudaEventRecord(ev.first, sim->stream));
             }
-            if ((rc = launch_pair_sym32(P, sp, s.jrec32, s.Np, s.N, sim->eps, s.part, sim->stream))) return rc;
+            if ((rc = launch_pair_sym32(P, sp, sy, s.jrec32, s.Np, s.N, sim->eps, s.part, sim->stream))) return rc;
             if (sim->timing) {
                 MH_CUDA(cudaEventRecord(ev.second, sim->stream));
                 sim->ev_pending.push_back(ev);
@@ -409,6 +444,15 @@ void mh_config_default(mh_config *cfg)
 }
 
 const char *mh_last_error(void) { return g_last_error.c_str(); }
+
+int mh_sym_schedule_check(int64_t N, int slots, int *info)
+{
+    if (N < 1 || slots < 1) {
+        set_error("mh_sym_schedule_check: N and slots must be positive");
+        return MH_EINVAL;
+    }
+    return sym_schedule_check(pad_to(N, kPad), slots, info);
+}
 
 }  // extern "C"
 
@@ -981,6 +1025,16 @@ static int check_flag(mh_sim *sim)
     int flag = 0;
     MH_CUDA(cudaMemcpyAsync(&flag, sim->s.flag, sizeof(int), cudaMemcpyDeviceToHost, sim->stream));
     MH_CUDA(cudaStreamSynchronize(sim->stream));
+    if (flag & kFlagSymWait) {
+        // the ordered accumulation's counters may be left mid-way: clear them for
+        // later launches; the state itself is invalid and stays flagged
+        DeviceState &s = sim->s;
+        if (s.symsync) MH_CUDA(cudaMemsetAsync(s.symsync, 0, s.symsync_words * sizeof(unsigned), sim->stream));
+        MH_CUDA(cudaStreamSynchronize(sim->stream));
+        set_error("a pair-symmetric evaluation waited longer than its limit for its turn to add its sums; "
+                  "the state is invalid");
+        return MH_ETIMEOUT;
+    }
     if (flag) {
         set_error("non-finite position or velocity produced by a step");
         return MH_ENONFINITE;
@@ -1035,6 +1089,7 @@ int mh_set_state(mh_sim *sim, const mh_state *in)
     to_soa(in->v, s.N, 1, s.Np, h, 0.0);
     MH_CUDA(cudaMemcpy(s.v0, h.data(), 3 * s.Np * sizeof(double), cudaMemcpyHostToDevice));
     MH_CUDA(cudaMemsetAsync(s.flag, 0, sizeof(int), sim->stream));
+    if (s.symsync) MH_CUDA(cudaMemsetAsync(s.symsync, 0, s.symsync_words * sizeof(unsigned), sim->stream));
     if (int rc = upload_bounds(s, in->x, in->v, sim->stream)) return rc;
     sim->t = in->t;
     if (s.tst) MH_CUDA(cudaMemcpy(s.tst, &in->t, sizeof(double), cudaMemcpyHostToDevice));

@@ -126,14 +126,17 @@ struct DeviceState {
     int ts_prev = 0;
     // Compensated summation (Section 3.2): [6][Np] carried compensation of x, v.
     double *comp = nullptr;
+    // Pair-symmetric evaluation: the item counter and the per-(chunk, block)
+    // write counters of its ordered j-side accumulation (all 0 between launches).
+    unsigned *symsync = nullptr;
+    size_t symsync_words = 0;
 };
 
 constexpr int kMaxHeavy = 32;
 
-// Largest partial-sum buffer the pair-symmetric evaluation may use (about
-// 0.375 Np^2 bytes at order 8, i.e. Np up to ~146k); above it the one-sided
-// kernel runs.
-constexpr size_t kSymMaxPartBytes = (size_t)8 << 30;
+// Bits of the device status word (DeviceState::flag).
+constexpr int kFlagNonFinite = 1;   // a step produced a non-finite position or velocity
+constexpr int kFlagSymWait = 2;     // a pair-symmetric evaluation's bounded wait ran out
 // Smallest padded body count for which symmetric = 1 picks the pair-symmetric
 // kernel (16 blocks of 128 bodies, 144 block pairs).
 constexpr int64_t kSymMinNp = 2048;
@@ -244,21 +247,42 @@ PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hin
 // All-pairs FP64 evaluation that computes each unordered pair once (pair_sym.cu),
 // P = 1 .. 5 (the precision form's, P = 1 .. 3).
 // Valid (nB > 0) when ld is a positive multiple of its 128-body block; writes
-// `slots` partial-sum slots of (P+1)*3 rows of stride ld, every one of them in full.
+// `slots` = C (1 + G) partial-sum slots of (P+1)*3 rows of stride ld, every one
+// of them in full: C i-side slots (one per row chunk) and C G j-side slots (per
+// row chunk and chain), each accumulated by several rows in a fixed order.
 struct SymPlan {
-    int nB = 0, D = 0, C = 0, Bc = 0;   // blocks, distances, row chunks, blocks per chunk
+    int nB = 0, D = 0, C = 0, Bc = 0;   // blocks, distances, row chunks, distances per chunk
+    int G = 1;                          // accumulation chains per chunk (writer rows by row mod G)
     int grid = 0;
-    int slots = 0;                      // C + D
+    bool cyclic = false;                // one item per CTA, all resident (else items handed out in row order)
+    int slots = 0;                      // C (1 + G)
+    int sync_words = 0;                 // 1 + C G nB counters of the ordered accumulation
 };
 SymPlan plan_sym(int P, int64_t ld, int device, bool fp32 = false);
+// The same plan for a given number of resident CTAs (host only).
+SymPlan plan_sym_slots(int64_t ld, int slots);
+// Checks of a plan's ordered accumulation (mh_sym_schedule_check).
+int sym_schedule_check(int64_t ld, int slots, int *info);
+// Device words of the ordered accumulation: `words` holds sync_words counters,
+// all 0 between launches (a launch leaves them so); `flag` the simulation's
+// status word, in which a wait that runs out after wait_ns sets kFlagSymWait.
+// bias (0 in normal use) is added to every awaited count: the host's fault
+// injection sets it so that the waits cannot end and must run out.
+struct SymSync {
+    unsigned *words = nullptr;
+    int *flag = nullptr;
+    unsigned long long wait_ns = 4000000000ull;
+    unsigned bias = 0;
+};
 // The precision form's pair-symmetric evaluation (FP32 pairs, FP64 sums), same
 // plan and slots; jrec32 as written by the step kernels (mass row holding G m).
-int launch_pair_sym32(int P, const SymPlan &plan, const float *jrec32, int64_t ld, int64_t N, double eps,
-                      double *part, cudaStream_t st);
+int launch_pair_sym32(int P, const SymPlan &plan, const SymSync &sync, const float *jrec32, int64_t ld,
+                      int64_t N, double eps, double *part, cudaStream_t st);
 // wmax (optional, device): raised to the maximum over pairs of G (m_i + m_j) s^(-3/2)
 // as a bit pattern (the time-step criterion of Section 3.3, Eq. 24).
-int launch_pair_sym(int P, const SymPlan &plan, const double *jrec, const double *m, int64_t ld, int64_t N,
-                    double eps, double G, double *part, cudaStream_t st, unsigned long long *wmax = nullptr);
+int launch_pair_sym(int P, const SymPlan &plan, const SymSync &sync, const double *jrec, const double *m,
+                    int64_t ld, int64_t N, double eps, double G, double *part, cudaStream_t st,
+                    unsigned long long *wmax = nullptr);
 
 // FP64 contributions of the heavy source bodies to every body i < N, written
 // to partial slot `slot` (rows (P+1)*3 of stride ld) of part.

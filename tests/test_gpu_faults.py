@@ -100,3 +100,29 @@ def test_unrelated_fault_names_are_ignored(mh, monkeypatch):
     with mh.Simulation(8, m, x, v, 1e-4) as sim:
         sim.step(dt, 3)
         sim.sync()
+
+
+@pytest.mark.parametrize("N,precision", [(8000, 0), (8000, 1), (40000, 0)])
+def test_ordered_accumulation_wait_runs_out(mh, monkeypatch, N, precision):
+    """The pair-symmetric evaluation's turns are bounded waits.  MH_FAULT=symwait
+    makes every turn unreachable (an awaited count nothing sets) and shortens
+    the limit to 20 ms: the launch must still end, the sync must report
+    MH_ETIMEOUT, and the device must stay usable, a new simulation stepping to
+    the same bits as one that never saw the fault.  8000 bodies: every item
+    resident at once (distance order); 40000 bodies: items handed out in row
+    order over several waves."""
+    from paper_2006_02501_gb300 import _capi
+    m, x, v = I.smbh_disc(seed=52, N=N - 1)
+    dt = 2 * np.pi * 1e-3
+    with mh.Simulation(8, m, x, v, 1e-4, precision=precision) as sim:
+        monkeypatch.setenv("MH_FAULT", "symwait")
+        sim.step(dt, 3)
+        monkeypatch.delenv("MH_FAULT")
+        with pytest.raises(mh.MHError) as e:
+            sim.sync()
+        assert e.value.code == _capi.MH_ETIMEOUT
+    with mh.Simulation(8, m, x, v, 1e-4, precision=precision) as a, \
+            mh.Simulation(8, m, x, v, 1e-4, precision=precision) as b:
+        a.step(dt, 3)
+        b.step(dt, 3)
+        np.testing.assert_array_equal(a.sync()[1], b.sync()[1])

@@ -1,0 +1,47 @@
+"""CPU checks of the pair-symmetric evaluation's ordered accumulation (no GPU).
+
+The shared-step evaluation adds each block's j-side sums into one slot per row
+chunk, row after row in a fixed order; a row waits for its turn.  The library's
+own plan and turn computation are checked here on the host, for every padded
+size from one block up to config-scale discs and several resident-CTA counts
+(152 SMs x 2, 3, 4 CTAs, and small counts that force many waves): each slot's
+writers hold the turns 0 .. n-1 exactly once, slots without writers are the
+ones zeroed, and no turn waits on a writer that could be waiting on it.
+"""
+import pytest
+
+import paper_2006_02501_gb300 as mh
+
+
+SMALL = [1, 2, 129, 256, 257, 511, 700, 1024, 1100, 2048, 3000, 4097, 8000, 8192, 16384, 16385]
+LARGE = [32768, 65537, 100000, 131072, 262144]
+CASES = [(N, s) for N in SMALL for s in (3, 17, 152 * 2, 152 * 3, 152 * 4)] + \
+        [(N, s) for N in LARGE for s in (152 * 3, 152 * 4)]
+
+
+@pytest.mark.parametrize("N,slots", CASES)
+def test_ordered_accumulation_schedule(N, slots):
+    plan = mh.sym_schedule_check(N, slots)
+    nB = (N + 255) // 256 * 2
+    assert plan["blocks"] == nB
+    assert plan["grid"] <= max(slots, nB * plan["chunks"] if plan["cyclic"] else slots)
+    if plan["cyclic"]:
+        # one item per CTA only when every item is resident at once
+        assert nB * plan["chunks"] <= slots
+
+
+def test_slot_memory_is_linear():
+    """The partial sums take C (1 + G) slots, C row chunks and G chains: O(N C),
+    not O(N^2) (the earlier design kept one slot per block distance, Np/256)."""
+    for N in (65537, 262144):
+        for slots in (152 * 3, 152 * 4):
+            plan = mh.sym_schedule_check(N, slots)
+            assert 1 <= plan["chains"] <= 4
+            assert plan["chunks"] * (1 + plan["chains"]) <= 48
+
+
+def test_schedule_check_rejects_bad_arguments():
+    with pytest.raises(mh.MHError):
+        mh.sym_schedule_check(0, 10)
+    with pytest.raises(mh.MHError):
+        mh.sym_schedule_check(100, 0)
