@@ -404,13 +404,16 @@ const char *mh_last_error(void);
  * paper's method; no device is used).  The shared-step evaluation of N bodies
  * (padded to a multiple of 256) adds every block's j-side sums into one slot per
  * row chunk, row after row in a fixed order, each row waiting for its turn.
- * For `slots` resident CTAs this rebuilds the plan the library would use and
+ * For `slots` resident CTAs and the form `precision` (MH_PREC_FP64 or
+ * MH_PREC_FP32PAIR) this rebuilds the plan the library would use and
  * checks that every slot's writers hold the turns 0 .. n-1 once each and that no
  * turn waits on a writer that could be waiting on it.  Returns MH_OK, a positive
- * code naming the violated property, or MH_EINVAL; info (6 ints, NULL ok)
+ * code naming the violated property, or MH_EINVAL; info (7 ints, NULL ok)
  * receives blocks, row chunks, distances per chunk, 1 for the all-resident
- * distance order (else 0), the grid and the accumulation chains per chunk. */
-int mh_sym_schedule_check(int64_t N, int slots, int *info);
+ * distance order (else 0), the grid, the accumulation chains per chunk and the
+ * rows per item.  For the precision form, slots is the number of SMs (one
+ * CTA of six rows each). */
+int mh_sym_schedule_check(int64_t N, int slots, int precision, int *info);
 
 /* ------------------------------------------------------------------------- */
 /* Kernel-level entry points on caller-owned DEVICE memory.                   */

@@ -505,11 +505,12 @@ def measure_peaks() -> dict:
     return {"fp64_tflops": out[0], "fp32_tflops": out[1], "fp32x2_tflops": out[2], "rsqrt_tera_per_s": out[3]}
 
 
-def sym_schedule_check(N: int, slots: int) -> dict:
+def sym_schedule_check(N: int, slots: int, precision: int = MH_PREC_FP64) -> dict:
     """Host-side check of the pair-symmetric evaluation's ordered accumulation
-    for N bodies and `slots` resident CTAs (mh_sym_schedule_check; no device
-    needed).  Raises MHError when a property fails; returns the plan."""
-    info = (ctypes.c_int * 6)()
-    check(_capi.lib().mh_sym_schedule_check(int(N), int(slots), info))
+    for N bodies, `slots` resident CTAs and a form (MH_PREC_FP64 or
+    MH_PREC_FP32PAIR) (mh_sym_schedule_check; no device needed).  Raises
+    MHError when a property fails; returns the plan."""
+    info = (ctypes.c_int * 7)()
+    check(_capi.lib().mh_sym_schedule_check(int(N), int(slots), int(precision), info))
     return {"blocks": info[0], "chunks": info[1], "distances_per_chunk": info[2], "cyclic": bool(info[3]),
-            "grid": info[4], "chains": info[5]}
+            "grid": info[4], "chains": info[5], "rows_per_item": info[6]}

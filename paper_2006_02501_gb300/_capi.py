@@ -105,7 +105,7 @@ def lib() -> ctypes.CDLL:
             L.mh_pair_eval_noalloc.argtypes = [I, I, I64, P, P, D, D, I64, I64, P, P]
             I64P = ctypes.POINTER(ctypes.c_int64)
             IP = ctypes.POINTER(ctypes.c_int)
-            L.mh_sym_schedule_check.argtypes = [I64, I, IP]
+            L.mh_sym_schedule_check.argtypes = [I64, I, I, IP]
             L.mh_create_batch.argtypes = [ctypes.POINTER(P), I64, I64P, DP, DP, DP, DP, D, I,
                                           ctypes.POINTER(Config), P]
             L.mh_step_batch.argtypes = [P, I64, I]

@@ -445,13 +445,13 @@ void mh_config_default(mh_config *cfg)
 
 const char *mh_last_error(void) { return g_last_error.c_str(); }
 
-int mh_sym_schedule_check(int64_t N, int slots, int *info)
+int mh_sym_schedule_check(int64_t N, int slots, int precision, int *info)
 {
-    if (N < 1 || slots < 1) {
-        set_error("mh_sym_schedule_check: N and slots must be positive");
+    if (N < 1 || slots < 1 || (precision != MH_PREC_FP64 && precision != MH_PREC_FP32PAIR)) {
+        set_error("mh_sym_schedule_check: N and slots must be positive, precision FP64 or FP32-pair");
         return MH_EINVAL;
     }
-    return sym_schedule_check(pad_to(N, kPad), slots, info);
+    return sym_schedule_check(pad_to(N, kPad), slots, precision == MH_PREC_FP32PAIR, info);
 }
 
 }  // extern "C"

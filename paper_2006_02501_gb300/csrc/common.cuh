@@ -253,6 +253,8 @@ PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hin
 struct SymPlan {
     int nB = 0, D = 0, C = 0, Bc = 0;   // blocks, distances, row chunks, distances per chunk
     int G = 1;                          // accumulation chains per chunk (writer rows by row mod G)
+    int K = 1;                          // rows per item (FP32-pair: one CTA of 2K warps sweeps K rows)
+    int items = 0;                      // ceil(nB / K) C
     int grid = 0;
     bool cyclic = false;                // one item per CTA, all resident (else items handed out in row order)
     int slots = 0;                      // C (1 + G)
@@ -260,9 +262,9 @@ struct SymPlan {
 };
 SymPlan plan_sym(int P, int64_t ld, int device, bool fp32 = false);
 // The same plan for a given number of resident CTAs (host only).
-SymPlan plan_sym_slots(int64_t ld, int slots);
+SymPlan plan_sym_slots(int64_t ld, int slots, bool fp32, int kmax);
 // Checks of a plan's ordered accumulation (mh_sym_schedule_check).
-int sym_schedule_check(int64_t ld, int slots, int *info);
+int sym_schedule_check(int64_t ld, int slots, bool fp32, int *info);
 // Device words of the ordered accumulation: `words` holds sync_words counters,
 // all 0 between launches (a launch leaves them so); `flag` the simulation's
 // status word, in which a wait that runs out after wait_ns sets kFlagSymWait.

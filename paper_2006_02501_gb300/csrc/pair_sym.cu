@@ -67,14 +67,17 @@ constexpr int kSymR = 32 * kSymWarps;     // bodies per block
 // Accumulation chains per j-slot: the writer before row I in its chain is row
 // I - G, which reaches the block G sweeps earlier, so a row may run up to G - 1
 // blocks ahead of the rows before it without waiting.
-constexpr int kSymChains = 4;
+constexpr int kSymChains64 = 4;
+// The precision form runs K rows per CTA, one CTA per SM, and one chain (see
+// k_pair_fp32_sym): K = 6 where six rows' shared memory fits, else 4.
 
 // Schedule of one launch (from SymPlan) and the ordered-accumulation words.
 struct SymSched {
     int nB, D, C, Bc;
     int G;                 // accumulation chains per j-slot: writer rows are split by row mod G
+    int K;                 // rows per item (rows qK .. qK + K - 1 of one chunk)
     int cyclic;            // 1: one item per CTA, all resident; writers by descending distance
-    int items;             // nB * C
+    int items;             // ceil(nB / K) * C
     unsigned *fetch;       // [1] next item to hand out (multi-wave order); reset by the launch's last fetch
     unsigned *count;       // [C][G][nB] writes done into j-slot (ch, g, J) in this launch; 0 between launches
     int *flag;             // status word: kFlagSymWait when a wait ran out
@@ -111,24 +114,60 @@ __device__ __forceinline__ unsigned next_item(const SymSched &sc, int n)
     return v;
 }
 
+// Distances [lo, hi) of the off-diagonal blocks of row chunk ch.
+__host__ __device__ __forceinline__ void chunk_range(const SymSched &sc, int ch, int &lo, int &hi)
+{
+    lo = ch * sc.Bc > 1 ? ch * sc.Bc : 1;
+    hi = ch * sc.Bc + sc.Bc < sc.D + 1 ? ch * sc.Bc + sc.Bc : sc.D + 1;
+}
+
+// Whether row J - b (mod nB) adds into j-slot (ch, g, J) at distance b (a
+// distance of chunk ch), i.e. evaluates that block and is in chain g; *before:
+// whether it comes before row I (which evaluates J at distance bI) in the
+// accumulation order.
+__host__ __device__ __forceinline__ bool j_writer(const SymSched &sc, int J, int g, int b, int I, int bI,
+                                                  bool *before)
+{
+    int r = J - b;
+    if (r < 0) r += sc.nB;
+    if ((sc.nB & 1) == 0 && b == sc.D && r >= sc.nB / 2) return false;   // rows >= nB/2 skip distance nB/2
+    if (r % sc.G != g) return false;
+    *before = sc.cyclic ? (b > bI) : (r < I);
+    return true;
+}
+
 // The rows that add into j-slot (ch, g, J): I' = J - b (mod nB) for the
 // distances b >= 1 of chunk ch that row I' evaluates, with I' = g (mod G).
 // Returns how many there are and, in *rank, how many of them come before row I
-// (which evaluates J at distance bI).
+// (which evaluates J at distance bI).  One thread.
 __host__ __device__ __forceinline__ int j_writers(const SymSched &sc, int J, int ch, int g, int I, int bI,
                                                   int *rank)
 {
-    const bool even = (sc.nB & 1) == 0;
-    const int lo = ch * sc.Bc > 1 ? ch * sc.Bc : 1;
-    const int hi = ch * sc.Bc + sc.Bc < sc.D + 1 ? ch * sc.Bc + sc.Bc : sc.D + 1;
-    int nw = 0, rk = 0;
+    int lo, hi, nw = 0, rk = 0;
+    chunk_range(sc, ch, lo, hi);
     for (int b = lo; b < hi; ++b) {
-        int r = J - b;
-        if (r < 0) r += sc.nB;
-        if (even && b == sc.D && r >= sc.nB / 2) continue;   // rows >= nB/2 skip distance nB/2
-        if (r % sc.G != g) continue;
-        ++nw;
-        rk += sc.cyclic ? (b > bI) : (r < I);
+        bool before = false;
+        if (j_writer(sc, J, g, b, I, bI, &before)) {
+            ++nw;
+            rk += before;
+        }
+    }
+    *rank = rk;
+    return nw;
+}
+
+// The same count by the 32 lanes of one warp (each lane takes every 32nd
+// distance); every lane gets the result.
+__device__ __forceinline__ int j_writers_warp(const SymSched &sc, int J, int ch, int g, int I, int bI, int *rank)
+{
+    int lo, hi, nw = 0, rk = 0;
+    chunk_range(sc, ch, lo, hi);
+    const int lane = threadIdx.x & 31;
+    for (int b0 = lo; b0 < hi; b0 += 32) {
+        bool before = false;
+        const bool wr = b0 + lane < hi && j_writer(sc, J, g, b0 + lane, I, bI, &before);
+        nw += __popc(__ballot_sync(0xffffffffu, wr));
+        rk += __popc(__ballot_sync(0xffffffffu, wr && before));
     }
     *rank = rk;
     return nw;
@@ -151,18 +190,18 @@ __device__ __noinline__ void wait_turn(const unsigned *c, unsigned want, const S
 
 // Shared-memory words of one CTA for the ordered flush.
 struct FlushSmem {
-    int item, rank, next;
+    int item, rank, next, ready;
     unsigned zero;        // bit g: j-slot (ch, g) of the item's own block has no writer
 };
 
-// Thread 0 at the start of item (I, ch): which of block I's j-slots of chunk ch
+// Warp 0 at the start of item (I, ch): which of block I's j-slots of chunk ch
 // no row adds into (they must hold zeros).
 __device__ __forceinline__ unsigned unwritten_chains(const SymSched &sc, int I, int ch)
 {
     unsigned z = 0;
     for (int g = 0; g < sc.G; ++g) {
         int rk;
-        if (j_writers(sc, I, ch, g, I, 0, &rk) == 0) z |= 1u << g;
+        if (j_writers_warp(sc, I, ch, g, I, 0, &rk) == 0) z |= 1u << g;
     }
     return z;
 }
@@ -173,17 +212,29 @@ __host__ __device__ __forceinline__ int64_t j_slot(const SymSched &sc, int ch, i
     return (int64_t)sc.C + (int64_t)ch * sc.G + g;
 }
 
-// Thread 0 before row I's ordered flush into j-slot (ch, I mod G, J): wait for
-// its turn and publish the rank (0: this row writes first) to the CTA.
-__device__ __forceinline__ void flush_begin(const SymSched &sc, FlushSmem &fs, int I, int J, int ch, int b)
+// Warp 0 before row I's ordered flush into j-slot (ch, I mod G, J): publish the
+// rank (0: this row writes first) and whether the turn has come (one look).
+__device__ __forceinline__ void flush_rank(const SymSched &sc, FlushSmem &fs, int I, int J, int ch, int b)
 {
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         const int g = I % sc.G;
         int rank = 0;
-        const int nw = j_writers(sc, J, ch, g, I, b, &rank);
-        fs.rank = rank;
-        fs.next = rank + 1 == nw ? 0 : rank + 1;
-        if (rank > 0) wait_turn(&sc.count[(j_slot(sc, ch, g) - sc.C) * sc.nB + J], (unsigned)rank + sc.bias, sc);
+        const int nw = j_writers_warp(sc, J, ch, g, I, b, &rank);
+        if (threadIdx.x == 0) {
+            fs.rank = rank;
+            fs.next = rank + 1 == nw ? 0 : rank + 1;
+            fs.ready = rank == 0 ||
+                       ld_acquire(&sc.count[(j_slot(sc, ch, g) - sc.C) * sc.nB + J]) == (unsigned)rank + sc.bias;
+        }
+    }
+}
+
+// Thread 0: wait (bounded) for the turn flush_rank published, unless it had come.
+__device__ __forceinline__ void flush_wait(const SymSched &sc, FlushSmem &fs, int I, int J, int ch)
+{
+    if (threadIdx.x == 0 && !fs.ready) {
+        wait_turn(&sc.count[(j_slot(sc, ch, I % sc.G) - sc.C) * sc.nB + J], (unsigned)fs.rank + sc.bias, sc);
+        fs.ready = 1;
     }
 }
 
@@ -263,7 +314,10 @@ __global__ void __launch_bounds__(kSymR, P <= 3 ? 3 : 2) k_pair_fp64_sym(SymArgs
         if (item >= sc.items) break;
         const int I = item / sc.C;
         const int ch = item % sc.C;
-        if (threadIdx.x == 0) fs.zero = unwritten_chains(sc, I, ch);
+        if (threadIdx.x < 32) {
+            const unsigned z = unwritten_chains(sc, I, ch);
+            if (threadIdx.x == 0) fs.zero = z;
+        }
         const int64_t ib = (int64_t)I * kSymR + threadIdx.x;
         double ri[P + 1][3], gmi;
         load_body<P>(a, ib, ri, gmi);
@@ -356,8 +410,9 @@ __global__ void __launch_bounds__(kSymR, P <= 3 ? 3 : 2) k_pair_fp64_sym(SymArgs
                     for (int c = 0; c < 3; ++c) accs[3 * k + c][js * 32 + lane] = accj[k][c];
                 __syncthreads();
             }
-            // ordered flush of block J's j-side sums into j-slot (ch, J)
-            flush_begin(sc, fs, I, J, ch, b);
+            // ordered flush of block J's j-side sums into j-slot (ch, I mod G, J)
+            flush_rank(sc, fs, I, J, ch, b);
+            flush_wait(sc, fs, I, J, ch);
             __syncthreads();
             const bool add = fs.rank > 0;
             double *out = a.part + j_slot(sc, ch, I % sc.G) * NR * a.ld + (int64_t)J * kSymR + threadIdx.x;
@@ -391,6 +446,7 @@ __global__ void __launch_bounds__(kSymR, P <= 3 ? 3 : 2) k_pair_fp64_sym(SymArgs
 struct SymLaunch {
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
+    SymLaunch(const SymLaunch &) = delete;
     SymLaunch(const SymPlan &pl, int threads, cudaStream_t st)
     {
         cfg.gridDim = dim3((unsigned)pl.grid);
@@ -406,7 +462,7 @@ struct SymLaunch {
 
 SymSched make_sched(const SymPlan &pl, const SymSync &sy)
 {
-    return SymSched{pl.nB, pl.D, pl.C, pl.Bc, pl.G, pl.cyclic ? 1 : 0, pl.nB * pl.C, sy.words, sy.words + 1,
+    return SymSched{pl.nB, pl.D, pl.C, pl.Bc, pl.G, pl.K, pl.cyclic ? 1 : 0, pl.items, sy.words, sy.words + 1,
                     sy.flag, sy.wait_ns, sy.bias};
 }
 
@@ -459,14 +515,13 @@ __device__ __forceinline__ void load_body32(const SymArgs32<P> &a, int64_t b, fl
     }
 }
 
-// Two warps per CTA, two i-bodies per lane: lane l of warp w holds the bodies
-// of i-subtiles 2w and 2w + 1 in the two lanes of Blackwell's paired FP32
-// instructions (FFMA2/FMUL2/FADD2), so every j-record passed around the ring
-// serves two pairs and one issue slot advances both.  The i-side sums are
-// packed too; the j-side sum of a ring lane adds both pairs' terms in FP32.
-// FP32 sums cover one 128-body block (as the tiles of the ordered kernels) and
-// are added to FP64 once per block.
-constexpr int kSym32Warps = 2;
+// Two warps per row of blocks: lane l of warp w holds the bodies of i-subtiles
+// 2w and 2w + 1 in the two lanes of Blackwell's paired FP32 instructions
+// (FFMA2/FMUL2/FADD2), so every j-record passed around the ring serves two
+// pairs and one issue slot advances both.  The i-side sums are packed too; the
+// j-side sum of a ring lane adds both pairs' terms in FP32.  FP32 sums cover
+// one 128-body block (as the tiles of the ordered kernels) and are added to
+// FP64 once per block.
 
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -518,58 +573,170 @@ __device__ __forceinline__ void pair_abg_terms_x2(const float2 (&r)[P + 1][3], f
     }
 }
 
+// cp.async of 16 bytes from global to shared memory, bypassing L1 (the data
+// were written by other CTAs).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Two warps per row of blocks, two i-bodies per lane; FP32 sums over one
+// block.  A CTA takes K consecutive rows (one item: rows qK .. qK + K - 1 of
+// one chunk), one pair of warps per row, and every row sweeps the chunk's
+// distances from the largest down.  The writer before row I in the single
+// accumulation chain is row I - 1 at the next larger distance: for all rows
+// but the CTA's first it is a row of the same CTA, which reaches that block one
+// block earlier.  The rows of a CTA meet only at the item boundaries (a row's
+// two warps use a named barrier of their own), so a row that runs ahead waits
+// on the turn counter as a row of another CTA would.  One CTA per SM: CTAs
+// that share an SM progress at very different speeds and their rows drift
+// apart by many blocks; within one CTA the drift stays small (measured at
+// 65537 bodies: 5 % of the flushes wait, for under 1 % of the time).
+//
+// The flush of a block's j-side sums is deferred by one block: right after the
+// block each row looks whether its turn has come and, if so, starts
+// asynchronous copies of the j-slot into shared memory; after the next block
+// the turn is waited for if it had not come, the copies have landed, the sums
+// are added and stored, and the turn is passed on.  The slot's latency is thus
+// hidden behind a block of pair arithmetic.  The i-side FP64 sums of the item
+// live in shared memory.  Shared memory per CTA: K (2 + 2 + 2) NR 128 words
+// (dynamic, up to 216 KB at K = 6, P = 3).
+// Barrier of the 64 threads of row u of the item (barrier 0 is __syncthreads).
+__device__ __forceinline__ void row_sync(int u)
+{
+    asm volatile("bar.sync %0, 64;" ::"r"(u + 1) : "memory");
+}
+
 template <int P>
-__global__ void __launch_bounds__(32 * kSym32Warps, 4) k_pair_fp32_sym(SymArgs32<P> a)
+struct Smem32 {
+    static constexpr int NR = 3 * (P + 1);
+    static constexpr size_t accs = (size_t)2 * NR * kSymR * sizeof(float);     // per row: two blocks in flight
+    static constexpr size_t sbuf = (size_t)NR * kSymR * sizeof(double);        // per row: the j-slot being flushed
+    static constexpr size_t acc64 = (size_t)NR * kSymR * sizeof(double);       // per row: i-side FP64 sums
+    static constexpr size_t per_row = accs + sbuf + acc64;
+    static size_t bytes(int K) { return (size_t)K * per_row; }
+};
+
+template <int P, int K>
+__global__ void __launch_bounds__(64 * K, 1) k_pair_fp32_sym(SymArgs32<P> a)
 {
     constexpr int NF = Rec32s<P>::NF;
     constexpr int NR = 3 * (P + 1);
+    using SM = Smem32<P>;
     const SymSched &sc = a.sc;
-    __shared__ float accs[NR][kSymR];     // j-side FP32 sums of the current block, by column
-    __shared__ FlushSmem fs;
-    const int lane = threadIdx.x & 31;
-    const int w = threadIdx.x >> 5;
+    extern __shared__ __align__(16) unsigned char smem32[];
+    __shared__ FlushSmem fsu[K];
+    __shared__ int pend_J[K];
+    __shared__ int s_item;
+    const int u = threadIdx.x >> 6;                // this thread's row of the item
+    const int tu = threadIdx.x & 63;               // thread within the row's two warps
+    const int lane = tu & 31;
+    const int w = tu >> 5;
     const int src = (lane + 1) & 31;
+    const int fc = 2 * tu;                         // the two j-slot columns this thread flushes
+    float(*accs)[NR][kSymR] = reinterpret_cast<float(*)[NR][kSymR]>(smem32 + u * SM::per_row);
+    double(*sbuf)[kSymR] = reinterpret_cast<double(*)[kSymR]>(smem32 + u * SM::per_row + SM::accs);
+    double(*acc64s)[kSymR] = reinterpret_cast<double(*)[kSymR]>(smem32 + u * SM::per_row + SM::accs + SM::sbuf);
+    FlushSmem &fs = fsu[u];
     const bool even = (sc.nB & 1) == 0;
     const float2 eps2 = f2(a.eps2);
     for (int n = 0;; ++n) {
-        if (threadIdx.x == 0) fs.item = (int)min(next_item(sc, n), (unsigned)sc.items);
+        if (threadIdx.x == 0) s_item = (int)min(next_item(sc, n), (unsigned)sc.items);
         __syncthreads();
-        const int item = fs.item;
+        const int item = s_item;
         if (item >= sc.items) break;
-        const int I = item / sc.C;
+        const int I = (item / sc.C) * K + u;
         const int ch = item % sc.C;
-        if (threadIdx.x == 0) fs.zero = unwritten_chains(sc, I, ch);
+        const bool live = I < sc.nB;
+        if (tu < 32) {
+            const unsigned z = live ? unwritten_chains(sc, I, ch) : 0u;
+            if (tu == 0) fs.zero = z;
+        }
         // the lane's two i-bodies, negated (differences become additions), packed
         float2 ni[NF - 1], gmi;
         {
             float r0[NF], r1[NF];
-            load_body32<P>(a, (int64_t)I * kSymR + (2 * w) * 32 + lane, r0);
-            load_body32<P>(a, (int64_t)I * kSymR + (2 * w + 1) * 32 + lane, r1);
+            const int64_t base = (int64_t)(live ? I : 0) * kSymR;
+            load_body32<P>(a, base + (2 * w) * 32 + lane, r0);
+            load_body32<P>(a, base + (2 * w + 1) * 32 + lane, r1);
 #pragma unroll
             for (int q = 0; q < NF - 1; ++q) ni[q] = make_float2(-r0[q], -r1[q]);
             gmi = make_float2(r0[NF - 1], r1[NF - 1]);
         }
-        double acc64[2][NR];
 #pragma unroll
         for (int k = 0; k < 2; ++k)
 #pragma unroll
-            for (int q = 0; q < NR; ++q) acc64[k][q] = 0.0;
+            for (int q = 0; q < NR; ++q) acc64s[q][(2 * w + k) * 32 + lane] = 0.0;
         __syncthreads();
-        for (int g = 0; g < sc.G; ++g)
-            if (fs.zero >> g & 1u) {
+        if (live && (fs.zero & 1u)) {
+            // no row adds into this block's j-slot of chunk ch: it holds zeros
 #pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    double *out = a.part + j_slot(sc, ch, g) * NR * a.ld + (int64_t)I * kSymR + threadIdx.x + k * 64;
+            for (int k = 0; k < 2; ++k) {
+                double *out = a.part + j_slot(sc, ch, 0) * NR * a.ld + (int64_t)I * kSymR + tu + k * 64;
 #pragma unroll
-                    for (int q = 0; q < NR; ++q) out[q * a.ld] = 0.0;
+                for (int q = 0; q < NR; ++q) out[q * a.ld] = 0.0;
+            }
+        }
+
+        bool pending = false, copied = false;
+        int kb = 0;                                // accs buffer of the row's current block
+        // copy this thread's two columns of the row's pending j-slot (the first
+        // writer has nothing to copy)
+        auto start_copy = [&]() {
+            if (fs.rank > 0) {
+                const double *src_slot = a.part + j_slot(sc, ch, 0) * NR * a.ld + (int64_t)pend_J[u] * kSymR + fc;
+#pragma unroll
+                for (int q = 0; q < NR; ++q) cp_async16(&sbuf[q][fc], src_slot + q * a.ld);
+            }
+            cp_async_commit();
+        };
+        // finish the rows' pending flushes (the whole CTA takes part): wait for the
+        // turn where it had not come, add the copied slot, store, pass the turn on
+        auto finish_flushes = [&]() {
+            if (pending && tu == 0 && !fs.ready) {
+                wait_turn(&sc.count[(j_slot(sc, ch, 0) - sc.C) * sc.nB + pend_J[u]], (unsigned)fs.rank + sc.bias, sc);
+                fs.ready = 1;
+            }
+            row_sync(u);
+            if (pending) {
+                if (!copied) start_copy();
+                cp_async_commit_wait_all();
+                const bool add = fs.rank > 0;
+                const int pb = kb ^ 1;
+                double *out = a.part + j_slot(sc, ch, 0) * NR * a.ld + (int64_t)pend_J[u] * kSymR + fc;
+#pragma unroll
+                for (int q = 0; q < NR; ++q) {
+                    double2 v = make_double2((double)accs[pb][q][fc], (double)accs[pb][q][fc + 1]);
+                    if (add) {
+                        v.x += sbuf[q][fc];
+                        v.y += sbuf[q][fc + 1];
+                    }
+                    __stcg(reinterpret_cast<double2 *>(out + q * a.ld), v);
                 }
             }
+            row_sync(u);
+            if (pending && tu == 0)
+                st_release(&sc.count[(j_slot(sc, ch, 0) - sc.C) * sc.nB + pend_J[u]], (unsigned)fs.next);
+            pending = false;
+        };
 
-        const int dmax = (even && I >= sc.nB / 2) ? sc.D - 1 : sc.D;
         const int b0 = ch * sc.Bc;
-        const int b1 = min(b0 + sc.Bc, dmax + 1);
+        const int b1 = min(b0 + sc.Bc, sc.D + 1);
+        const int dmax = (even && I >= sc.nB / 2) ? sc.D - 1 : sc.D;
         for (int b = b1 - 1; b >= b0; --b) {
-            const bool diag = b == 0;
+            const bool diag = b == 0;                // the same for every row of the CTA
+            const bool active = live && b <= dmax;   // rows >= nB/2 skip distance nB/2
             const int J = (I + b) % sc.nB;
             float2 acci[P + 1][3];
 #pragma unroll
@@ -580,91 +747,107 @@ __global__ void __launch_bounds__(32 * kSym32Warps, 4) k_pair_fp32_sym(SymArgs32
                 // off-diagonal: at stage jt warp w takes j-subtile (2w + jt) mod 4 (the two
                 // warps never share one); diagonal block: every warp takes every subtile
                 const int js = diag ? jt : (2 * w + jt) & 3;
-                float rj[NF];
-                load_body32<P>(a, (int64_t)J * kSymR + js * 32 + lane, rj);
-                float accj[P + 1][3];
+                if (active) {
+                    float rj[NF];
+                    load_body32<P>(a, (int64_t)J * kSymR + js * 32 + lane, rj);
+                    float accj[P + 1][3];
 #pragma unroll
-                for (int n2 = 0; n2 <= P; ++n2)
+                    for (int n2 = 0; n2 <= P; ++n2)
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) accj[n2][c] = 0.0f;
-                for (int t = 0; t < 32; ++t) {
-                    float2 r[P + 1][3];
+                        for (int c = 0; c < 3; ++c) accj[n2][c] = 0.0f;
+#pragma unroll 2
+                    for (int t = 0; t < 32; ++t) {
+                        float2 r[P + 1][3];
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        r[0][c] = add2(add2(f2(rj[c]), ni[c]), add2(f2(rj[3 + c]), ni[3 + c]));
-                        r[1][c] = add2(add2(f2(rj[6 + c]), ni[6 + c]), add2(f2(rj[9 + c]), ni[9 + c]));
-                        if constexpr (P >= 2) r[2][c] = add2(f2(rj[12 + c]), ni[12 + c]);
-                        if constexpr (P >= 3) r[3][c] = add2(f2(rj[15 + c]), ni[15 + c]);
+                        for (int c = 0; c < 3; ++c) {
+                            r[0][c] = add2(add2(f2(rj[c]), ni[c]), add2(f2(rj[3 + c]), ni[3 + c]));
+                            r[1][c] = add2(add2(f2(rj[6 + c]), ni[6 + c]), add2(f2(rj[9 + c]), ni[9 + c]));
+                            if constexpr (P >= 2) r[2][c] = add2(f2(rj[12 + c]), ni[12 + c]);
+                            if constexpr (P >= 3) r[3][c] = add2(f2(rj[15 + c]), ni[15 + c]);
+                        }
+                        float2 s = fma2(r[0][0], r[0][0], fma2(r[0][1], r[0][1], fma2(r[0][2], r[0][2], eps2)));
+                        const bool self0 = diag && js == 2 * w && t == 0;
+                        const bool self1 = diag && js == 2 * w + 1 && t == 0;
+                        s.x = self0 ? 1.0f : s.x;
+                        s.y = self1 ? 1.0f : s.y;
+                        const float2 rinv = make_float2(rsqrt_mufu(s.x), rsqrt_mufu(s.y));
+                        const float2 sinv = mul2(rinv, rinv);
+                        const float2 S = mul2(rinv, sinv);
+                        float2 wi = mul2(f2(rj[NF - 1]), S);
+                        wi.x = self0 ? 0.0f : wi.x;
+                        wi.y = self1 ? 0.0f : wi.y;
+                        const float2 wj = diag ? f2(0.0f) : mul2(gmi, S);
+                        pair_abg_terms_x2<P>(r, sinv, [&](int n3, int c, float2 B) {
+                            acci[n3][c] = fma2(wi, B, acci[n3][c]);
+                            accj[n3][c] = fmaf(-wj.y, B.y, fmaf(-wj.x, B.x, accj[n3][c]));
+                        });
+#pragma unroll
+                        for (int q = 0; q < NF; ++q) rj[q] = __shfl_sync(0xffffffffu, rj[q], src);
+                        if (!diag) {
+#pragma unroll
+                            for (int n3 = 0; n3 <= P; ++n3)
+#pragma unroll
+                                for (int c = 0; c < 3; ++c)
+                                    accj[n3][c] = __shfl_sync(0xffffffffu, accj[n3][c], src);
+                        }
                     }
-                    float2 s = fma2(r[0][0], r[0][0], fma2(r[0][1], r[0][1], fma2(r[0][2], r[0][2], eps2)));
-                    const bool self0 = diag && js == 2 * w && t == 0;
-                    const bool self1 = diag && js == 2 * w + 1 && t == 0;
-                    s.x = self0 ? 1.0f : s.x;
-                    s.y = self1 ? 1.0f : s.y;
-                    const float2 rinv = make_float2(rsqrt_mufu(s.x), rsqrt_mufu(s.y));
-                    const float2 sinv = mul2(rinv, rinv);
-                    const float2 S = mul2(rinv, sinv);
-                    float2 wi = mul2(f2(rj[NF - 1]), S);
-                    wi.x = self0 ? 0.0f : wi.x;
-                    wi.y = self1 ? 0.0f : wi.y;
-                    const float2 wj = diag ? f2(0.0f) : mul2(gmi, S);
-                    pair_abg_terms_x2<P>(r, sinv, [&](int n3, int c, float2 B) {
-                        acci[n3][c] = fma2(wi, B, acci[n3][c]);
-                        accj[n3][c] = fmaf(-wj.y, B.y, fmaf(-wj.x, B.x, accj[n3][c]));
-                    });
-#pragma unroll
-                    for (int q = 0; q < NF; ++q) rj[q] = __shfl_sync(0xffffffffu, rj[q], src);
                     if (!diag) {
+                        // each column is visited twice, by warp 0 and by warp 1: first at
+                        // stage 0 (columns 0, 2) or 1 (columns 1, 3), second at stage 2 or 3
 #pragma unroll
                         for (int n3 = 0; n3 <= P; ++n3)
 #pragma unroll
-                            for (int c = 0; c < 3; ++c) accj[n3][c] = __shfl_sync(0xffffffffu, accj[n3][c], src);
+                            for (int c = 0; c < 3; ++c) {
+                                float &cell = accs[kb][3 * n3 + c][js * 32 + lane];
+                                cell = (jt < 2 ? 0.0f : cell) + accj[n3][c];
+                            }
                     }
                 }
-                if (!diag) {
-                    // each column is visited twice, by warp 0 and by warp 1: first at stage
-                    // 0 (columns 0, 2) or 1 (columns 1, 3), second at stage 2 or 3
-#pragma unroll
-                    for (int n3 = 0; n3 <= P; ++n3)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            float &cell = accs[3 * n3 + c][js * 32 + lane];
-                            cell = (jt < 2 ? 0.0f : cell) + accj[n3][c];
-                        }
-                    __syncthreads();
-                }
+                if (!diag) row_sync(u);
             }
+            if (active) {
 #pragma unroll
-            for (int n2 = 0; n2 <= P; ++n2)
+                for (int n2 = 0; n2 <= P; ++n2)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    acc64[0][3 * n2 + c] += (double)acci[n2][c].x;
-                    acc64[1][3 * n2 + c] += (double)acci[n2][c].y;
-                }
+                    for (int c = 0; c < 3; ++c) {
+                        acc64s[3 * n2 + c][(2 * w) * 32 + lane] += (double)acci[n2][c].x;
+                        acc64s[3 * n2 + c][(2 * w + 1) * 32 + lane] += (double)acci[n2][c].y;
+                    }
+            }
+            finish_flushes();
             if (!diag) {
-                // ordered flush of block J's j-side sums into j-slot (ch, J)
-                flush_begin(sc, fs, I, J, ch, b);
-                __syncthreads();
-                const bool add = fs.rank > 0;
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const int col = threadIdx.x + k * 64;
-                    double *out = a.part + j_slot(sc, ch, I % sc.G) * NR * a.ld + (int64_t)J * kSymR + col;
-#pragma unroll
-                    for (int q = 0; q < NR; ++q) {
-                        const double v = (double)accs[q][col];
-                        __stcg(out + q * a.ld, add ? __ldcg(out + q * a.ld) + v : v);
+                // take the turn for block J's j-side sums if it has come (within the
+                // CTA it has: the row before swept this block one step ago); else
+                // after the next block
+                if (active && tu < 32) {
+                    int rank = 0;
+                    const int nw = j_writers_warp(sc, J, ch, 0, I, b, &rank);
+                    if (tu == 0) {
+                        fs.rank = rank;
+                        fs.next = rank + 1 == nw ? 0 : rank + 1;
+                        fs.ready = rank == 0 || ld_acquire(&sc.count[(j_slot(sc, ch, 0) - sc.C) * sc.nB + J]) ==
+                                                    (unsigned)rank + sc.bias;
+                        pend_J[u] = J;
                     }
                 }
-                __syncthreads();
-                flush_end(sc, fs, I, J, ch);
+                row_sync(u);
+                if (active) {
+                    copied = fs.ready;
+                    if (copied) start_copy();
+                    pending = true;
+                    kb ^= 1;
+                }
             }
         }
+        finish_flushes();
+        if (live) {
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            double *out = a.part + (int64_t)ch * NR * a.ld + (int64_t)I * kSymR + (2 * w + k) * 32 + lane;
+            for (int k = 0; k < 2; ++k) {
+                const int col = (2 * w + k) * 32 + lane;
+                double *out = a.part + (int64_t)ch * NR * a.ld + (int64_t)I * kSymR + col;
 #pragma unroll
-            for (int q = 0; q < NR; ++q) out[q * a.ld] = acc64[k][q];
+                for (int q = 0; q < NR; ++q) out[q * a.ld] = acc64s[q][col];
+            }
         }
     }
 }
@@ -674,8 +857,12 @@ int launch_sym32(const SymPlan &pl, const SymSync &sy, const float *jrec32, int6
                  double *part, cudaStream_t st)
 {
     SymArgs32<P> a{jrec32, ld, N, make_sched(pl, sy), (float)(eps * eps), part};
-    const SymLaunch l(pl, 32 * kSym32Warps, st);
-    MH_CUDA(cudaLaunchKernelEx(&l.cfg, k_pair_fp32_sym<P>, a));
+    SymLaunch l(pl, 64 * pl.K, st);
+    l.cfg.dynamicSmemBytes = Smem32<P>::bytes(pl.K);
+    if (pl.K == 6)
+        MH_CUDA(cudaLaunchKernelEx(&l.cfg, k_pair_fp32_sym<P, 6>, a));
+    else
+        MH_CUDA(cudaLaunchKernelEx(&l.cfg, k_pair_fp32_sym<P, 4>, a));
     return MH_OK;
 }
 
@@ -686,8 +873,10 @@ int launch_sym32(const SymPlan &pl, const SymSync &sy, const float *jrec32, int6
 // at once (distance order); otherwise the CTAs take items in row order, and rows
 // at the end of a launch that is only just above one wave wait for the first
 // rows (their blocks near the wrap-around come last in that order): count one
-// wave more.
-SymPlan plan_sym_slots(int64_t ld, int slots)
+// wave more.  FP64: one row per item (4 warps), 4 chains.  FP32-pair: K rows per
+// item (K = kmax or 4, whichever wastes less of the last wave; a CTA sweeps K
+// blocks per step), one chain.
+SymPlan plan_sym_slots(int64_t ld, int slots, bool fp32, int kmax)
 {
     SymPlan pl{};
     if (ld % kSymR != 0 || ld < kSymR || slots < 1) return pl;
@@ -695,24 +884,30 @@ SymPlan plan_sym_slots(int64_t ld, int slots)
     pl.D = pl.nB / 2;
     const int nb = pl.D + 1;                        // blocks of the longest row
     double best = 1e300;
-    for (int C = 1; C <= nb; ++C) {
-        const int Bc = (nb + C - 1) / C;
-        if ((nb + Bc - 1) / Bc != C) continue;
-        const int64_t items = (int64_t)pl.nB * C;
-        const bool cyclic = items <= slots;
-        int64_t waves = cyclic ? 1 : (items + slots - 1) / slots;
-        if (!cyclic && items < slots + nb) waves += 1;
-        const double cost = (double)waves * (Bc + 1.0) * (1.0 + 0.001 * C);
-        if (cost < best) {
-            best = cost;
-            pl.C = C;
-            pl.Bc = Bc;
-            pl.cyclic = cyclic;
+    const int Ks[2] = {fp32 ? kmax : 1, 4};
+    for (int ki = 0; ki < (fp32 && kmax != 4 ? 2 : 1); ++ki) {
+        const int K = Ks[ki];
+        const int64_t groups = (pl.nB + K - 1) / K;
+        for (int C = 1; C <= nb; ++C) {
+            const int Bc = (nb + C - 1) / C;
+            if ((nb + Bc - 1) / Bc != C) continue;
+            const int64_t items = groups * C;
+            const bool cyclic = items <= slots;
+            int64_t waves = cyclic ? 1 : (items + slots - 1) / slots;
+            if (!cyclic && items < slots + nb) waves += 1;
+            const double cost = (double)waves * (Bc + 1.0) * K * (1.0 + 0.005 * C);
+            if (cost < best) {
+                best = cost;
+                pl.C = C;
+                pl.Bc = Bc;
+                pl.K = K;
+                pl.cyclic = cyclic;
+                pl.items = (int)items;
+            }
         }
     }
-    const int64_t items = (int64_t)pl.nB * pl.C;
-    pl.grid = (int)(pl.cyclic ? items : std::min<int64_t>(items, slots));
-    pl.G = std::min(kSymChains, std::max(pl.Bc - 1, 1));
+    pl.grid = (int)(pl.cyclic ? pl.items : std::min(pl.items, slots));
+    pl.G = fp32 ? 1 : std::min(kSymChains64, std::max(pl.Bc - 1, 1));
     pl.slots = pl.C * (1 + pl.G);
     pl.sync_words = 1 + pl.C * pl.G * pl.nB;
     return pl;
@@ -721,28 +916,46 @@ SymPlan plan_sym_slots(int64_t ld, int slots)
 SymPlan plan_sym(int P, int64_t ld, int device, bool fp32)
 {
     if (ld % kSymR != 0 || ld < kSymR || P < 1 || P > (fp32 ? 3 : 5)) return SymPlan{};
-    // resident CTAs per device, cached per (device, P, form)
+    // resident CTAs per device (FP32-pair: SMs, one CTA of K rows each, and the
+    // largest K whose shared memory fits), cached per (device, P, form)
     static int slot_cache[64][16] = {{0}};
+    static int kmax_cache[64][16] = {{0}};
     const int ci = P + (fp32 ? 8 : 0);
-    int slots = device >= 0 && device < 64 ? slot_cache[device][ci] : 0;
+    const bool cached = device >= 0 && device < 64;
+    int slots = cached ? slot_cache[device][ci] : 0;
+    int kmax = cached ? kmax_cache[device][ci] : 0;
     if (slots == 0) {
         int n_sm = 0, occ = 0;
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
         if (fp32) {
-            const void *fn = P == 1 ? (const void *)k_pair_fp32_sym<1>
-                           : P == 2 ? (const void *)k_pair_fp32_sym<2> : (const void *)k_pair_fp32_sym<3>;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * kSym32Warps, 0);
+            kmax = 4;
+            const void *fn6 = P == 1 ? (const void *)k_pair_fp32_sym<1, 6>
+                            : P == 2 ? (const void *)k_pair_fp32_sym<2, 6> : (const void *)k_pair_fp32_sym<3, 6>;
+            const void *fn4 = P == 1 ? (const void *)k_pair_fp32_sym<1, 4>
+                            : P == 2 ? (const void *)k_pair_fp32_sym<2, 4> : (const void *)k_pair_fp32_sym<3, 4>;
+            const size_t b6 = P == 1 ? Smem32<1>::bytes(6) : P == 2 ? Smem32<2>::bytes(6) : Smem32<3>::bytes(6);
+            const size_t b4 = P == 1 ? Smem32<1>::bytes(4) : P == 2 ? Smem32<2>::bytes(4) : Smem32<3>::bytes(4);
+            cudaFuncSetAttribute(fn4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b4);
+            if (cudaFuncSetAttribute(fn6, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b6) == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn6, 64 * 6, b6) == cudaSuccess && occ >= 1)
+                kmax = 6;
+            cudaGetLastError();
+            occ = 1;
         } else {
             const void *fn = P == 1 ? (const void *)k_pair_fp64_sym<1, false>
                            : P == 2 ? (const void *)k_pair_fp64_sym<2, false>
                            : P == 3 ? (const void *)k_pair_fp64_sym<3, false>
                            : P == 4 ? (const void *)k_pair_fp64_sym<4, false> : (const void *)k_pair_fp64_sym<5, false>;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kSymR, 0);
+            kmax = 1;
         }
         slots = std::max(n_sm, 1) * std::max(occ, 1);
-        if (device >= 0 && device < 64) slot_cache[device][ci] = slots;
+        if (cached) {
+            slot_cache[device][ci] = slots;
+            kmax_cache[device][ci] = kmax;
+        }
     }
-    return plan_sym_slots(ld, slots);
+    return plan_sym_slots(ld, slots, fp32, kmax);
 }
 
 int launch_pair_sym32(int P, const SymPlan &pl, const SymSync &sy, const float *jrec32, int64_t ld, int64_t N,
@@ -777,32 +990,36 @@ int launch_pair_sym(int P, const SymPlan &pl, const SymSync &sy, const double *j
 // cannot be waiting on it in turn: in the row order one handed out earlier, in
 // the distance order one at a larger distance (so the waits of a launch whose
 // CTAs are all resident form no cycle).
-int sym_schedule_check(int64_t ld, int slots, int *info)
+int sym_schedule_check(int64_t ld, int slots, bool fp32, int *info)
 {
-    const SymPlan pl = plan_sym_slots(ld, slots);
+    const SymPlan pl = plan_sym_slots(ld, slots, fp32, fp32 ? 6 : 1);
     if (pl.nB == 0) return MH_EINVAL;
-    SymSched sc{pl.nB, pl.D, pl.C, pl.Bc, pl.G, pl.cyclic ? 1 : 0, pl.nB * pl.C, nullptr, nullptr, nullptr, 0, 0};
+    SymSched sc{pl.nB, pl.D, pl.C, pl.Bc, pl.G, pl.K, pl.cyclic ? 1 : 0, pl.items, nullptr, nullptr, nullptr, 0, 0};
     const bool even = (pl.nB & 1) == 0;
     const int64_t nslot = (int64_t)pl.C * pl.G * pl.nB;
     std::vector<int> seen(nslot, 0), nwv(nslot, -1);
     std::vector<std::vector<std::pair<int, int>>> by_rank(nslot);   // rank -> (item, distance)
     for (int item = 0; item < sc.items; ++item) {
-        const int I = item / sc.C, ch = item % sc.C;
-        const int dmax = (even && I >= sc.nB / 2) ? sc.D - 1 : sc.D;
-        const int b0 = ch * sc.Bc, b1 = std::min(b0 + sc.Bc, dmax + 1);
-        for (int b = b1 - 1; b >= b0 && b >= 1; --b) {
-            const int J = (I + b) % sc.nB;
-            const int g = I % sc.G;
-            int rank = 0;
-            const int nw = j_writers(sc, J, ch, g, I, b, &rank);
-            const int64_t q = (j_slot(sc, ch, g) - sc.C) * sc.nB + J;
-            if (nwv[q] < 0) {
-                nwv[q] = nw;
-                by_rank[q].assign(nw, {-1, -1});
+        const int ch = item % sc.C;
+        for (int u = 0; u < sc.K; ++u) {
+            const int I = (item / sc.C) * sc.K + u;
+            if (I >= sc.nB) continue;
+            const int dmax = (even && I >= sc.nB / 2) ? sc.D - 1 : sc.D;
+            const int b0 = ch * sc.Bc, b1 = std::min(b0 + sc.Bc, dmax + 1);
+            for (int b = b1 - 1; b >= b0 && b >= 1; --b) {
+                const int J = (I + b) % sc.nB;
+                const int g = I % sc.G;
+                int rank = 0;
+                const int nw = j_writers(sc, J, ch, g, I, b, &rank);
+                const int64_t q = (j_slot(sc, ch, g) - sc.C) * sc.nB + J;
+                if (nwv[q] < 0) {
+                    nwv[q] = nw;
+                    by_rank[q].assign(nw, {-1, -1});
+                }
+                if (nwv[q] != nw || rank < 0 || rank >= nw || by_rank[q][rank].first >= 0) return 1;
+                by_rank[q][rank] = {item, b};
+                seen[q] += 1;
             }
-            if (nwv[q] != nw || rank < 0 || rank >= nw || by_rank[q][rank].first >= 0) return 1;
-            by_rank[q][rank] = {item, b};
-            seen[q] += 1;
         }
     }
     for (int64_t q = 0; q < nslot; ++q) {
@@ -812,7 +1029,12 @@ int sym_schedule_check(int64_t ld, int slots, int *info)
         if (seen[q] != nw) return 2;
         for (int r = 1; r < nw; ++r) {
             const auto &cur = by_rank[q][r], &prev = by_rank[q][r - 1];
-            if (sc.cyclic ? !(prev.second > cur.second) : !(prev.first < cur.first)) return 3;
+            // distance order: the writer before sweeps a larger distance (all items
+            // resident); row order: it was handed out earlier, or it is an earlier
+            // row of the same item, which sweeps the larger distance first
+            const bool ok = sc.cyclic ? prev.second > cur.second
+                                      : prev.first < cur.first || (prev.first == cur.first && prev.second > cur.second);
+            if (!ok) return 3;
         }
     }
     if (info) {
@@ -822,6 +1044,7 @@ int sym_schedule_check(int64_t ld, int slots, int *info)
         info[3] = pl.cyclic ? 1 : 0;
         info[4] = pl.grid;
         info[5] = pl.G;
+        info[6] = pl.K;
     }
     return MH_OK;
 }

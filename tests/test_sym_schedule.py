@@ -15,29 +15,33 @@ import paper_2006_02501_gb300 as mh
 
 SMALL = [1, 2, 129, 256, 257, 511, 700, 1024, 1100, 2048, 3000, 4097, 8000, 8192, 16384, 16385]
 LARGE = [32768, 65537, 100000, 131072, 262144]
-CASES = [(N, s) for N in SMALL for s in (3, 17, 152 * 2, 152 * 3, 152 * 4)] + \
-        [(N, s) for N in LARGE for s in (152 * 3, 152 * 4)]
+CASES = [(N, s) for N in SMALL for s in (3, 17, 152, 152 * 2, 152 * 3)] + \
+        [(N, s) for N in LARGE for s in (152, 152 * 3)]
 
 
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("N,slots", CASES)
-def test_ordered_accumulation_schedule(N, slots):
-    plan = mh.sym_schedule_check(N, slots)
+def test_ordered_accumulation_schedule(N, slots, precision):
+    plan = mh.sym_schedule_check(N, slots, precision)
     nB = (N + 255) // 256 * 2
     assert plan["blocks"] == nB
-    assert plan["grid"] <= max(slots, nB * plan["chunks"] if plan["cyclic"] else slots)
+    items = -(-nB // plan["rows_per_item"]) * plan["chunks"]
     if plan["cyclic"]:
         # one item per CTA only when every item is resident at once
-        assert nB * plan["chunks"] <= slots
+        assert plan["grid"] == items <= slots
+    else:
+        assert plan["grid"] == slots < items
 
 
 def test_slot_memory_is_linear():
     """The partial sums take C (1 + G) slots, C row chunks and G chains: O(N C),
     not O(N^2) (the earlier design kept one slot per block distance, Np/256)."""
     for N in (65537, 262144):
-        for slots in (152 * 3, 152 * 4):
-            plan = mh.sym_schedule_check(N, slots)
-            assert 1 <= plan["chains"] <= 4
-            assert plan["chunks"] * (1 + plan["chains"]) <= 48
+        for slots, precision in ((152 * 3, 0), (152, 1)):
+            plan = mh.sym_schedule_check(N, slots, precision)
+            assert plan["chains"] == (1 if precision else min(4, plan["distances_per_chunk"] - 1))
+            assert plan["rows_per_item"] == (6 if precision else 1)
+            assert plan["chunks"] * (1 + plan["chains"]) <= 40
 
 
 def test_schedule_check_rejects_bad_arguments():
@@ -45,3 +49,5 @@ def test_schedule_check_rejects_bad_arguments():
         mh.sym_schedule_check(0, 10)
     with pytest.raises(mh.MHError):
         mh.sym_schedule_check(100, 0)
+    with pytest.raises(mh.MHError):
+        mh.sym_schedule_check(100, 10, 7)
