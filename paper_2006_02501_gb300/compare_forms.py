@@ -85,17 +85,20 @@ def run_ecc(args):
 
 
 def run_block(args):
-    """Block time steps on the SMBH disc at N = 262144: FP32-pair and FP64 forms
-    from the same start over args.dtmax_units x dt_max, 8th and 6th order."""
+    """Block time steps on the SMBH disc (N stars + SMBH, total star mass 0.01,
+    seed 3): FP32-pair and FP64 forms from the same start over
+    args.dtmax_units x dt_max (dt_max = 2^-5, levels k <= 12, eta = 0.05),
+    8th and 6th order."""
     torch, mh, I = _setup()
     st = torch.cuda.Stream()
     m, x, v = I.smbh_disc(seed=3, N=args.N)
     eps = 1e-4
     blk = dict(dt_max=2.0 ** -5, k_max=12, eta=0.05)
     span = args.dtmax_units * blk["dt_max"]
+    forms = [(p, n) for p, n in ((mh.MH_PREC_FP32PAIR, "fp32pair"), (mh.MH_PREC_FP64, "fp64")) if n in args.forms]
     for order in args.orders:
         out = {}
-        for prec, name in ((mh.MH_PREC_FP32PAIR, "fp32pair"), (mh.MH_PREC_FP64, "fp64")):
+        for prec, name in forms:
             with mh.Simulation(order, m, x, v, eps, stream=st, precision=prec, block=blk) as s:
                 lv = s.levels()
                 E0 = s.energy()
@@ -108,11 +111,14 @@ def run_block(args):
                          "pair_interactions_per_s": (c1["pair_interactions"] - c0["pair_interactions"]) / sec,
                          "block_steps": c1["steps"] - c0["steps"], "dE_rel": E1 / E0 - 1,
                          "levels": np.bincount(lv, minlength=blk["k_max"] + 1).tolist(), "e": e}
-        diff = abs(out["fp32pair"]["dE_rel"] - out["fp64"]["dE_rel"])
-        ecc_diff = _ecc_err(out["fp32pair"].pop("e"), out["fp64"].pop("e"))
-        print(json.dumps({"order": order, "N": len(m), "span": span, "fp32pair": out["fp32pair"],
-                          "fp64": out["fp64"], "dE_rel_difference": diff,
-                          "ecc_median_difference_fp32_vs_fp64": ecc_diff}), flush=True)
+        row = {"order": order, "N": len(m), "span": span}
+        if len(out) == 2:
+            row["dE_rel_difference"] = abs(out["fp32pair"]["dE_rel"] - out["fp64"]["dE_rel"])
+            row["ecc_median_difference_fp32_vs_fp64"] = _ecc_err(out["fp32pair"]["e"], out["fp64"]["e"])
+        for name in out:
+            out[name].pop("e")
+            row[name] = out[name]
+        print(json.dumps(row), flush=True)
 
 
 def run_batch(args):
@@ -207,6 +213,28 @@ def run_learned(args):
         res[name + "_fraction_converged"] = frac
     print(json.dumps({"N": len(m), "training_rows": int(F.shape[0]), "collect_s": collect_s, "train_s": train_s,
                       "tol": tol, **res}), flush=True)
+    # equal-error comparison: eccentricity-vector error after K steps from the
+    # same state (reference: dt/2, P(EC)^4) and particle-steps/s, plain P(EC)^n
+    # against learned P(EC)^n
+    K = args.ecc_steps
+    with mh.Simulation(8, m, x0, v0, eps, stream=st) as s:
+        s.set_state(x0, v0, d0, t=t)
+        s.step(dt / 2, 4, nsteps=2 * K)
+        _, e_ref = s.diagnostics(central=0)
+    rows = []
+    for name, use in (("plain", False), ("learned", True)):
+        for n in (1, 2, 3):
+            with mh.Simulation(8, m, x0, v0, eps, stream=st) as s:
+                s.set_state(x0, v0, d0, t=t)
+                if use:
+                    s.set_predictor(net)
+                s.step(dt, n)                       # warm-up (graphs, tuner)
+                s.set_state(x0, v0, d0, t=t)
+                sec = _timed(torch, st, lambda: s.step(dt, n, nsteps=K))
+                _, e = s.diagnostics(central=0)
+            rows.append({"predictor": name, "n": n, "ecc_error": _ecc_err(e, e_ref),
+                         "particle_steps_per_s": K * len(m) / sec, "ms_per_step": 1e3 * sec / K})
+    print(json.dumps({"N": len(m), "steps": K, "dt": dt, "ecc_vs_reference": rows}), flush=True)
 
 
 def run_table1(args):
@@ -255,6 +283,7 @@ def main():
     b.add_argument("--N", type=int, default=262144)
     b.add_argument("--dtmax-units", type=int, default=1)
     b.add_argument("--orders", type=int, nargs="+", default=[8, 6])
+    b.add_argument("--forms", nargs="+", default=["fp32pair", "fp64"], choices=["fp32pair", "fp64"])
     c = sub.add_parser("batch")
     c.add_argument("--S", type=int, default=4096)
     c.add_argument("--steps", type=int, default=10000)
@@ -266,6 +295,7 @@ def main():
     d.add_argument("--steps-per-disc", type=int, default=8)
     d.add_argument("--epochs", type=int, default=30)
     d.add_argument("--max-passes", type=int, default=6)
+    d.add_argument("--ecc-steps", type=int, default=10)
     t1 = sub.add_parser("table1")
     t1.add_argument("--n", type=int, nargs="+", default=[3, 4])
     t1.add_argument("--eta", type=float, nargs="+", default=[0.08, 0.04, 0.02, 0.01, 0.005])

@@ -700,31 +700,50 @@ static int block_advance(mh_sim *sim, double dt, int n_iter)
         if (prec == MH_PREC_FP32PAIR)
             if (int rc = tuned_variant(sim, s.p, n_act, s.act, &ipt)) return rc;
         sim->ctr.pair_variant = ipt;
+        // partial sums by active position, rows of the padded active count
+        const int64_t part_ld = pad_to(n_act, 32);
+        // a few bodies due: one warp per (body, j-chunk) over all the sources
+        const bool short_list = n_act <= kShortActive && c.split_j == 0;
         for (int it = 0; it < n_iter; ++it) {
-            const PairPlan pl = plan_pair(s.p, prec, n_act, s.N, c.split_j, sim->device, ipt);
+            const PairPlan pl = short_list ? PairPlan{} : plan_pair(s.p, prec, n_act, s.N, c.split_j, sim->device, ipt);
+            const int split0 = short_list ? plan_short(n_act, s.N, sim->device) : pl.split;
             const bool heavy = prec == MH_PREC_FP32PAIR && s.n_heavy > 0;
-            const int slots = pl.split + (heavy ? 1 : 0);
-            if (int rc = ensure_part(s, (size_t)slots * (s.p + 1) * 3 * s.Np, sim->stream)) return rc;
+            const int slots = split0 + (heavy ? 1 : 0);
+            if (int rc = ensure_part(s, (size_t)slots * (s.p + 1) * 3 * part_ld, sim->stream)) return rc;
             std::pair<cudaEvent_t, cudaEvent_t> ev{};
             if (sim->timing) {
                 if (int rc = timed_event_pair(sim, &ev)) return rc;
                 MH_CUDA(cudaEventRecord(ev.first, sim->stream));
             }
-            if (int rc = launch_pair(s.p, prec, s.N, s.Np, s.m, s.jrec, s.jrec32, sim->eps, c.G, 0, n_act,
-                                     s.part, s.Np, pl, sim->stream, s.act))
+            if (short_list) {
+                if (int rc = launch_pair_short(s.p, prec, n_act, s.N, s.Np, s.m, s.jrec, s.jrec32, sim->eps, c.G,
+                                               s.part, part_ld, split0, s.act, sim->stream))
+                    return rc;
+            } else if (int rc = launch_pair(s.p, prec, s.N, s.Np, s.m, s.jrec, s.jrec32, sim->eps, c.G, 0, n_act,
+                                            s.part, part_ld, pl, sim->stream, s.act)) {
                 return rc;
+            }
             if (sim->timing) {
                 MH_CUDA(cudaEventRecord(ev.second, sim->stream));
                 sim->ev_pending.push_back(ev);
             }
             if (heavy) {
                 if (int rc = launch_pair_heavy(s.p, n_act, s.Np, s.m, s.jrec, s.heavy, s.n_heavy, sim->eps, c.G,
-                                               s.part, pl.split, sim->stream, s.act))
+                                               s.part, split0, sim->stream, s.act, part_ld))
                     return rc;
                 sim->ctr.kernel_launches += 1;
             }
             const bool last = it == n_iter - 1;
-            if (int rc = launch_block_phase(s, c, T_next, n_act, 1, last, slots, sim->stream)) return rc;
+            int split = slots;
+            if (slots > 16 && n_act <= 4096) {
+                // a short active list spread over many j-chunks: add the slots with
+                // one warp per (row, body) instead of one thread
+                if (int rc = launch_reduce_slots_warp(n_act, part_ld, (s.p + 1) * 3, slots, s.part, sim->stream))
+                    return rc;
+                sim->ctr.kernel_launches += 1;
+                split = 1;
+            }
+            if (int rc = launch_block_phase(s, c, T_next, n_act, 1, last, split, sim->stream, part_ld)) return rc;
             if (!last) s.flip ^= 1;
             sim->ctr.kernel_launches += 2;
             sim->ctr.evaluations += 1;

@@ -206,11 +206,16 @@ int mlp_dims(const mh_mlp *n, int *n_in, int *n_out);
 int launch_init_rows(const DeviceState &s, int have, cudaStream_t st);
 int launch_block_init(const DeviceState &s, const mh_config &cfg, cudaStream_t st);
 int launch_block_schedule(const DeviceState &s, const mh_config &cfg, cudaStream_t st);
+// part_ld: row stride of the active bodies' partial sums (by active position);
+// 0 = the padded body count.
 int launch_block_phase(const DeviceState &s, const mh_config &cfg, long long T_next, int64_t n_act,
-                       int phase, bool last, int split, cudaStream_t st);
+                       int phase, bool last, int split, cudaStream_t st, int64_t part_ld = 0);
 int launch_init_reduce(const DeviceState &s, int nr, int lo, int hi, int split, cudaStream_t st);
 // Small systems: slot 0 of s.part <- sum of its first `split` slots (rows nr).
 int launch_reduce_slots(const DeviceState &s, int nr, int split, cudaStream_t st);
+// Slot 0 of part (n positions, rows nr of stride ld) <- sum of its first `split`
+// slots, one warp per (row, position), in a fixed order.
+int launch_reduce_slots_warp(int64_t n, int64_t ld, int nr, int split, double *part, cudaStream_t st);
 int launch_reduce_out(int64_t n, int64_t ld_part, int nr, int split, const double *part, double *out,
                       cudaStream_t st);
 int launch_split32(int64_t N, int P, const double *traj, const double *m, double G, float *rows,
@@ -240,6 +245,16 @@ int launch_energy(const DeviceState &s, double eps, double G, double *scratch, d
                   cudaStream_t st);
 int launch_ecc(const DeviceState &s, double G, int central, double *ecc, cudaStream_t st);
 size_t energy_scratch_doubles(int64_t N);
+
+// Short active lists: one warp per (body, j-chunk), lanes over the sources.
+// plan_short gives the number of j-chunks (partial-sum slots); launch_pair_short
+// fills slots [0, split) of part (rows (P+1)*3 of stride part_ld, by active
+// position) for P = 1 .. 3 in either form.
+constexpr int64_t kShortActive = 256;
+int plan_short(int64_t n_i, int64_t n_j, int device);
+int launch_pair_short(int P, int precision, int64_t n_i, int64_t n_j, int64_t ld, const double *m,
+                      const double *jrec, const float *jrec32, double eps, double G, double *part,
+                      int64_t part_ld, int split, const int *ilist, cudaStream_t st);
 
 // FP32 form variant: 1 = one i-body per thread, 2 = two, 3 = two in packed FP32x2 lanes.
 PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hint, int device, int variant = 1);
@@ -287,10 +302,10 @@ int launch_pair_sym(int P, const SymPlan &plan, const SymSync &sync, const doubl
                     unsigned long long *wmax = nullptr);
 
 // FP64 contributions of the heavy source bodies to every body i < N, written
-// to partial slot `slot` (rows (P+1)*3 of stride ld) of part.
+// to partial slot `slot` (rows (P+1)*3 of stride part_ld, 0 = ld) of part.
 int launch_pair_heavy(int P, int64_t N, int64_t ld, const double *m, const double *jrec,
                       const int *heavy, int n_heavy, double eps, double G, double *part, int slot,
-                      cudaStream_t st, const int *ilist = nullptr);
+                      cudaStream_t st, const int *ilist = nullptr, int64_t part_ld = 0);
 
 // Number of FP32 rows of the precision-form evaluation input for a given P.
 __host__ __device__ constexpr int nf32(int P) { return 12 + 3 * (P >= 2) + 3 * (P >= 3) + 1; }

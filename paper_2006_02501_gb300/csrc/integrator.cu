@@ -656,6 +656,25 @@ __global__ void k_reduce_slots(int64_t N, int64_t ld, int nr, int split, double 
     part[(int64_t)r * ld + i] = s;
 }
 
+// Slot 0 <- the sum of `split` slots, one warp per (row, position): lane l adds
+// slots l, l + 32, ... in order, then the lanes' sums meet in a fixed tree, so
+// the result does not depend on scheduling.  For short active lists with many
+// j-chunks, where one thread per (row, position) would add hundreds of slots
+// one after another.
+__global__ void k_reduce_slots_warp(int64_t n, int64_t ld, int nr, int split, double *part)
+{
+    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (e >= (int64_t)nr * n) return;            // whole warps leave together
+    const int r = (int)(e / n);
+    const int64_t i = e - (int64_t)r * n;
+    double s = 0.0;
+    for (int q = lane; q < split; q += 32) s += part[((int64_t)q * nr + r) * ld + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) part[(int64_t)r * ld + i] = s;
+}
+
 // d0 rows [lo, hi) <- sum over S partial slots of rows [lo, hi) (slot row count nr).
 __global__ void k_init_reduce(int64_t N, int64_t ld, int nr, int lo, int hi, int split,
                               const double *part, double *d0)
@@ -764,10 +783,11 @@ int launch_block_kernels(const StepArgs &a, const BlockArgs &b, int phase, bool 
     return MH_OK;
 }
 
-static BlockArgs block_args(const DeviceState &s, const mh_config &cfg, long long T_next, int64_t n_act)
+static BlockArgs block_args(const DeviceState &s, const mh_config &cfg, long long T_next, int64_t n_act,
+                            int64_t part_ld)
 {
     BlockArgs b{s.T, s.level, s.act, s.blk, cfg.k_max, cfg.dt_max, ldexp(cfg.dt_max, -cfg.k_max),
-                cfg.eta, T_next, n_act, s.Np};
+                cfg.eta, T_next, n_act, part_ld};
     return b;
 }
 
@@ -814,14 +834,14 @@ int launch_learned_apply(const DeviceState &s, const mh_config &cfg, double dt, 
 
 int launch_block_init(const DeviceState &s, const mh_config &cfg, cudaStream_t st)
 {
-    k_block_init_levels<<<blocks_for(s.N, 128), 128, 0, st>>>(s.N, s.Np, s.d0, block_args(s, cfg, 0, 0));
+    k_block_init_levels<<<blocks_for(s.N, 128), 128, 0, st>>>(s.N, s.Np, s.d0, block_args(s, cfg, 0, 0, s.Np));
     MH_LAUNCHED("k_block_init_levels");
     return MH_OK;
 }
 
 int launch_block_schedule(const DeviceState &s, const mh_config &cfg, cudaStream_t st)
 {
-    const BlockArgs b = block_args(s, cfg, 0, 0);
+    const BlockArgs b = block_args(s, cfg, 0, 0, s.Np);
     k_block_reset<<<1, 1, 0, st>>>(s.blk);
     MH_LAUNCHED("k_block_reset");
     k_block_next<<<blocks_for(s.N, 128), 128, 0, st>>>(s.N, b);
@@ -833,12 +853,12 @@ int launch_block_schedule(const DeviceState &s, const mh_config &cfg, cudaStream
 
 // phase 0: predict all bodies to T_next; phase 1: correct the active list.
 int launch_block_phase(const DeviceState &s, const mh_config &cfg, long long T_next, int64_t n_act,
-                       int phase, bool last, int split, cudaStream_t st)
+                       int phase, bool last, int split, cudaStream_t st, int64_t part_ld)
 {
     StepArgs a{s.N, s.Np, 0.0, s.m, s.x0, s.v0, s.d0, s.x1, s.v1, s.jrec, s.jrec32, s.part,
                split, cfg.precision, cfg.beta_mode, s.flag,
                s.bound ? s.bound + 2 * s.flip : nullptr, s.bound ? s.bound + 2 * (1 - s.flip) : nullptr};
-    const BlockArgs b = block_args(s, cfg, T_next, n_act);
+    const BlockArgs b = block_args(s, cfg, T_next, n_act, part_ld > 0 ? part_ld : s.Np);
     switch (s.p) {
     case 2: return launch_block_kernels<2>(a, b, phase, last, st);
     case 3: return launch_block_kernels<3>(a, b, phase, last, st);
@@ -880,6 +900,14 @@ int launch_reduce_slots(const DeviceState &s, int nr, int split, cudaStream_t st
     const int64_t n = (int64_t)nr * s.N;
     k_reduce_slots<<<blocks_for(n, 32), 32, 0, st>>>(s.N, s.Np, nr, split, s.part);
     MH_LAUNCHED("k_reduce_slots");
+    return MH_OK;
+}
+
+int launch_reduce_slots_warp(int64_t n, int64_t ld, int nr, int split, double *part, cudaStream_t st)
+{
+    const int64_t warps = (int64_t)nr * n;
+    k_reduce_slots_warp<<<(unsigned)((warps + 3) / 4), 128, 0, st>>>(n, ld, nr, split, part);
+    MH_LAUNCHED("k_reduce_slots_warp");
     return MH_OK;
 }
 

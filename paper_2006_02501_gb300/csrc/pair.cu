@@ -29,6 +29,7 @@
 //             sums run in FP32 over one shared-memory tile and are added to
 //             FP64 accumulators after every tile.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "hermite_consts.cuh"
@@ -511,7 +512,7 @@ template <int P>
 __global__ void k_pair_heavy(int64_t N, int64_t ld, const double *__restrict__ m,
                              const double *__restrict__ jrec, const int *__restrict__ heavy,
                              int n_heavy, double eps2, double G, double *__restrict__ out,
-                             const int *__restrict__ ilist)
+                             int64_t out_ld, const int *__restrict__ ilist)
 {
     const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= N) return;                       // N: number of positions (bodies or active list)
@@ -541,7 +542,7 @@ __global__ void k_pair_heavy(int64_t N, int64_t ld, const double *__restrict__ m
 #pragma unroll
     for (int k = 0; k <= P; ++k)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) out[(3 * k + c) * ld + pos] = acc[k][c];
+        for (int c = 0; c < 3; ++c) out[(3 * k + c) * out_ld + pos] = acc[k][c];
 }
 
 template <int P>
@@ -607,18 +608,132 @@ int launch_fp32(const float *jrec32, int64_t ld, int64_t n_j, double eps, int64_
 
 int launch_pair_heavy(int P, int64_t N, int64_t ld, const double *m, const double *jrec,
                       const int *heavy, int n_heavy, double eps, double G, double *part, int slot,
-                      cudaStream_t st, const int *ilist)
+                      cudaStream_t st, const int *ilist, int64_t part_ld)
 {
-    double *out = part + (int64_t)slot * (P + 1) * 3 * ld;
+    const int64_t pld = part_ld > 0 ? part_ld : ld;
+    double *out = part + (int64_t)slot * (P + 1) * 3 * pld;
     const unsigned g = (unsigned)((N + 127) / 128);
+    const double e2 = eps * eps;
     switch (P) {
-    case 1: k_pair_heavy<1><<<g, 128, 0, st>>>(N, ld, m, jrec, heavy, n_heavy, eps * eps, G, out, ilist); break;
-    case 2: k_pair_heavy<2><<<g, 128, 0, st>>>(N, ld, m, jrec, heavy, n_heavy, eps * eps, G, out, ilist); break;
-    case 3: k_pair_heavy<3><<<g, 128, 0, st>>>(N, ld, m, jrec, heavy, n_heavy, eps * eps, G, out, ilist); break;
+    case 1: k_pair_heavy<1><<<g, 128, 0, st>>>(N, ld, m, jrec, heavy, n_heavy, e2, G, out, pld, ilist); break;
+    case 2: k_pair_heavy<2><<<g, 128, 0, st>>>(N, ld, m, jrec, heavy, n_heavy, e2, G, out, pld, ilist); break;
+    case 3: k_pair_heavy<3><<<g, 128, 0, st>>>(N, ld, m, jrec, heavy, n_heavy, e2, G, out, pld, ilist); break;
     default: set_error("launch_pair_heavy: P must be 1..3"); return MH_EINVAL;
     }
     MH_LAUNCHED("k_pair_heavy");
     return MH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Short active lists (block steps at which only a few bodies are due): one warp
+// per (active body, j-chunk), the lanes over the chunk's sources in strides of
+// 32, so that every lane evaluates useful pairs; the lanes' sums meet in a
+// fixed shuffle tree (deterministic), and each (body, chunk) writes its own
+// partial-sum slot.  FP32-pair: the precision form's pair arithmetic with FP32
+// sums over at most 64 pairs per lane, added to FP64; the heavy bodies (mass 0
+// in the FP32 rows) are added by k_pair_heavy.  FP64: the plain form.
+// ---------------------------------------------------------------------------
+
+template <int P>
+struct ShortArgs {
+    const double *jrec;   // FP64 rows [3(P+1)][ld] (FP64 form)
+    const double *m;      // masses (FP64 form)
+    const float *jrec32;  // FP32 rows [nf32(P)][ld] (precision form)
+    int64_t ld, n_j, n_i;
+    double eps2, G;
+    double *part;         // [S][(P+1)*3][part_ld], by active position
+    int64_t part_ld, chunk;
+    int split;
+    const int *ilist;     // active position -> body
+};
+
+template <int P, bool kF32>
+__global__ void __launch_bounds__(128) k_pair_short(ShortArgs<P> a)
+{
+    constexpr int NR = (P + 1) * 3;
+    const int lane = threadIdx.x & 31;
+    const int64_t items = a.n_i * a.split;
+    for (int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < items;
+         item += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t pos = item % a.n_i;
+        const int jc = (int)(item / a.n_i);
+        const int64_t i = a.ilist[pos];
+        const int64_t jb = (int64_t)jc * a.chunk;
+        const int64_t je = min(jb + a.chunk, a.n_j);
+        double acc64[P + 1][3];
+#pragma unroll
+        for (int k = 0; k <= P; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc64[k][c] = 0.0;
+        if constexpr (kF32) {
+            constexpr int NF = Rec32<P>::NF;
+            float xh[3], xl[3], vh[3], vl[3], ai[3], ji[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                xh[c] = a.jrec32[(0 + c) * a.ld + i];
+                xl[c] = a.jrec32[(3 + c) * a.ld + i];
+                vh[c] = a.jrec32[(6 + c) * a.ld + i];
+                vl[c] = a.jrec32[(9 + c) * a.ld + i];
+                ai[c] = P >= 2 ? a.jrec32[(12 + c) * a.ld + i] : 0.0f;
+                ji[c] = P >= 3 ? a.jrec32[(15 + c) * a.ld + i] : 0.0f;
+            }
+            const float eps2 = (float)a.eps2;
+            for (int64_t j0 = jb; j0 < je; j0 += 64 * 32) {
+                float acc[P + 1][3];
+#pragma unroll
+                for (int k = 0; k <= P; ++k)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) acc[k][c] = 0.0f;
+                const int64_t j1 = min(j0 + 64 * 32, je);
+                for (int64_t j = j0 + lane; j < j1; j += 32) {
+                    float rec[NF];
+#pragma unroll
+                    for (int q = 0; q < NF; ++q) rec[q] = a.jrec32[q * a.ld + j];
+                    interact32<P, true>(rec, j == i, xh, xl, vh, vl, ai, ji, eps2, acc);
+                }
+#pragma unroll
+                for (int k = 0; k <= P; ++k)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) acc64[k][c] += (double)acc[k][c];
+            }
+        } else {
+            double ri[P + 1][3];
+#pragma unroll
+            for (int k = 0; k <= P; ++k)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) ri[k][c] = a.jrec[(3 * k + c) * a.ld + i];
+            for (int64_t j = jb + lane; j < je; j += 32) {
+                double r[P + 1][3];
+#pragma unroll
+                for (int k = 0; k <= P; ++k)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) r[k][c] = a.jrec[(3 * k + c) * a.ld + j] - ri[k][c];
+                double s = fma(r[0][0], r[0][0], fma(r[0][1], r[0][1], fma(r[0][2], r[0][2], a.eps2)));
+                const bool self = j == i;
+                s = self ? 1.0 : s;
+                const double rinv = rsqrt_fp64(s);
+                const double sinv = rinv * rinv;
+                const double mS = self ? 0.0 : a.G * a.m[j] * (rinv * sinv);
+                pair_derivs<P, double>(r, mS, sinv, acc64);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k <= P; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                double v = acc64[k][c];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                acc64[k][c] = v;
+            }
+        if (lane == 0) {
+            double *out = a.part + (int64_t)jc * NR * a.part_ld + pos;
+#pragma unroll
+            for (int k = 0; k <= P; ++k)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) out[(3 * k + c) * a.part_ld] = acc64[k][c];
+        }
+    }
 }
 
 // FP64 plan for evaluations too small to fill the GPU with 128-body i-tiles
@@ -638,9 +753,19 @@ static PairPlan plan_fine64(int64_t n_i, int64_t n_j, int split_hint, int n_sm)
     const int64_t n_jt = (n_j + pl.tj - 1) / pl.tj;
     int best_S = 1;
     double best_cost = 1e300;
-    const int s_max = (int)std::min<int64_t>(64, n_jt);
+    // up to 64 j-chunks, more when few i-tiles would leave SMs idle (active lists
+    // of a few bodies under block steps: the callers size the partial sums by
+    // the evaluated bodies, so the extra slots are small)
+    const int s_cap = (int)std::max<int64_t>(64, std::min<int64_t>(slots / std::max<int64_t>(pl.n_itiles, 1), 512));
+    const int s_max = (int)std::min<int64_t>(s_cap, n_jt);
+    // a split hint takes the largest split <= hint that cuts the j-tiles into
+    // chunks of equal length (the hint itself when it does)
+    int hinted = 0;
+    if (split_hint > 0)
+        for (int S = std::min(split_hint, s_max); S >= 1 && !hinted; --S)
+            if ((n_jt + (n_jt + S - 1) / S - 1) / ((n_jt + S - 1) / S) == S) hinted = S;
     for (int S = 1; S <= s_max; ++S) {
-        if (split_hint > 0 && S != std::min(split_hint, s_max)) continue;
+        if (hinted && S != hinted) continue;
         const int64_t tiles_per_chunk = (n_jt + S - 1) / S;
         if ((n_jt + tiles_per_chunk - 1) / tiles_per_chunk != S) continue;
         const int64_t waves = (pl.n_itiles * S + slots - 1) / slots;
@@ -675,9 +800,19 @@ PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hin
     const int64_t n_jt = (n_j + pl.tj - 1) / pl.tj;        // j-tiles
     int best_S = 1;
     double best_cost = 1e300;
-    const int s_max = (int)std::min<int64_t>(64, n_jt);
+    // up to 64 j-chunks, more when few i-tiles would leave SMs idle (active lists
+    // of a few bodies under block steps: the callers size the partial sums by
+    // the evaluated bodies, so the extra slots are small)
+    const int s_cap = (int)std::max<int64_t>(64, std::min<int64_t>(slots / std::max<int64_t>(pl.n_itiles, 1), 512));
+    const int s_max = (int)std::min<int64_t>(s_cap, n_jt);
+    // a split hint takes the largest split <= hint that cuts the j-tiles into
+    // chunks of equal length (the hint itself when it does)
+    int hinted = 0;
+    if (split_hint > 0)
+        for (int S = std::min(split_hint, s_max); S >= 1 && !hinted; --S)
+            if ((n_jt + (n_jt + S - 1) / S - 1) / ((n_jt + S - 1) / S) == S) hinted = S;
     for (int S = 1; S <= s_max; ++S) {
-        if (split_hint > 0 && S != std::min(split_hint, s_max)) continue;
+        if (hinted && S != hinted) continue;
         const int64_t tiles_per_chunk = (n_jt + S - 1) / S;
         const int64_t S_eff = (n_jt + tiles_per_chunk - 1) / tiles_per_chunk;
         if (S_eff != S) continue;
@@ -694,6 +829,50 @@ PairPlan plan_pair(int P, int precision, int64_t n_i, int64_t n_j, int split_hin
     pl.grid = (int)std::min<int64_t>(items, slots);
     if (precision == MH_PREC_FP64 && items < 2 * (int64_t)n_sm) return plan_fine64(n_i, n_j, split_hint, n_sm);
     return pl;
+}
+
+int plan_short(int64_t n_i, int64_t n_j, int device)
+{
+    static int n_sm_cache[64] = {0};
+    int n_sm = device >= 0 && device < 64 ? n_sm_cache[device] : 0;
+    if (n_sm == 0) {
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
+        if (n_sm <= 0) n_sm = 148;
+        if (device >= 0 && device < 64) n_sm_cache[device] = n_sm;
+    }
+    // about 16 warps per SM in all, and at least 64 sources per warp
+    const int64_t want = (16 * (int64_t)n_sm + n_i - 1) / std::max<int64_t>(n_i, 1);
+    const int64_t cap = std::max<int64_t>(1, n_j / 64);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(want, cap), 4096));
+}
+
+int launch_pair_short(int P, int precision, int64_t n_i, int64_t n_j, int64_t ld, const double *m,
+                      const double *jrec, const float *jrec32, double eps, double G, double *part,
+                      int64_t part_ld, int split, const int *ilist, cudaStream_t st)
+{
+    if (P < 1 || P > 3 || split < 1 || n_i < 1) {
+        set_error("launch_pair_short: P must be 1..3, split and n_i positive");
+        return MH_EINVAL;
+    }
+    const int64_t chunk = (n_j + split - 1) / split;
+    const int64_t warps = n_i * split;
+    const unsigned grid = (unsigned)std::min<int64_t>((warps + 3) / 4, 65535);
+    const bool f32 = precision == MH_PREC_FP32PAIR;
+    auto go = [&](auto tag) -> int {
+        constexpr int PP = decltype(tag)::value;
+        ShortArgs<PP> a{jrec, m, jrec32, ld, n_j, n_i, eps * eps, G, part, part_ld, chunk, split, ilist};
+        if (f32)
+            k_pair_short<PP, true><<<grid, 128, 0, st>>>(a);
+        else
+            k_pair_short<PP, false><<<grid, 128, 0, st>>>(a);
+        MH_LAUNCHED("k_pair_short");
+        return MH_OK;
+    };
+    switch (P) {
+    case 1: return go(std::integral_constant<int, 1>{});
+    case 2: return go(std::integral_constant<int, 2>{});
+    default: return go(std::integral_constant<int, 3>{});
+    }
 }
 
 int launch_pair(int P, int precision, int64_t n_j, int64_t ld, const double *m, const double *jrec,

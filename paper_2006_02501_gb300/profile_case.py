@@ -14,6 +14,10 @@ initialisation also launches one evaluation (k_dd_pair) per pass.
 memory checker): FP64 with the pair-symmetric and the ordered kernel, the
 FP32-pair form with both (orders up to 8), the double-double form, and a
 double-double batch of three systems cut from the disc.
+--precision batch runs the batched form instead: --N planetary systems of 3 to
+64 bodies (the bench's recipe, seed 4), 6th order, P(EC)^2, dt = P_min/128,
+--steps steps in one launch after a fixed configuration (6 warps per CTA,
+largest systems first), so that the profiled launch is the first k_batch one.
 """
 import argparse
 import os
@@ -25,7 +29,7 @@ import numpy as np
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--N", type=int, default=16384)
-    ap.add_argument("--precision", choices=["fp64", "fp32pair", "dd", "all"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "fp32pair", "dd", "all", "batch"], default="fp64")
     ap.add_argument("--order", type=int, default=8)
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--n-iter", type=int, default=3)
@@ -36,6 +40,13 @@ def main():
     import paper_2006_02501_gb300 as mh
     from paper_2006_02501_gb300 import inputs
     mh.build_library()
+    if a.precision == "batch":
+        off, m, x, v, pmin = inputs.planetary_systems(seed=4, S=a.N)
+        with mh.Batch(6, off, m, x, v, pmin / 128.0, 1e-8) as b:
+            b.step(a.steps, 2)
+            ok = bool(np.isfinite(b.sync()[1]).all())
+        print(f"ok batch systems {a.N} bodies {int(off[-1])} steps {a.steps} finite={ok}")
+        return
     m, x, v = inputs.smbh_disc(seed=2, N=a.N)
     dt = 2 * np.pi * 1e-3
     if a.precision == "all":

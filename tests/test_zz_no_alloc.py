@@ -68,6 +68,34 @@ def test_noalloc_matches_allocating_entry_point_twice(L, P, prec, tol_a, tol_k):
             assert rel_rows(got[:, k], ref[:, k], 1e-6) < tol_k, (call, k)
 
 
+def test_noalloc_shrinks_the_split_to_fit(L):
+    """A problem whose normal plan does not fit the fixed scratch: the precision
+    form on 400000 bodies (its FP32 input rows take 30 MB of the 32 MiB) for
+    2000 bodies, whose j-split must shrink from the planner's to at most 16 slots
+    of 192 KB.  The result still matches mh_pair_eval's, twice in a row."""
+    m, x, v = I.smbh_disc(seed=23, N=399999)
+    traj = kepler_traj(m, x, v, 3)
+    for i0 in (1000, 250000):
+        rc_ref, ref = _call(L.mh_pair_eval, 3, 1, m, traj, 1e-4, i0, i0 + 2000)
+        rc, got = _call(L.mh_pair_eval_noalloc, 3, 1, m, traj, 1e-4, i0, i0 + 2000)
+        assert rc_ref == 0 and rc == 0, L.mh_last_error()
+        assert rel_rows(got[:, 0], ref[:, 0]) < 2e-6
+        for k in range(1, 4):
+            assert rel_rows(got[:, k], ref[:, k], 1e-6) < 5e-5, k
+
+
+def test_noalloc_matches_oracle(L, orc):
+    """The allocation-free path against the CPU oracle directly (FP64, P = 3, a
+    range of bodies that spans several i-tiles with a ragged end), at 1e-12."""
+    m, x, v = I.smbh_disc(seed=24, N=2999)
+    traj = kepler_traj(m, x, v, 3)
+    rc, got = _call(L.mh_pair_eval_noalloc, 3, 0, m, traj, 1e-4, 37, 1337)
+    assert rc == 0, L.mh_last_error()
+    ref = orc.evaluate(m, traj, 1e-4, i0=37, i1=1337)
+    for k in range(4):
+        assert rel_rows(got[:, k], ref[:, k], 1e-6) < 1e-12, k
+
+
 def test_noalloc_rejects_oversize_problem(L):
     # 6 * 3 * 300000 doubles of one partial-sum slot exceed the 32 MiB scratch
     p = ctypes.c_void_p(16)        # never dereferenced: the size check comes first
