@@ -38,8 +38,15 @@
  *     mh_dd_create_batch fail with MH_ENOMEM, freeing what was allocated),
  *     "launch" / "timeout" (mh_step, mh_dd_step and mh_dd_step_batch return
  *     MH_ECUDA / MH_ETIMEOUT before queuing work, leaving the state unchanged),
- *     "nonfinite" (mh_sync and mh_dd_sync return MH_ENONFINITE).  The library
- *     has no device-side waits; MH_ETIMEOUT exists for callers' handling paths.
+ *     "nonfinite" (mh_sync and mh_dd_sync return MH_ENONFINITE), "symwait"
+ *     (the bounded waits of the pair-symmetric evaluation cannot end and run
+ *     out after 20 ms; the step's launches still end and the next mh_sync
+ *     returns MH_ETIMEOUT).
+ *   - Device-side waits: the CTAs of a pair-symmetric evaluation (shared steps,
+ *     2048 or more bodies) add their sums into shared partial-sum slots in a
+ *     fixed order and wait for their turn; every wait is bounded (4 s).  A wait
+ *     that runs out marks the state invalid: mh_sync and mh_diagnostics then
+ *     return MH_ETIMEOUT.
  */
 #ifndef MH_H
 #define MH_H

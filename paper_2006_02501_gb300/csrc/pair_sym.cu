@@ -64,12 +64,10 @@ namespace {
 
 constexpr int kSymWarps = 4;
 constexpr int kSymR = 32 * kSymWarps;     // bodies per block
-// Accumulation chains per j-slot: the writer before row I in its chain is row
-// I - G, which reaches the block G sweeps earlier, so a row may run up to G - 1
-// blocks ahead of the rows before it without waiting.
-constexpr int kSymChains64 = 4;
-// The precision form runs K rows per CTA, one CTA per SM, and one chain (see
-// k_pair_fp32_sym): K = 6 where six rows' shared memory fits, else 4.
+// Both forms run K rows of one chunk per CTA, one CTA per SM, and one
+// accumulation chain (G = 1): FP64 K = 3 (2 above P = 3), FP32-pair K = 6 where
+// six rows' shared memory fits, else 4.  The turn computation takes any G
+// (rows split into chains by row mod G); the plans use G = 1.
 
 // Schedule of one launch (from SymPlan) and the ordered-accumulation words.
 struct SymSched {
@@ -212,15 +210,16 @@ __host__ __device__ __forceinline__ int64_t j_slot(const SymSched &sc, int ch, i
     return (int64_t)sc.C + (int64_t)ch * sc.G + g;
 }
 
-// Warp 0 before row I's ordered flush into j-slot (ch, I mod G, J): publish the
-// rank (0: this row writes first) and whether the turn has come (one look).
-__device__ __forceinline__ void flush_rank(const SymSched &sc, FlushSmem &fs, int I, int J, int ch, int b)
+// Warp 0 of a row's threads (tu: thread index within the row) before row I's
+// ordered flush into j-slot (ch, I mod G, J): publish the rank (0: this row
+// writes first) and whether the turn has come (one look).
+__device__ __forceinline__ void flush_rank(const SymSched &sc, FlushSmem &fs, int tu, int I, int J, int ch, int b)
 {
-    if (threadIdx.x < 32) {
+    if (tu < 32) {
         const int g = I % sc.G;
         int rank = 0;
         const int nw = j_writers_warp(sc, J, ch, g, I, b, &rank);
-        if (threadIdx.x == 0) {
+        if (tu == 0) {
             fs.rank = rank;
             fs.next = rank + 1 == nw ? 0 : rank + 1;
             fs.ready = rank == 0 ||
@@ -229,22 +228,28 @@ __device__ __forceinline__ void flush_rank(const SymSched &sc, FlushSmem &fs, in
     }
 }
 
-// Thread 0: wait (bounded) for the turn flush_rank published, unless it had come.
-__device__ __forceinline__ void flush_wait(const SymSched &sc, FlushSmem &fs, int I, int J, int ch)
+// The row's thread 0: wait (bounded) for the turn flush_rank published, unless it had come.
+__device__ __forceinline__ void flush_wait(const SymSched &sc, FlushSmem &fs, int tu, int I, int J, int ch)
 {
-    if (threadIdx.x == 0 && !fs.ready) {
+    if (tu == 0 && !fs.ready) {
         wait_turn(&sc.count[(j_slot(sc, ch, I % sc.G) - sc.C) * sc.nB + J], (unsigned)fs.rank + sc.bias, sc);
         fs.ready = 1;
     }
 }
 
-// Thread 0 after the CTA's stores of the flush (behind a barrier): pass the
-// turn on with a release store, which orders the whole CTA's stores before it
-// (the last writer leaves the counter at 0).
-__device__ __forceinline__ void flush_end(const SymSched &sc, const FlushSmem &fs, int I, int J, int ch)
+// The row's thread 0 after the row's stores of the flush (behind the row's
+// barrier): pass the turn on with a release store, which orders the row's
+// stores before it (the last writer leaves the counter at 0).
+__device__ __forceinline__ void flush_end(const SymSched &sc, const FlushSmem &fs, int tu, int I, int J, int ch)
 {
-    if (threadIdx.x == 0)
+    if (tu == 0)
         st_release(&sc.count[(j_slot(sc, ch, I % sc.G) - sc.C) * sc.nB + J], (unsigned)fs.next);
+}
+
+// Barrier of the n threads of row u of an item (barrier 0 is __syncthreads).
+__device__ __forceinline__ void row_sync(int u, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(u + 1), "r"(n) : "memory");
 }
 
 template <int P>
@@ -290,35 +295,53 @@ __device__ __forceinline__ void rotate(double (&r)[P + 1][3], double &gm, int sr
     gm = __shfl_sync(0xffffffffu, gm, src);
 }
 
+// Rows per CTA of the FP64 kernel: 12 warps per SM at P <= 3, 8 above (its
+// registers).
+template <int P>
+__host__ __device__ constexpr int sym64_rows() { return P <= 3 ? 3 : 2; }
+
 // kH: also track w = G (m_i + m_j) s^(-3/2) over all pairs i != j, whose maximum
 // gives the time-step criterion of Section 3.3 (Eq. 24: H = eta w_max^(-1/2)).
 // Non-negative doubles order as their bit patterns, so the maximum is an
 // integer maximum (off the FP64 pipe) and the result does not depend on the
 // order of the pairs.
+//
+// A CTA takes K = sym64_rows<P>() consecutive rows of one chunk (4 warps per
+// row, one CTA per SM) and one accumulation chain, as the precision form's
+// kernel below: the writer before a row is the previous row of the same CTA,
+// which reaches the block one block earlier.  A row's warps meet at named
+// barriers of their own; the rows of a CTA only at the item boundaries.
 template <int P, bool kH>
-__global__ void __launch_bounds__(kSymR, P <= 3 ? 3 : 2) k_pair_fp64_sym(SymArgs<P> a)
+__global__ void __launch_bounds__(kSymR * sym64_rows<P>(), 1) k_pair_fp64_sym(SymArgs<P> a)
 {
     constexpr int NR = 3 * (P + 1);
+    constexpr int K = sym64_rows<P>();
     const SymSched &sc = a.sc;
     unsigned long long wm = 0ull;
-    __shared__ double accs[NR][kSymR];    // j-side sums of the current block, by column
-    __shared__ FlushSmem fs;
-    const int lane = threadIdx.x & 31;
-    const int w = threadIdx.x >> 5;
+    __shared__ double accs_all[K][NR][kSymR];   // per row: j-side sums of the current block, by column
+    __shared__ FlushSmem fsu[K];
+    __shared__ int s_item;
+    const int u = threadIdx.x / kSymR;           // this thread's row of the item
+    const int tu = threadIdx.x % kSymR;          // thread within the row's four warps
+    const int lane = tu & 31;
+    const int w = tu >> 5;
     const int src = (lane + 1) & 31;      // ring: after t passes lane l holds j-lane (l + t) mod 32
+    double(*accs)[kSymR] = accs_all[u];
+    FlushSmem &fs = fsu[u];
     const bool even = (sc.nB & 1) == 0;
     for (int n = 0;; ++n) {
-        if (threadIdx.x == 0) fs.item = (int)min(next_item(sc, n), (unsigned)sc.items);
+        if (threadIdx.x == 0) s_item = (int)min(next_item(sc, n), (unsigned)sc.items);
         __syncthreads();
-        const int item = fs.item;
+        const int item = s_item;
         if (item >= sc.items) break;
-        const int I = item / sc.C;
+        const int I = (item / sc.C) * K + u;
         const int ch = item % sc.C;
-        if (threadIdx.x < 32) {
-            const unsigned z = unwritten_chains(sc, I, ch);
-            if (threadIdx.x == 0) fs.zero = z;
+        const bool live = I < sc.nB;
+        if (tu < 32) {
+            const unsigned z = live ? unwritten_chains(sc, I, ch) : 0u;
+            if (tu == 0) fs.zero = z;
         }
-        const int64_t ib = (int64_t)I * kSymR + threadIdx.x;
+        const int64_t ib = (int64_t)(live ? I : 0) * kSymR + tu;
         double ri[P + 1][3], gmi;
         load_body<P>(a, ib, ri, gmi);
         double acci[P + 1][3];
@@ -328,7 +351,7 @@ __global__ void __launch_bounds__(kSymR, P <= 3 ? 3 : 2) k_pair_fp64_sym(SymArgs
             for (int c = 0; c < 3; ++c) acci[k][c] = 0.0;
         __syncthreads();
         for (int g = 0; g < sc.G; ++g)
-            if (fs.zero >> g & 1u) {
+            if (live && (fs.zero >> g & 1u)) {
                 // no row adds into this j-slot of the block: it holds zeros
                 double *out = a.part + j_slot(sc, ch, g) * NR * a.ld + ib;
 #pragma unroll
@@ -337,9 +360,11 @@ __global__ void __launch_bounds__(kSymR, P <= 3 ? 3 : 2) k_pair_fp64_sym(SymArgs
 
         const int dmax = (even && I >= sc.nB / 2) ? sc.D - 1 : sc.D;
         const int b0 = ch * sc.Bc;
-        const int b1 = min(b0 + sc.Bc, dmax + 1);
+        const int b1 = min(b0 + sc.Bc, sc.D + 1);
         for (int b = b1 - 1; b >= b0; --b) {
+            const bool active = live && b <= dmax;   // rows >= nB/2 skip distance nB/2
             if (b == 0) {
+                if (!active) continue;
                 // diagonal block: ordered pairs into the i-side only
                 for (int js = 0; js < kSymWarps; ++js) {
                     double rj[P + 1][3], gmj;
@@ -370,6 +395,7 @@ __global__ void __launch_bounds__(kSymR, P <= 3 ? 3 : 2) k_pair_fp64_sym(SymArgs
                 }
                 continue;
             }
+            if (!active) continue;                   // the row's four warps skip together
             const int J = (I + b) % sc.nB;
             for (int jt = 0; jt < kSymWarps; ++jt) {
                 const int js = (w + jt) % kSymWarps;
@@ -408,27 +434,29 @@ __global__ void __launch_bounds__(kSymR, P <= 3 ? 3 : 2) k_pair_fp64_sym(SymArgs
                 for (int k = 0; k <= P; ++k)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) accs[3 * k + c][js * 32 + lane] = accj[k][c];
-                __syncthreads();
+                row_sync(u, kSymR);
             }
             // ordered flush of block J's j-side sums into j-slot (ch, I mod G, J)
-            flush_rank(sc, fs, I, J, ch, b);
-            flush_wait(sc, fs, I, J, ch);
-            __syncthreads();
+            flush_rank(sc, fs, tu, I, J, ch, b);
+            flush_wait(sc, fs, tu, I, J, ch);
+            row_sync(u, kSymR);
             const bool add = fs.rank > 0;
-            double *out = a.part + j_slot(sc, ch, I % sc.G) * NR * a.ld + (int64_t)J * kSymR + threadIdx.x;
+            double *out = a.part + j_slot(sc, ch, I % sc.G) * NR * a.ld + (int64_t)J * kSymR + tu;
 #pragma unroll
             for (int q = 0; q < NR; ++q) {
-                const double v = accs[q][threadIdx.x];
+                const double v = accs[q][tu];
                 __stcg(out + q * a.ld, add ? __ldcg(out + q * a.ld) + v : v);
             }
-            __syncthreads();
-            flush_end(sc, fs, I, J, ch);
+            row_sync(u, kSymR);
+            flush_end(sc, fs, tu, I, J, ch);
         }
-        double *out = a.part + (int64_t)ch * NR * a.ld + ib;
+        if (live) {
+            double *out = a.part + (int64_t)ch * NR * a.ld + ib;
 #pragma unroll
-        for (int k = 0; k <= P; ++k)
+            for (int k = 0; k <= P; ++k)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) out[(3 * k + c) * a.ld] = acci[k][c];
+                for (int c = 0; c < 3; ++c) out[(3 * k + c) * a.ld] = acci[k][c];
+        }
     }
     if constexpr (kH) {
 #pragma unroll
@@ -471,7 +499,7 @@ int launch_sym(const SymPlan &pl, const SymSync &sy, const double *jrec, const d
                double eps, double G, double *part, unsigned long long *wmax, cudaStream_t st)
 {
     SymArgs<P> a{jrec, m, ld, N, make_sched(pl, sy), eps * eps, G, part, wmax};
-    const SymLaunch l(pl, kSymR, st);
+    const SymLaunch l(pl, kSymR * sym64_rows<P>(), st);
     if (wmax)
         MH_CUDA(cudaLaunchKernelEx(&l.cfg, k_pair_fp64_sym<P, true>, a));
     else
@@ -612,12 +640,6 @@ __device__ __forceinline__ void cp_async_commit()
 // hidden behind a block of pair arithmetic.  The i-side FP64 sums of the item
 // live in shared memory.  Shared memory per CTA: K (2 + 2 + 2) NR 128 words
 // (dynamic, up to 216 KB at K = 6, P = 3).
-// Barrier of the 64 threads of row u of the item (barrier 0 is __syncthreads).
-__device__ __forceinline__ void row_sync(int u)
-{
-    asm volatile("bar.sync %0, 64;" ::"r"(u + 1) : "memory");
-}
-
 template <int P>
 struct Smem32 {
     static constexpr int NR = 3 * (P + 1);
@@ -708,7 +730,7 @@ __global__ void __launch_bounds__(64 * K, 1) k_pair_fp32_sym(SymArgs32<P> a)
                 wait_turn(&sc.count[(j_slot(sc, ch, 0) - sc.C) * sc.nB + pend_J[u]], (unsigned)fs.rank + sc.bias, sc);
                 fs.ready = 1;
             }
-            row_sync(u);
+            row_sync(u, 64);
             if (pending) {
                 if (!copied) start_copy();
                 cp_async_commit_wait_all();
@@ -725,7 +747,7 @@ __global__ void __launch_bounds__(64 * K, 1) k_pair_fp32_sym(SymArgs32<P> a)
                     __stcg(reinterpret_cast<double2 *>(out + q * a.ld), v);
                 }
             }
-            row_sync(u);
+            row_sync(u, 64);
             if (pending && tu == 0)
                 st_release(&sc.count[(j_slot(sc, ch, 0) - sc.C) * sc.nB + pend_J[u]], (unsigned)fs.next);
             pending = false;
@@ -803,7 +825,7 @@ __global__ void __launch_bounds__(64 * K, 1) k_pair_fp32_sym(SymArgs32<P> a)
                             }
                     }
                 }
-                if (!diag) row_sync(u);
+                if (!diag) row_sync(u, 64);
             }
             if (active) {
 #pragma unroll
@@ -830,7 +852,7 @@ __global__ void __launch_bounds__(64 * K, 1) k_pair_fp32_sym(SymArgs32<P> a)
                         pend_J[u] = J;
                     }
                 }
-                row_sync(u);
+                row_sync(u, 64);
                 if (active) {
                     copied = fs.ready;
                     if (copied) start_copy();
@@ -884,7 +906,7 @@ SymPlan plan_sym_slots(int64_t ld, int slots, bool fp32, int kmax)
     pl.D = pl.nB / 2;
     const int nb = pl.D + 1;                        // blocks of the longest row
     double best = 1e300;
-    const int Ks[2] = {fp32 ? kmax : 1, 4};
+    const int Ks[2] = {kmax, 4};
     for (int ki = 0; ki < (fp32 && kmax != 4 ? 2 : 1); ++ki) {
         const int K = Ks[ki];
         const int64_t groups = (pl.nB + K - 1) / K;
@@ -907,7 +929,7 @@ SymPlan plan_sym_slots(int64_t ld, int slots, bool fp32, int kmax)
         }
     }
     pl.grid = (int)(pl.cyclic ? pl.items : std::min(pl.items, slots));
-    pl.G = fp32 ? 1 : std::min(kSymChains64, std::max(pl.Bc - 1, 1));
+    pl.G = 1;
     pl.slots = pl.C * (1 + pl.G);
     pl.sync_words = 1 + pl.C * pl.G * pl.nB;
     return pl;
@@ -946,8 +968,8 @@ SymPlan plan_sym(int P, int64_t ld, int device, bool fp32)
                            : P == 2 ? (const void *)k_pair_fp64_sym<2, false>
                            : P == 3 ? (const void *)k_pair_fp64_sym<3, false>
                            : P == 4 ? (const void *)k_pair_fp64_sym<4, false> : (const void *)k_pair_fp64_sym<5, false>;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kSymR, 0);
-            kmax = 1;
+            kmax = P <= 3 ? sym64_rows<3>() : sym64_rows<5>();
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kSymR * kmax, 0);
         }
         slots = std::max(n_sm, 1) * std::max(occ, 1);
         if (cached) {
@@ -992,7 +1014,7 @@ int launch_pair_sym(int P, const SymPlan &pl, const SymSync &sy, const double *j
 // CTAs are all resident form no cycle).
 int sym_schedule_check(int64_t ld, int slots, bool fp32, int *info)
 {
-    const SymPlan pl = plan_sym_slots(ld, slots, fp32, fp32 ? 6 : 1);
+    const SymPlan pl = plan_sym_slots(ld, slots, fp32, fp32 ? 6 : sym64_rows<3>());
     if (pl.nB == 0) return MH_EINVAL;
     SymSched sc{pl.nB, pl.D, pl.C, pl.Bc, pl.G, pl.K, pl.cyclic ? 1 : 0, pl.items, nullptr, nullptr, nullptr, 0, 0};
     const bool even = (pl.nB & 1) == 0;

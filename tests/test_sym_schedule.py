@@ -34,14 +34,14 @@ def test_ordered_accumulation_schedule(N, slots, precision):
 
 
 def test_slot_memory_is_linear():
-    """The partial sums take C (1 + G) slots, C row chunks and G chains: O(N C),
-    not O(N^2) (the earlier design kept one slot per block distance, Np/256)."""
+    """The partial sums take C (1 + G) slots, C row chunks and G chains (one):
+    O(N C), not O(N^2) (one slot per block distance would be Np/256)."""
     for N in (65537, 262144):
         for slots, precision in ((152 * 3, 0), (152, 1)):
             plan = mh.sym_schedule_check(N, slots, precision)
-            assert plan["chains"] == (1 if precision else min(4, plan["distances_per_chunk"] - 1))
-            assert plan["rows_per_item"] == (6 if precision else 1)
-            assert plan["chunks"] * (1 + plan["chains"]) <= 40
+            assert plan["chains"] == 1
+            assert plan["rows_per_item"] == (6 if precision else 3)
+            assert 2 * plan["chunks"] <= 40
 
 
 def test_schedule_check_rejects_bad_arguments():
