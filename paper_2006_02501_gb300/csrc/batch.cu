@@ -3,7 +3,9 @@
 //
 // Mapping: one warp integrates one system at a time, for all requested steps,
 // without any synchronisation beyond the warp.  Lane l owns bodies l and l+32
-// (x, v and a^(0..2p-1) in registers); the evaluation inputs of the whole
+// (x, v and a^(0..2p-1) in registers); the evaluation spreads each body's
+// sources over a group of lanes where the system leaves lanes idle
+// (eval_group); the evaluation inputs of the whole
 // system (x, v, a, a-dot and G m of every body) sit in two shared-memory
 // buffers that alternate between the passes of P(EC)^n, so a lane can write
 // its corrected bodies while others still read the previous ones.  Warps take
@@ -81,6 +83,54 @@ __device__ __forceinline__ void eval_body(const double *in, const double *gm, in
         const double sinv = rinv * rinv;
         pair_derivs<P, double>(r, mj * (rinv * sinv), sinv, acc);
     }
+}
+
+// a^(0..P) of bodies base .. base + m - 1 (m <= 32) of a system of n bodies by
+// the whole warp: each body gets a group of g lanes (g the largest power of two
+// with g m <= 32), lane l works on body base + l / g over the sources j = l % g,
+// l % g + g, ..., the group's sums meet in a fixed xor tree, and lane l returns
+// the sums of body base + l (its own body; lanes l >= m get garbage).  Every
+// body's sum is taken in an order fixed by n alone, so results do not depend on
+// the warp.  Systems that leave lanes idle (n < 32, or the second half of one of
+// 33 .. 64 bodies) spread their pairs over the idle lanes.
+template <int P>
+__device__ __forceinline__ void eval_group(const double *in, const double *gm, int n, int base, int m, int lane,
+                                           double eps2, double (&out)[P + 1][3])
+{
+    int g = 1;
+    while (2 * g * m <= 32) g *= 2;
+    const int k0 = lane / g, sub = lane % g;
+    const int i = base + (k0 < m ? k0 : 0);
+    double ri[P + 1][3], acc[P + 1][3];
+#pragma unroll
+    for (int k = 0; k <= P; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ri[k][c] = in[(3 * k + c) * kBatchMax + i];
+            acc[k][c] = 0.0;
+        }
+    for (int j = sub; j < n; j += g) {
+        double r[P + 1][3];
+#pragma unroll
+        for (int k = 0; k <= P; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) r[k][c] = in[(3 * k + c) * kBatchMax + j] - ri[k][c];
+        const bool self = j == i;
+        double s = fma(r[0][0], r[0][0], fma(r[0][1], r[0][1], fma(r[0][2], r[0][2], eps2)));
+        s = self ? 1.0 : s;
+        const double mj = self ? 0.0 : gm[j];
+        const double rinv = rsqrt_fp64(s);
+        const double sinv = rinv * rinv;
+        pair_derivs<P, double>(r, mj * (rinv * sinv), sinv, acc);
+    }
+#pragma unroll
+    for (int k = 0; k <= P; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double v = acc[k][c];
+            for (int o = 1; o < g; o *= 2) v += __shfl_xor_sync(0xffffffffu, v, o);
+            out[k][c] = __shfl_sync(0xffffffffu, v, (lane * g) & 31);
+        }
 }
 
 // One initialisation pass: a^(have .. min(have+1, 2p-1)) from x, v, a^(0..have-1).
@@ -185,9 +235,10 @@ __global__ void __launch_bounds__(256) k_batch(BatchArgs a)
 #pragma unroll
                 for (int b = 0; b < 2; ++b) {
                     const int i = lane + 32 * b;
-                    if (i >= n) continue;
+                    if (32 * b >= n) continue;           // the whole warp: n is the system's
                     double acc[p + 1][3];
-                    eval_body<p>(cur, gm, n, i, a.eps2, acc);
+                    eval_group<p>(cur, gm, n, 32 * b, min(n - 32 * b, 32), lane, a.eps2, acc);
+                    if (i >= n) continue;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         double dk[K], d1[p + 1], xn, vn;
