@@ -101,10 +101,11 @@ typedef struct {
                            which halves the FP64 work; 0 evaluates every ordered pair;
                            1 (default) chooses 2 from N padded to 256 >= 2048 bodies up
                            (below, the ordered kernel spreads the pairs over more SMs).
-                           The symmetric kernel needs (C + Np/256) partial-sum slots of
-                           (P+1)*3*Np doubles (C ~ 10; Np = N padded to 256), about
-                           1.7 GB at N = 65536 and order 8; above 8 GiB, or with block
-                           steps, the ordered kernel runs. */
+                           The symmetric kernel adds its sums into C (1 + G) partial-sum
+                           slots of (P+1)*3*Np doubles (C row chunks, G = 1 accumulation
+                           chain; Np = N padded to 256), 14 slots (88 MB) at N = 65536
+                           and order 8, in an order fixed per slot, so its results are
+                           bit-reproducible; block steps use the ordered kernel. */
     int fp32_variant;   /* precision form, ordered-pair evaluation kernel: 0 (default) =
                            chosen per size class by timing each once (autotuner), or
                            fixed: 1 = one i-body per thread, 2 = two, 3 = two in packed
@@ -267,7 +268,10 @@ typedef struct mh_dd mh_dd;
 /* Create a double-double simulation of N bodies (1 <= N <= 2^24) of order 4, 6,
  * 8, 10 or 12.  m: N masses; x2, v2: N x 3 x 2 positions and velocities (a
  * plain double state has lo = 0); eps >= 0; cfg: NULL for defaults, only
- * beta_mode and G are read; stream as for mh_create.  Computes a^(0..2p-1) at
+ * beta_mode, G and symmetric are read (symmetric: 1, the default, evaluates each
+ * unordered pair once from 2048 bodies up, as mh_dd_pair_eval; 2 always, 0
+ * never; the symmetric kernel's partial sums take N (N/64) 2p 48 bytes, at most
+ * 4 GiB, else the ordered kernel runs); stream as for mh_create.  Computes a^(0..2p-1) at
  * t = 0 by explicit pair derivatives in double-double (Section 3 intro).  On
  * error *out is NULL. */
 int mh_dd_create(mh_dd **out, int64_t N, int order, const double *m, const double *x2,
@@ -301,6 +305,31 @@ int mh_dd_diagnostics(mh_dd *sim, double *energy2, double *ecc2, int central);
 
 /* Size, order and counters of a double-double simulation (outputs may be NULL). */
 int mh_dd_info(mh_dd *sim, int64_t *N, int *order, mh_counters *counters);
+
+/* One double-double evaluation (Section 3 intro pair derivatives, every
+ * operation in double-double): a^(0..P) of bodies i0 .. i1-1 summed over all N
+ * bodies (j != i), the sums the steps of mh_dd_step use.  P: 1 .. 5.  m: N
+ * masses (host); tr2: N x (P+1) x 3 x 2 host doubles, the (hi, lo) trajectory
+ * records x, v, a, a-dot, ... of each body; out2: (i1-i0) x (P+1) x 3 x 2 host
+ * doubles.  symmetric: 0 ordered pairs (k_dd_pair); 2 each unordered pair once
+ * (k_dd_pair_sym, both bodies from one evaluation; needs N (N/64) (P+1) 48 bytes
+ * of slots within 4 GiB, else the ordered kernel runs); 1 the choice
+ * mh_dd_create makes (the symmetric kernel from 2048 bodies up).  Allocates and
+ * frees its own device memory and stream; waits.  Returns MH_EINVAL for bad
+ * arguments, MH_ENOMEM if the device memory cannot be had. */
+int mh_dd_pair_eval(int P, int64_t N, const double *m, const double *tr2, double eps, double G, int64_t i0,
+                    int64_t i1, int symmetric, double *out2);
+
+/* Host-side check of the symmetric double-double kernel's work map for N
+ * bodies (no device needed): every unordered pair of 64-body blocks (and
+ * every block with itself) is one item, and each of the nB partial-sum slots
+ * receives every block exactly once; inside an item the kernel's rings take
+ * every body pair of two blocks once, and every unordered pair of a block with
+ * itself once.  info (5 ints): blocks nB, items, block pairs not covered
+ * exactly once, (slot, block) entries not written exactly once, body pairs
+ * inside an item not taken exactly once (or subtiles shared by two warps in a
+ * phase).  MH_EINVAL (message via mh_last_error) if a count is non-zero. */
+int mh_dd_sym_check(int64_t N, int *info);
 
 /* Batched double-double form: S independent systems of 1 to 64 bodies each,
  * advanced together with shared steps of each system's own dt, one CTA per

@@ -368,18 +368,20 @@ class DDSimulation:
     Discussion).  Shared constant steps, orders 4 to 12.
 
     x, v: (N, 3) doubles or (N, 3, 2) (hi, lo) pairs.  Results come back as
-    (..., 2) pairs; value = hi + lo.
+    (..., 2) pairs; value = hi + lo.  symmetric: each unordered pair evaluated
+    once for both bodies (k_dd_pair_sym), 1 = from 2048 bodies up (default),
+    2 = always, 0 = never.
     """
 
     def __init__(self, order: int, m, x, v, eps: float, beta: int = MH_BETA_MODIFIED, G: float = 1.0,
-                 stream=None):
+                 stream=None, symmetric: int = 1):
         L = _capi.lib()
         m = _host(m)
         N = m.shape[0]
         x2, v2 = _dd_host(x, N), _dd_host(v, N)
         cfg = _capi.Config()
         L.mh_config_default(ctypes.byref(cfg))
-        cfg.order, cfg.beta_mode, cfg.G = order, beta, G
+        cfg.order, cfg.beta_mode, cfg.G, cfg.symmetric = order, beta, G, int(symmetric)
         h = ctypes.c_void_p()
         check(L.mh_dd_create(ctypes.byref(h), N, order, _ptr(m), _ptr(x2), _ptr(v2), float(eps),
                              ctypes.byref(cfg), _stream_handle(stream)))
@@ -503,6 +505,33 @@ def measure_peaks() -> dict:
     out = (ctypes.c_double * 4)()
     check(_capi.lib().mh_measure_peaks(out))
     return {"fp64_tflops": out[0], "fp32_tflops": out[1], "fp32x2_tflops": out[2], "rsqrt_tera_per_s": out[3]}
+
+
+def dd_pair_eval(P: int, m, tr2, eps: float, G: float = 1.0, i0: int = 0, i1: int | None = None,
+                 symmetric: int = 1) -> np.ndarray:
+    """a^(0..P) of bodies i0 .. i1-1 in double-double (mh_dd_pair_eval): tr2 is
+    (N, P+1, 3, 2) (hi, lo) trajectory records x, v, a, ...; returns
+    (i1-i0, P+1, 3, 2).  symmetric as in DDSimulation."""
+    m = _host(m)
+    N = m.shape[0]
+    tr2 = np.ascontiguousarray(tr2, dtype=np.float64)
+    if tr2.shape != (N, P + 1, 3, 2):
+        raise ValueError(f"tr2 must be ({N}, {P + 1}, 3, 2)")
+    i1 = N if i1 is None else int(i1)
+    out = np.zeros((max(i1 - int(i0), 0), P + 1, 3, 2))
+    check(_capi.lib().mh_dd_pair_eval(int(P), N, _ptr(m), _ptr(tr2), float(eps), float(G), int(i0), i1,
+                                      int(symmetric), _ptr(out)))
+    return out
+
+
+def dd_sym_check(N: int) -> dict:
+    """Host-side check of the symmetric double-double kernel's work map for N
+    bodies (mh_dd_sym_check; no device needed).  Raises MHError when a block
+    pair or a (slot, block) entry is not covered exactly once."""
+    info = (ctypes.c_int * 5)()
+    check(_capi.lib().mh_dd_sym_check(int(N), info))
+    return {"blocks": info[0], "items": info[1], "bad_pairs": info[2], "bad_slots": info[3],
+            "bad_body_pairs": info[4]}
 
 
 def sym_schedule_check(N: int, slots: int, precision: int = MH_PREC_FP64) -> dict:

@@ -34,7 +34,7 @@ EXPORTS = [
     "mh_mlp_destroy", "mh_mlp_num_params", "mh_mlp_get_params", "mh_mlp_set_params", "mh_mlp_forward",
     "mh_mlp_loss_grad", "mh_mlp_train", "mh_predict", "mh_step_timesym", "mh_measure_peaks",
     "mh_dd_create", "mh_dd_destroy", "mh_dd_step", "mh_dd_sync", "mh_dd_set_state", "mh_dd_diagnostics",
-    "mh_dd_info", "mh_dd_create_batch", "mh_dd_step_batch", "mh_dd_batch_energy", "mh_restore",
+    "mh_dd_info", "mh_dd_pair_eval", "mh_dd_sym_check", "mh_dd_create_batch", "mh_dd_step_batch", "mh_dd_batch_energy", "mh_restore",
     "mh_sym_schedule_check",
 ]
 
@@ -133,6 +133,8 @@ def lib() -> ctypes.CDLL:
             L.mh_dd_set_state.argtypes = [P, DP, DP, DP, DP]
             L.mh_dd_diagnostics.argtypes = [P, DP, DP, I]
             L.mh_dd_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(Counters)]
+            L.mh_dd_pair_eval.argtypes = [I, I64, DP, DP, D, D, I64, I64, I, DP]
+            L.mh_dd_sym_check.argtypes = [I64, IP]
             L.mh_dd_create_batch.argtypes = [ctypes.POINTER(P), I64, I64P, DP, DP, DP, DP, D, I,
                                              ctypes.POINTER(Config), P]
             L.mh_dd_step_batch.argtypes = [P, I64, I]

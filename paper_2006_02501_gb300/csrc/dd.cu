@@ -303,6 +303,170 @@ k_dd_pair_sys(const double2 *__restrict__ tr, const double *__restrict__ m, cons
     dd_store_sums<P, kTop2>(part + (size_t)(b0 + t) * R, acc);
 }
 
+// ---- pair-symmetric evaluation ----
+//
+// Each scaled pair term B_k (pair_math.cuh) is odd under i <-> j and the factor
+// S = s^-3/2 is even, so one evaluation of a pair gives both bodies' terms:
+// body i gets m_j (G S B_k) and body j gets -m_i (G S B_k).  Bodies form blocks
+// of kDDSymB = 32 W (W warps; nB blocks, the last one ragged).  An item is one
+// block pair (I, J = I + b mod nB): b = 1 .. Dfull for every row I (Dfull =
+// (nB - 1) / 2), and, when nB is even, the half distance b = nB / 2 for the
+// rows I < nB / 2 only, so that every unordered block pair is one item; b = 0
+// is the block with itself.  The CTA keeps block J's records and running
+// j-side sums in shared memory (row-major by record element, so the 32 lanes
+// of a ring step hit distinct banks); thread t owns body I kDDSymB + t.  Warp
+// w runs 32-step rings over j-subtile q = (w + phase) mod W, lane l pairing
+// with j = 32 q + (l + s) mod 32: within a phase no two warps share a subtile
+// and no two lanes a j, so the j-side sums are read, added to and written back
+// without atomics, in an order fixed by (phase, step).  A diagonal item takes
+// every unordered pair once by the same rings: within the own subtile the ring
+// distances 1 .. 16 (16 on lanes 0 .. 15 only), and subtile pairs (w, w + ph)
+// for ph < W/2, plus ph = W/2 for w < W/2.  A ring whose lanes are all past N
+// (the ragged last block) is skipped.
+//
+// Output: item (I, b) writes its i-side sums to slot b and its j-side sums to
+// slot Dmax + b (Dmax = nB / 2), except the half distance, whose j-side bodies
+// (blocks >= nB / 2) take slot b, the one their own i-side leaves empty; a
+// diagonal item adds its j-side sums to its i-side ones (in that order) into
+// slot 0.  Every body of every slot 0 .. nB - 1 is then written exactly once,
+// and the consumer adds the slots in slot order: deterministic results.
+// The sums use the sloppy double-word addition (dd.cuh: error ~u^2 of the
+// summed magnitudes, the same order as the terms' own rounding) and raw
+// products by the masses: ~950 FP64 operations per pair interaction at P = 3,
+// against ~1800 for k_dd_pair.  Two warps per block: items of 64 x 64 pairs
+// are small enough that 152 SMs finish together (with 128-body blocks, 3.5
+// items per SM at 4096 bodies left SMs idle for the last item).  Slots take
+// nB N (P + 1) 3 double-words (75 MB at N = 4096, P = 3); the planner keeps
+// them within kDDSymMaxBytes.
+constexpr int kDDSymW = 2;
+constexpr int kDDSymB = 32 * kDDSymW;
+
+struct DDSymItem {
+    int I, b;
+};
+
+__host__ __device__ __forceinline__ DDSymItem dd_sym_item(int t, int nB)
+{
+    const int Dfull = (nB - 1) / 2;
+    DDSymItem it;
+    if (t < nB * Dfull) {                       // full distances, largest work first
+        it.b = 1 + t / nB;
+        it.I = t - (it.b - 1) * nB;
+    } else if ((nB & 1) == 0 && t < nB * Dfull + nB / 2) {   // half distance, rows < nB / 2
+        it.b = nB / 2;
+        it.I = t - nB * Dfull;
+    } else {                                    // diagonal blocks (half the pairs) last
+        it.b = 0;
+        it.I = t - nB * Dfull - ((nB & 1) ? 0 : nB / 2);
+    }
+    return it;
+}
+
+__host__ __device__ __forceinline__ int dd_sym_items(int nB) { return nB * ((nB - 1) / 2) + ((nB & 1) ? 0 : nB / 2) + nB; }
+
+// Ring steps [s0, s1) of warp w in phase ph (over subtile (w + ph) mod W), and
+// whether the pair of a lane at step s counts: all 32 steps off the diagonal;
+// on it, the rules above.
+__host__ __device__ __forceinline__ void dd_sym_steps(bool diag, int ph, int w, int &s0, int &s1)
+{
+    s0 = 0;
+    s1 = 32;
+    if (diag) {
+        if (ph == 0) { s0 = 1; s1 = 17; }
+        else if (!(2 * ph < kDDSymW || (2 * ph == kDDSymW && w < kDDSymW / 2))) s1 = 0;
+    }
+}
+
+__host__ __device__ __forceinline__ bool dd_sym_take(bool diag, int ph, int s, int lane)
+{
+    return !(diag && ph == 0 && s == 16 && lane >= 16);
+}
+
+template <int P>
+__host__ __device__ constexpr size_t dd_sym_smem() { return (size_t)kDDSymB * (2 * (P + 1) * 3 * sizeof(double2) + sizeof(double)); }
+
+template <int P>
+__global__ void __launch_bounds__(kDDSymB, 8 / kDDSymW)
+k_dd_pair_sym(const double2 *__restrict__ tr, const double *__restrict__ m, int N, int nB, double eps, double G,
+              double2 *__restrict__ part)
+{
+    constexpr int R = (P + 1) * 3;
+    extern __shared__ double2 dd_sym_sh[];
+    double2 *sj = dd_sym_sh;                        // [R][kDDSymB] records of block J
+    double2 *ja = sj + R * kDDSymB;                 // [R][kDDSymB] j-side sums
+    double *sm = (double *)(ja + R * kDDSymB);      // [kDDSymB] masses of block J (0 past N)
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const DDSymItem it = dd_sym_item(blockIdx.x, nB);
+    const bool diag = it.b == 0;
+    const int J = diag ? it.I : (it.I + it.b) % nB;
+    const int i = it.I * kDDSymB + t, j0 = J * kDDSymB;
+    for (int q = t; q < R * kDDSymB; q += kDDSymB) {
+        const int jj = q / R, e = q - jj * R;       // coalesced over the AoS rows of the block
+        const int j = j0 + jj;
+        sj[e * kDDSymB + jj] = j < N ? tr[(size_t)j * R + e] : make_double2(0.0, 0.0);
+        ja[e * kDDSymB + jj] = make_double2(0.0, 0.0);
+    }
+    sm[t] = j0 + t < N ? m[j0 + t] : 0.0;
+    const bool ilive = i < N;
+    const double mi = ilive ? m[i] : 0.0;
+    dd ri[P + 1][3], acc[P + 1][3];
+#pragma unroll
+    for (int k = 0; k <= P; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ri[k][c] = ilive ? ld2(&tr[(size_t)i * R + k * 3 + c]) : dd(0.0);
+            acc[k][c] = dd(0.0);
+        }
+    const dd eps2 = two_prod(eps, eps);
+    __syncthreads();
+    for (int ph = 0; ph < kDDSymW; ++ph) {
+        const int q = (w + ph) % kDDSymW;
+        int s0, s1;
+        dd_sym_steps(diag, ph, w, s0, s1);
+        if (it.I * kDDSymB + 32 * w >= N || j0 + 32 * q >= N) s1 = s0;   // every lane past N
+        for (int s = s0; s < s1; ++s) {
+            const int jj = q * 32 + ((lane + s) & 31);
+            const bool live = ilive && j0 + jj < N && dd_sym_take(diag, ph, s, lane);
+            dd r[P + 1][3];
+#pragma unroll
+            for (int k = 0; k <= P; ++k)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) r[k][c] = ld2(&sj[(k * 3 + c) * kDDSymB + jj]) - ri[k][c];
+            dd s2 = eps2 + (r[0][0] * r[0][0] + r[0][1] * r[0][1] + r[0][2] * r[0][2]);
+            s2 = live ? s2 : dd(1.0);
+            const double mj = live ? sm[jj] : 0.0, mi_live = live ? mi : 0.0;
+            const dd y = rsqrt_dd(s2);
+            const dd sinv = y * y;
+            const dd GS = mul_d(sinv * y, G);
+            pair_odd_terms<P, dd>(r, sinv, [&](int k, int c, dd B) {
+                const dd sb = GS * B;
+                acc[k][c] = add_sloppy(acc[k][c], mul_d_raw(sb, mj));
+                double2 *pj = &ja[(k * 3 + c) * kDDSymB + jj];
+                st2(pj, add_sloppy(ld2(pj), mul_d_raw(sb, -mi_live)));
+            });
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+    const int slot_i = it.b;
+    const int Dmax = nB / 2;
+    if (diag) {
+        if (ilive)
+#pragma unroll
+            for (int k = 0; k <= P; ++k)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    st2(&part[(size_t)i * R + k * 3 + c], acc[k][c] + ld2(&ja[(k * 3 + c) * kDDSymB + t]));
+        return;
+    }
+    if (ilive) dd_store_sums<P, false>(part + ((size_t)slot_i * N + i) * R, acc);
+    const int slot_j = ((nB & 1) == 0 && it.b == Dmax) ? it.b : Dmax + it.b;
+    const int j = j0 + t;
+    if (j < N)
+#pragma unroll
+        for (int e = 0; e < R; ++e) part[((size_t)slot_j * N + j) * R + e] = ja[e * kDDSymB + t];
+}
+
 // Adds the S partial-sum slots of a^(0..p) in slot order into slot 0, one
 // thread per (body, order, component), so that the corrector reads one slot.
 // (A serial sum of S slots for all p + 1 orders in every corrector thread is a
@@ -317,6 +481,17 @@ k_dd_reduce_slots(double2 *__restrict__ part, int S, int N)
     if (t >= (int64_t)N * R) return;
     dd s = ld2(&part[t]);
     for (int q = 1; q < S; ++q) s += ld2(&part[(size_t)q * N * R + t]);
+    st2(&part[t], s);
+}
+
+// The same for any record width: nt = N R elements per slot.
+__global__ void __launch_bounds__(kDDThreads)
+k_dd_add_slots(double2 *__restrict__ part, int S, int64_t nt)
+{
+    const int64_t t = (int64_t)blockIdx.x * kDDThreads + threadIdx.x;
+    if (t >= nt) return;
+    dd s = ld2(&part[t]);
+    for (int q = 1; q < S; ++q) s += ld2(&part[(size_t)q * nt + t]);
     st2(&part[t], s);
 }
 
@@ -559,18 +734,56 @@ __global__ void k_dd_ecc(const double *__restrict__ m, const double2 *__restrict
 
 // ---- launch helpers ----
 
+// An evaluation's grid: ordered pairs (iblocks x S j-chunks of jchunk bodies)
+// or, when sym, the pair-symmetric items over nB blocks (S = nB slots).
 struct DDPlan {
-    int iblocks, S, jchunk;
+    int iblocks = 0, S = 1, jchunk = 0;
+    bool sym = false;
+    int nB = 0;
 };
 
-DDPlan dd_plan(int N)
+constexpr int kDDSymMinN = 2048;                         // automatic choice: from 16 blocks up
+constexpr size_t kDDSymMaxBytes = (size_t)4 << 30;        // partial-sum slots of the symmetric kernel
+
+// Whether an evaluation of N bodies with records of R double-words uses the
+// pair-symmetric kernel (a simulation sizes its slots for the widest
+// initialisation record, R = 6p): mode 0 never, 2 whenever the slots fit, 1
+// from kDDSymMinN bodies up (below, the ordered kernel spreads the pairs over
+// more SMs).
+bool dd_use_sym(int N, int R, int mode)
+{
+    if (mode == 0) return false;
+    const size_t nB = (size_t)((N + kDDSymB - 1) / kDDSymB);
+    if (nB * (size_t)N * (size_t)R * sizeof(double2) > kDDSymMaxBytes) return false;
+    return mode == 2 || N >= kDDSymMinN;
+}
+
+DDPlan dd_plan(int N, bool sym = false)
 {
     DDPlan pl;
+    if (sym) {
+        pl.sym = true;
+        pl.nB = (N + kDDSymB - 1) / kDDSymB;
+        pl.S = pl.nB;
+        return pl;
+    }
     pl.iblocks = (N + kDDThreads - 1) / kDDThreads;
     int S = std::max(1, std::min((N + kDDMinJ - 1) / kDDMinJ, kDDTargetCtas / pl.iblocks));
     pl.jchunk = (N + S - 1) / S;
     pl.S = (N + pl.jchunk - 1) / pl.jchunk;
     return pl;
+}
+
+// Opens the dynamic shared memory of the symmetric kernels (set before any
+// launch or capture; idempotent).
+int dd_sym_attrs()
+{
+    MH_CUDA(cudaFuncSetAttribute(k_dd_pair_sym<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dd_sym_smem<1>()));
+    MH_CUDA(cudaFuncSetAttribute(k_dd_pair_sym<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dd_sym_smem<2>()));
+    MH_CUDA(cudaFuncSetAttribute(k_dd_pair_sym<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dd_sym_smem<3>()));
+    MH_CUDA(cudaFuncSetAttribute(k_dd_pair_sym<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dd_sym_smem<4>()));
+    MH_CUDA(cudaFuncSetAttribute(k_dd_pair_sym<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dd_sym_smem<5>()));
+    return MH_OK;
 }
 
 // Batched form on the device: system offsets, the system of every body, and
@@ -588,6 +801,11 @@ void launch_pair_kernel(const double2 *tr, const double *m, int N, double eps, d
 {
     if (b)
         k_dd_pair_sys<P, kTop2><<<b->S, kDDSysMax, 0, st>>>(tr, m, b->off, eps, G, part);
+    else if constexpr (!kTop2 && P <= kDDMaxP)
+        if (pl.sym)
+            k_dd_pair_sym<P><<<dd_sym_items(pl.nB), kDDSymB, dd_sym_smem<P>(), st>>>(tr, m, N, pl.nB, eps, G, part);
+        else
+            k_dd_pair<P, kTop2><<<dim3(pl.iblocks, pl.S), kDDThreads, 0, st>>>(tr, m, N, eps, G, pl.jchunk, part);
     else
         k_dd_pair<P, kTop2><<<dim3(pl.iblocks, pl.S), kDDThreads, 0, st>>>(tr, m, N, eps, G, pl.jchunk, part);
 }
@@ -612,9 +830,9 @@ int launch_dd_pair(int P, const double2 *tr, const double *m, int N, double eps,
 template <int p>
 int launch_dd_step_p(double2 *x, double2 *v, double2 *d, double2 *tr, double2 *part, const double *m, int N,
                      double eps, double G, int bm, double dt, int n_iter, int *flag, cudaStream_t st,
-                     const DDBatchDev *b)
+                     const DDBatchDev *b, bool sym)
 {
-    const DDPlan pl = dd_plan(N);
+    const DDPlan pl = dd_plan(N, sym);
     const bool reduce = !b && pl.S > 1;
     const int slots = 1;                       // the corrector reads slot 0 (pre-summed when S > 1)
     const double *dts = b ? b->dts : nullptr;
@@ -658,6 +876,7 @@ using namespace mh;
 struct mh_dd {
     int64_t N = 0;
     int p = 0, order = 0, bm = 0;
+    bool sym = false;               // single system: pair-symmetric evaluation (dd_use_sym)
     double eps = 0.0, G = 1.0;
     double t_hi = 0.0, t_lo = 0.0;
     cudaStream_t stream = nullptr;
@@ -732,12 +951,12 @@ int dd_consts_once(cudaStream_t st)
 int dd_initialise(mh_dd *s)
 {
     const int N = (int)s->N, K = 2 * s->p;
-    const DDPlan pl = dd_plan(N);
     const DDBatchDev b = s->batch();
     const DDBatchDev *bp = s->S ? &b : nullptr;
-    const int slots = s->S ? 1 : pl.S;
     for (int have = 0; have < K; have += 2) {
         const int P = have + 1;
+        const DDPlan pl = dd_plan(N, s->sym && P <= kDDMaxP);
+        const int slots = s->S ? 1 : pl.S;
         const int64_t nt = (int64_t)N * (have + 2) * 3;
         k_dd_init_tr<<<(unsigned)((nt + kDDThreads - 1) / kDDThreads), kDDThreads, 0, s->stream>>>(
             s->x, s->v, s->d, N, K, have, s->tr);
@@ -759,11 +978,11 @@ int dd_step_once(mh_dd *s, double dt, int n_iter)
     const DDBatchDev b = s->batch();
     const DDBatchDev *bp = s->S ? &b : nullptr;
     switch (s->p) {
-        case 1: return launch_dd_step_p<1>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream, bp);
-        case 2: return launch_dd_step_p<2>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream, bp);
-        case 3: return launch_dd_step_p<3>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream, bp);
-        case 4: return launch_dd_step_p<4>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream, bp);
-        case 5: return launch_dd_step_p<5>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream, bp);
+        case 1: return launch_dd_step_p<1>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream, bp, s->sym);
+        case 2: return launch_dd_step_p<2>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream, bp, s->sym);
+        case 3: return launch_dd_step_p<3>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream, bp, s->sym);
+        case 4: return launch_dd_step_p<4>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream, bp, s->sym);
+        case 5: return launch_dd_step_p<5>(s->x, s->v, s->d, s->tr, s->part, s->m, N, s->eps, s->G, s->bm, dt, n_iter, s->flag, s->stream, bp, s->sym);
         default: set_error("double-double step: unsupported order"); return MH_EINVAL;
     }
 }
@@ -797,7 +1016,7 @@ void dd_count(mh_dd *sim, int n_iter, int64_t nsteps, double pairs_per_eval)
     sim->ctr.evaluations += nsteps * n_iter;
     sim->ctr.pair_interactions += (double)nsteps * n_iter * pairs_per_eval;
     sim->ctr.particle_steps += (double)nsteps * (double)sim->N;
-    const bool reduce = !sim->S && dd_plan((int)sim->N).S > 1;
+    const bool reduce = !sim->S && dd_plan((int)sim->N, sim->sym).S > 1;
     sim->ctr.kernel_launches += nsteps * (1 + (reduce ? 3 : 2) * n_iter);
 }
 
@@ -858,8 +1077,14 @@ int dd_create(mh_dd **out, const char *fn, int64_t N, int order, const double *m
     s->G = c.G;
     s->S = S;
     const int K = 2 * s->p;
+    if (c.symmetric < 0 || c.symmetric > 2) {
+        delete s;
+        set_error(f + ": symmetric must be 0, 1 or 2");
+        return MH_EINVAL;
+    }
+    s->sym = !S && dd_use_sym((int)N, 6 * s->p, c.symmetric);
     const DDPlan pl = dd_plan((int)N);
-    const size_t slots = S ? 1 : (size_t)pl.S;
+    const size_t slots = S ? 1 : std::max((size_t)pl.S, s->sym ? (size_t)dd_plan((int)N, true).S : (size_t)0);
     const size_t R = (size_t)K * 3;      // widest trajectory record (initialisation, P + 1 <= 2p)
     const int nb = (int)((N + kDDThreads - 1) / kDDThreads);
     const size_t ndiag = std::max<size_t>((size_t)nb + 1, (size_t)S);
@@ -916,6 +1141,7 @@ int dd_create(mh_dd **out, const char *fn, int64_t N, int order, const double *m
         rc = cuda_fail(cudaGetLastError(), (f + ": memset").c_str());
     if (!rc && cudaMemsetAsync(s->d, 0, N * K * 3 * sizeof(double2), s->stream) != cudaSuccess)
         rc = cuda_fail(cudaGetLastError(), (f + ": memset").c_str());
+    if (!rc && s->sym) rc = dd_sym_attrs();
     if (!rc) rc = dd_consts_once(s->stream);
     if (!rc) rc = dd_initialise(s);
     if (!rc && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), fn);
@@ -1082,6 +1308,122 @@ int mh_dd_batch_energy(mh_dd *sim, double *energy2)
     sim->ctr.kernel_launches += 1;
     MH_CUDA(cudaMemcpyAsync(energy2, sim->diag, (size_t)sim->S * sizeof(double2), cudaMemcpyDeviceToHost, sim->stream));
     MH_CUDA(cudaStreamSynchronize(sim->stream));
+    return MH_OK;
+}
+
+int mh_dd_pair_eval(int P, int64_t N, const double *m, const double *tr2, double eps, double G, int64_t i0,
+                    int64_t i1, int symmetric, double *out2)
+{
+    const std::string f = "mh_dd_pair_eval";
+    if (P < 1 || P > kDDMaxP) { set_error(f + ": P must be 1 .. 5"); return MH_EINVAL; }
+    if (N < 1 || N > (int64_t)1 << 24) { set_error(f + ": N must be 1 .. 2^24"); return MH_EINVAL; }
+    if (i0 < 0 || i1 > N || i0 > i1) { set_error(f + ": need 0 <= i0 <= i1 <= N"); return MH_EINVAL; }
+    if (symmetric < 0 || symmetric > 2) { set_error(f + ": symmetric must be 0, 1 or 2"); return MH_EINVAL; }
+    if (!m || !tr2 || (i1 > i0 && !out2)) { set_error(f + ": m, tr2 and out2 are required"); return MH_EINVAL; }
+    if (!(eps >= 0.0) || !std::isfinite(eps) || !std::isfinite(G)) { set_error(f + ": eps, G must be finite, eps >= 0"); return MH_EINVAL; }
+    if (i1 == i0) return MH_OK;
+    const int n = (int)N, R = (P + 1) * 3;
+    const bool sym = dd_use_sym(n, R, symmetric);
+    const DDPlan pl = dd_plan(n, sym);
+    double *dm = nullptr;
+    double2 *dtr = nullptr, *dpart = nullptr;
+    cudaStream_t st = nullptr;
+    int rc = MH_OK;
+    auto done = [&](int r) {
+        if (st) cudaStreamDestroy(st);
+        cudaFree(dm); cudaFree(dtr); cudaFree(dpart);
+        return r;
+    };
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        st = nullptr;
+        return done(cuda_fail(cudaGetLastError(), "cudaStreamCreate"));
+    }
+    if (cudaMalloc((void **)&dm, N * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void **)&dtr, N * R * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc((void **)&dpart, (size_t)pl.S * N * R * sizeof(double2)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error(f + ": device allocation failed");
+        return done(MH_ENOMEM);
+    }
+    if (sym && (rc = dd_sym_attrs())) return done(rc);
+    if ((rc = dd_consts_once(st))) return done(rc);
+    if (cudaMemcpyAsync(dm, m, N * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(dtr, tr2, N * R * sizeof(double2), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return done(cuda_fail(cudaGetLastError(), "mh_dd_pair_eval: upload"));
+    if ((rc = launch_dd_pair(P, dtr, dm, n, eps, G, pl, dpart, st, nullptr))) return done(rc);
+    if (pl.S > 1) {
+        const int64_t nt = N * R;
+        k_dd_add_slots<<<(unsigned)((nt + kDDThreads - 1) / kDDThreads), kDDThreads, 0, st>>>(dpart, pl.S, nt);
+        MH_LAUNCHED("k_dd_add_slots");
+    }
+    if (cudaMemcpyAsync(out2, dpart + (size_t)i0 * R, (size_t)(i1 - i0) * R * sizeof(double2),
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return done(cuda_fail(cudaGetLastError(), "mh_dd_pair_eval"));
+    return done(MH_OK);
+}
+
+int mh_dd_sym_check(int64_t N, int *info)
+{
+    if (N < 1 || N > (int64_t)1 << 24 || !info) { set_error("mh_dd_sym_check: need 1 <= N <= 2^24 and info"); return MH_EINVAL; }
+    const int n = (int)N, nB = (n + kDDSymB - 1) / kDDSymB, items = dd_sym_items(nB), Dmax = nB / 2;
+    std::vector<int> pairs((size_t)nB * nB, 0), slots((size_t)nB * nB, 0);   // [I][J], [slot][block]
+    for (int t = 0; t < items; ++t) {
+        const DDSymItem it = dd_sym_item(t, nB);
+        if (it.I < 0 || it.I >= nB || it.b < 0 || it.b > Dmax) { info[2] = t; set_error("mh_dd_sym_check: item out of range"); return MH_EINVAL; }
+        const int J = (it.I + it.b) % nB;
+        pairs[(size_t)std::min(it.I, J) * nB + std::max(it.I, J)] += 1;
+        slots[(size_t)it.b * nB + it.I] += 1;                         // i-side (diagonal: both sides)
+        if (it.b > 0) {
+            const int sj = ((nB & 1) == 0 && it.b == Dmax) ? it.b : Dmax + it.b;
+            if (sj >= nB) { info[2] = t; set_error("mh_dd_sym_check: j-side slot out of range"); return MH_EINVAL; }
+            slots[(size_t)sj * nB + J] += 1;
+        }
+    }
+    int bad_pairs = 0, bad_slots = 0;
+    for (int I = 0; I < nB; ++I)
+        for (int J = I; J < nB; ++J) bad_pairs += pairs[(size_t)I * nB + J] != 1;
+    for (size_t q = 0; q < slots.size(); ++q) bad_slots += slots[q] != 1;
+    // Inside an item: the kernel's rings (dd_sym_steps, dd_sym_take) take every
+    // body pair of two blocks once, and every unordered pair of a block with
+    // itself once (no body with itself); no two warps share a subtile in a phase.
+    int bad_body_pairs = 0;
+    for (int diag = 0; diag < 2; ++diag) {
+        std::vector<int> cnt((size_t)kDDSymB * kDDSymB, 0);
+        for (int ph = 0; ph < kDDSymW; ++ph) {
+            int owner[kDDSymW];
+            for (int q = 0; q < kDDSymW; ++q) owner[q] = -1;
+            for (int w = 0; w < kDDSymW; ++w) {
+                int s0, s1;
+                dd_sym_steps(diag != 0, ph, w, s0, s1);
+                const int q = (w + ph) % kDDSymW;
+                if (s1 > s0) {
+                    if (owner[q] >= 0) ++bad_body_pairs;
+                    owner[q] = w;
+                }
+                for (int st = s0; st < s1; ++st)
+                    for (int lane = 0; lane < 32; ++lane)
+                        if (dd_sym_take(diag != 0, ph, st, lane))
+                            ++cnt[(size_t)(32 * w + lane) * kDDSymB + 32 * q + ((lane + st) & 31)];
+            }
+        }
+        for (int a = 0; a < kDDSymB; ++a)
+            for (int b = 0; b < kDDSymB; ++b) {
+                const int c = cnt[(size_t)a * kDDSymB + b];
+                if (!diag) bad_body_pairs += c != 1;
+                else if (a == b) bad_body_pairs += c != 0;
+                else if (a < b) bad_body_pairs += c + cnt[(size_t)b * kDDSymB + a] != 1;
+            }
+    }
+    info[0] = nB;
+    info[1] = items;
+    info[2] = bad_pairs;
+    info[3] = bad_slots;
+    info[4] = bad_body_pairs;
+    if (bad_pairs || bad_slots || bad_body_pairs) {
+        set_error("mh_dd_sym_check: block pairs, body pairs or slots not covered exactly once");
+        return MH_EINVAL;
+    }
     return MH_OK;
 }
 

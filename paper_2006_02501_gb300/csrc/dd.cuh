@@ -82,6 +82,27 @@ __device__ __forceinline__ dd mul_d(dd x, double y)
     return fast_two_sum(c.hi, __fma_rn(x.lo, y, c.lo));
 }
 
+// double-word x double without the closing renormalisation: hi = RN(x.hi y)
+// and lo = its exact error plus x.lo y, |lo| up to ~ulp(hi).  For a product that
+// goes straight into a double-word sum, which renormalises its result anyway.
+__device__ __forceinline__ dd mul_d_raw(dd x, double y)
+{
+    const double p = __dmul_rn(x.hi, y);
+    return dd(p, __fma_rn(x.lo, y, __fma_rn(x.hi, y, -p)));
+}
+
+// The sloppy sum of two double-words (Dekker 1971; Joldes, Muller and Popescu
+// 2017, the SloppyDWPlusDW algorithm): one two_sum of the high words, the low
+// words added in double.  Its error is at most ~2u^2 (|x| + |y|) (no relative
+// bound when x and y cancel), the same order as the rounding the summed
+// terms already carry, so it serves long sums of pair terms; 11 FP64
+// operations against 20 for the accurate sum.
+__device__ __forceinline__ dd add_sloppy(dd x, dd y)
+{
+    const dd s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, __dadd_rn(s.lo, __dadd_rn(x.lo, y.lo)));
+}
+
 __device__ __forceinline__ dd &operator+=(dd &x, dd y) { return x = x + y; }
 __device__ __forceinline__ dd &operator-=(dd &x, dd y) { return x = x - y; }
 

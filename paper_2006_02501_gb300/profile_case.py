@@ -9,7 +9,8 @@ wants the first step's evaluation skips those.  FP64 evaluations use the
 pair-symmetric kernel (k_pair_fp64_sym) for P <= 3 unless --ordered is given;
 the 8th-order initialisation's last pass (P = 5) always runs k_pair_fp64.
 --precision dd runs the double-double form (mh_dd_*) on the same disc; its
-initialisation also launches one evaluation (k_dd_pair) per pass.
+initialisation also launches one evaluation per pass (k_dd_pair_sym from 2048
+bodies up, k_dd_pair with --ordered or below).
 --precision all runs one step of every form on the same small disc (for a
 memory checker): FP64 with the pair-symmetric and the ordered kernel, the
 FP32-pair form with both (orders up to 8), the double-double form, and a
@@ -71,7 +72,7 @@ def main():
             print(f"ok dd batch systems {np.diff(off).tolist()} finite={bool(np.isfinite(b.sync()[1]).all())}")
         return
     if a.precision == "dd":
-        with mh.DDSimulation(a.order, m, x, v, 1e-4) as sim:
+        with mh.DDSimulation(a.order, m, x, v, 1e-4, symmetric=0 if a.ordered else 1) as sim:
             sim.step(2 * np.pi * 1e-3, a.n_iter, nsteps=a.steps)
             t2, x2, v2, d2 = sim.sync()
         print(f"ok N={len(m)} dd order {a.order} steps {a.steps} t={t2[0]:.6f} "

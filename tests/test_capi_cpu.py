@@ -142,6 +142,22 @@ def test_double_double_and_restore_arguments_rejected_before_device_use(L):
     dt = np.array([0.01, 0.0])                   # a zero step
     assert L.mh_dd_create_batch(ctypes.byref(h), 2, off.ctypes.data_as(i64), ptr(m), ptr(x2), ptr(v2), ptr(dt),
                                 0.0, 8, None, None) == _capi.MH_EINVAL
+    cfg = _capi.Config()
+    L.mh_config_default(ctypes.byref(cfg))
+    cfg.symmetric = 3
+    assert L.mh_dd_create(ctypes.byref(h), 3, 8, ptr(m), ptr(x2), ptr(v2), 0.0, ctypes.byref(cfg),
+                          None) == _capi.MH_EINVAL
+    # the direct double-double evaluation checks its arguments first
+    tr2 = np.zeros((3, 4, 3, 2))
+    out = np.zeros((3, 4, 3, 2))
+    assert L.mh_dd_pair_eval(6, 3, ptr(m), ptr(tr2), 0.0, 1.0, 0, 3, 1, ptr(out)) == _capi.MH_EINVAL
+    assert L.mh_dd_pair_eval(3, 3, ptr(m), ptr(tr2), 0.0, 1.0, 0, 4, 1, ptr(out)) == _capi.MH_EINVAL
+    assert L.mh_dd_pair_eval(3, 3, ptr(m), ptr(tr2), 0.0, 1.0, 2, 1, 1, ptr(out)) == _capi.MH_EINVAL
+    assert L.mh_dd_pair_eval(3, 3, ptr(m), ptr(tr2), 0.0, 1.0, 0, 3, 3, ptr(out)) == _capi.MH_EINVAL
+    assert L.mh_dd_pair_eval(3, 3, None, ptr(tr2), 0.0, 1.0, 0, 3, 1, ptr(out)) == _capi.MH_EINVAL
+    assert L.mh_dd_pair_eval(3, 3, ptr(m), ptr(tr2), -1.0, 1.0, 0, 3, 1, ptr(out)) == _capi.MH_EINVAL
+    assert L.mh_dd_pair_eval(3, 3, ptr(m), ptr(tr2), 0.0, 1.0, 1, 1, 1, None) == _capi.MH_OK   # empty range
+    assert L.mh_dd_sym_check(0, None) == _capi.MH_EINVAL
     assert L.mh_dd_step(None, 0.01, 3, 1) == _capi.MH_EINVAL
     assert L.mh_dd_step_batch(None, 1, 3) == _capi.MH_EINVAL
     assert L.mh_dd_batch_energy(None, None) == _capi.MH_EINVAL

@@ -217,3 +217,91 @@ def test_dd_bench_size_sampled_start(mh, orc):
             diff = np.linalg.norm(dd_diff(d2[i0:i1, k], ref[:, k]), axis=-1)
             scale = np.linalg.norm(ref[:, k, :, 0], axis=-1)
             assert (diff <= 1e-26 * scale).all(), (i0, k, diff / scale)
+
+
+# ---- pair-symmetric double-double evaluation (k_dd_pair_sym) ----
+
+def _dd_traj(seed, N, P):
+    """Seeded evaluation input of N bodies: an SMBH disc's x, v with the Kepler
+    a, a-dot (helpers.kepler_traj), normal rows above a-dot, and low words of
+    up to 2^-54 of each value (so every double-word is normalised and the low
+    words take part)."""
+    from helpers import kepler_traj
+    m, x, v = I.smbh_disc(seed=seed, N=N - 1)
+    traj = kepler_traj(m, x, v, min(P, 3))
+    rng = np.random.default_rng(seed)
+    if P > 3:
+        traj = np.concatenate([traj, rng.normal(size=(N, P - 3, 3))], axis=1)
+    lo = traj * 2.0 ** -54 * rng.uniform(-1.0, 1.0, size=traj.shape)
+    return m, np.ascontiguousarray(np.stack([traj, lo], axis=-1))
+
+
+def _rows_ok(got2, ref2, tol):
+    diff = np.linalg.norm(dd_diff(got2, ref2), axis=-1)
+    scale = np.linalg.norm(np.asarray(ref2)[..., 0], axis=-1)
+    return float((diff / scale).max()) <= tol, float((diff / scale).max())
+
+
+@pytest.mark.parametrize("N", [2100, 2500])      # 33 blocks of 64 (odd) and 40 (even), both ragged
+@pytest.mark.parametrize("P", [1, 3, 5])
+def test_dd_symmetric_eval_sampled_against_oracle(mh, orc, N, P):
+    """Each unordered pair once, both bodies from one evaluation: sampled bodies
+    (the SMBH, a block boundary, the middle, the ragged tail) against binary128
+    direct sums over all N bodies, at 1e-26 of each row as the bench-size test;
+    the ordered kernel on the same input gives the same rows."""
+    m, tr2 = _dd_traj(40 + P, N, P)
+    for i0, i1 in ((0, 3), (127, 130), (1234, 1236), (N - 5, N)):
+        ref = orc.dd_evaluate(m, tr2, 1e-4, 1.0, i0, i1)
+        got = mh.dd_pair_eval(P, m, tr2, 1e-4, 1.0, i0, i1, symmetric=2)
+        ordered = mh.dd_pair_eval(P, m, tr2, 1e-4, 1.0, i0, i1, symmetric=0)
+        for k in range(P + 1):
+            ok, e = _rows_ok(got[:, k], ref[:, k], 1e-26)
+            assert ok, (i0, k, e)
+            ok, e = _rows_ok(ordered[:, k], ref[:, k], 1e-26)
+            assert ok, (i0, k, e, "ordered")
+
+
+def test_dd_symmetric_matches_ordered_all_bodies(mh):
+    """All 4096 bodies of the bench-size disc at P = 3: the symmetric and the
+    ordered kernels agree to 1e-27 of each row (both sit ~1e-31 from the exact
+    sums), and two symmetric runs are bit-identical (the slots are added in a
+    fixed order)."""
+    m, tr2 = _dd_traj(44, 4096, 3)
+    sym = mh.dd_pair_eval(3, m, tr2, 1e-4, 1.0, symmetric=2)
+    ordered = mh.dd_pair_eval(3, m, tr2, 1e-4, 1.0, symmetric=0)
+    for k in range(4):
+        ok, e = _rows_ok(sym[:, k], ordered[:, k], 1e-27)
+        assert ok, (k, e)
+    again = mh.dd_pair_eval(3, m, tr2, 1e-4, 1.0, symmetric=2)
+    assert np.array_equal(sym, again)
+
+
+@pytest.mark.parametrize("order", [4, 12])
+def test_dd_symmetric_steps_parity_planets(mh, orc, order):
+    """Ten steps of a 7-body planetary system with the symmetric kernel forced
+    (one diagonal item: the ring distances 1 .. 16 of one subtile, 57 empty
+    lanes) against the binary128 oracle, at the tolerances of the ordered tests."""
+    m, x, v, pmin = _planets()
+    dt = pmin / 64
+    xr, vr, dr = orc.dd_run(order, m, x, v, 0.0, dt, 3, 10)
+    with mh.DDSimulation(order, m, x, v, 0.0, symmetric=2) as sim:
+        sim.step(dt, 3, nsteps=10)
+        _, x2, v2, d2 = sim.sync()
+    assert _rel(x2, xr) < 1e-27, _rel(x2, xr)
+    assert _rel(v2, vr) < 1e-27, _rel(v2, vr)
+    assert dd_scaled_stack_err(d2, dr, dt) < 1e-25
+
+
+def test_dd_symmetric_steps_parity_ragged(mh, orc):
+    """The 133-body softened ring of test_dd_ragged_multi_chunk with the
+    symmetric kernel forced: three blocks of 64 bodies (three diagonal items and
+    three at distance 1, the third block ragged with 5 bodies), two steps of n = 3."""
+    m, x, v = I.planetesimal_ring(seed=9, n=132, m=1e-7)
+    dt = 2 * np.pi / 256
+    xr, vr, dr = orc.dd_run(8, m, x, v, 1e-3, dt, 3, 2)
+    with mh.DDSimulation(8, m, x, v, 1e-3, symmetric=2) as sim:
+        sim.step(dt, 3, nsteps=2)
+        _, x2, v2, d2 = sim.sync()
+    assert _rel(x2, xr) < 1e-27, _rel(x2, xr)
+    assert _rel(v2, vr) < 1e-27, _rel(v2, vr)
+    assert dd_scaled_stack_err(d2, dr, dt) < 1e-25

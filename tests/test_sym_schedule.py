@@ -51,3 +51,19 @@ def test_schedule_check_rejects_bad_arguments():
         mh.sym_schedule_check(100, 0)
     with pytest.raises(mh.MHError):
         mh.sym_schedule_check(100, 10, 7)
+
+
+@pytest.mark.parametrize("N", [1, 2, 127, 128, 129, 255, 256, 257, 300, 383, 384, 385, 1000, 2047, 2048,
+                               2100, 2176, 2177, 2500, 4095, 4096, 4097, 9999, 30000])
+def test_dd_symmetric_work_map(N):
+    """The symmetric double-double kernel (one item per unordered pair of
+    64-body blocks, its diagonal block included): every block pair is one
+    item, each of the nB partial-sum slots gets every block once, for odd
+    and even block counts and a ragged last block, and the kernel's own ring
+    schedule takes every body pair inside an item once (the diagonal item's
+    unordered pairs once, no self pair)."""
+    r = mh.dd_sym_check(N)
+    nB = -(-N // 64)
+    assert r["blocks"] == nB
+    assert r["items"] == nB * (nB + 1) // 2
+    assert r["bad_pairs"] == 0 and r["bad_slots"] == 0 and r["bad_body_pairs"] == 0
