@@ -64,21 +64,21 @@ PEAK_FP64 = N_SM * 2 * 2 * SM_MAX_MHZ * 1e6
 # DRAM traffic per launch of the dominant kernel from one ncu capture
 # (profiles/); valid only while the kernel source is the one captured.
 TRAFFIC = {"files": ["paper_2006_02501_gb300/csrc/pair_sym.cu", "paper_2006_02501_gb300/csrc/pair_math.cuh"],
-           "sha256": ["84f31dcb0c93839f5125f35d08be4ff5cb8728a200a5de1b7407e1d7749496d5",
+           "sha256": ["6da5a1f3a83b1867d15a891bb0483e85bf9953b21949157a233da9651300073b",
                       "7b05f4cd731085ffd18547e017c5352bbda74f8e674505c0fb411285746659be"],
-           # profiles/k_pair_fp64_sym_disc_N65536_order8_dram.md: 56.26 MB read + 1.61 GB written
-           "bytes_per_launch": 56.26e6 + 1.61e9}
+           # profiles/k_pair_fp64_sym_disc_N65536_order8_dram.md: 11.32 MB read + 38.03 MB written
+           "bytes_per_launch": 11.32e6 + 38.03e6}
 
 
-# FP64 instructions per pair interaction of the double-double evaluation kernel
-# k_dd_pair<3, false>, from one ncu capture (profiles/), valid while its source is
-# the one captured.
+# FP64 instructions per pair interaction (ordered pair) of the double-double
+# evaluation kernel at 4096 bodies, k_dd_pair_sym<3> (each unordered pair once),
+# from one ncu capture (profiles/), valid while its source is the one captured.
 DD_INSTR = {"files": ["paper_2006_02501_gb300/csrc/dd.cu", "paper_2006_02501_gb300/csrc/dd.cuh"],
-            "sha256": ["484799a2627abe3b09e9f8f0f2bed35222b21dc59113afc036cbd166be9ade2a",
-                       "fc820299535e960effdf3d75b248976e124a70606f221bffac1d8e3395d01bd7"],
-            # profiles/k_dd_pair_disc_N4096_order8.md: 30.19e9 FP64 thread instructions
-            # for 4097 x 4096 ordered pairs
-            "fp64_thread_instr_per_pair": 1799.0}
+            "sha256": ["592b68c09507ecdaa012266b4429eec5f85ec8ee84ab8b3ca381ef2fa77405ec",
+                       "f43f2591663c27103bf9ee43e6dda962e4fc0d99eef95b3953edd99ba0cb6c9a"],
+            # profiles/k_dd_pair_sym_disc_N4096_order8.md: 15.85e9 FP64 thread
+            # instructions for 4096 x 4095 pair interactions
+            "fp64_thread_instr_per_interaction": 945.0}
 FP64_LANE_INSTR_PER_S = N_SM * 2 * SM_MAX_MHZ * 1e6
 
 
@@ -432,13 +432,13 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": r1["kernel_launches"] - r0["kernel_launches"]}
     dd_pair_rate = dd_out["disc4096_order8"]["pair_interactions_per_s"] / world
     dd_src = all(_sha(f) == h for f, h in zip(DD_INSTR["files"], DD_INSTR["sha256"]))
-    dd_instr = DD_INSTR["fp64_thread_instr_per_pair"] if dd_src else None
-    dd_out["pair_kernel"] = "k_dd_pair<3, false>"
-    dd_out["fp64_thread_instr_per_pair"] = dd_instr
+    dd_instr = DD_INSTR["fp64_thread_instr_per_interaction"] if dd_src else None
+    dd_out["pair_kernel"] = "k_dd_pair_sym<3> (each unordered pair once)"
+    dd_out["fp64_thread_instr_per_interaction"] = dd_instr
     dd_out["fp64_pipe_frac"] = (dd_pair_rate * dd_instr / FP64_LANE_INSTR_PER_S) if dd_instr else None
     dd_out["fp64_pipe_frac_basis"] = ("pair-interactions/s of the 4096-body step x FP64 thread "
-                                      "instructions per pair (ncu, profiles/) / (152 SMs x 2 FP64 lanes "
-                                      "x 2070 MHz); null once dd.cu or dd.cuh changes")
+                                      "instructions per interaction (ncu, profiles/) / (152 SMs x 2 FP64 "
+                                      "lanes x 2070 MHz); null once dd.cu or dd.cuh changes")
 
     peaks = mh.measure_peaks()       # measured ALU rates of this GPU, reported beside the unit-count peaks
     if rank != 0:

@@ -119,9 +119,13 @@ def test_learned_predictor_gain(mh):
     then on a fresh ring compare with the plain Taylor predictor: the worst
     body's predicted x and v errors (against a converged step), the error after
     one evaluate-correct pass, and the passes to a 1e-13 convergence tolerance.
-    The P(EC)^n iteration contracts by about 1e3 per pass here, so a predictor
-    that is a few times better shortens the first pass but does not remove one
-    at 1e-13; the test records that and guards against any regression."""
+
+    The gain claimed is the prediction's: x and v errors at least 2x lower
+    (measured 2.7x and 3.5x), and a lower error after the first pass (1.14x).
+    No pass is saved: the P(EC)^n iteration contracts by about 1e3 per pass
+    here, so a predictor a few times better does not remove one at 1e-13
+    (measured 4.05 passes per step with either predictor).  The pass count is
+    held to no loss beyond one pass in the 20 steps."""
     from paper_2006_02501_gb300 import train_predictor as tp
     eps, dt, tol = 1e-6, 0.15, 1e-13
     ring = lambda seed: I.planetesimal_ring(seed=seed, n=4000, m=1e-12, a_lo=0.7, a_hi=1.2, sigma_e=0.05,
@@ -158,5 +162,5 @@ def test_learned_predictor_gain(mh):
         _, xa, _, _ = a.sync()
         _, xb, _, _ = b.sync()
     print("passes to 1e-13: plain", np.mean(plain), "learned", np.mean(learned))
-    assert np.mean(learned) <= np.mean(plain) + 0.25
+    assert np.mean(learned) <= np.mean(plain) + 0.05
     assert np.abs(xa - xb).max() < 1e-11                     # both converge to the same solution
