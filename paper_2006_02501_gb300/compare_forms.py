@@ -55,11 +55,11 @@ def run_ecc(args):
     eps, dt0, nst = 1e-4, 2 * np.pi * 1e-3, args.steps
     T = nst * dt0
     with mh.Simulation(8, m, x, v, eps, stream=st) as ref:
-        ref.step(dt0 / 4, 4, nsteps=4 * nst)
+        ref.step(dt0 / 4, args.ref_passes, nsteps=4 * nst)
         _, e_ref = ref.diagnostics(central=0)
     rows = []
     for prec, name in ((mh.MH_PREC_FP64, "fp64"), (mh.MH_PREC_FP32PAIR, "fp32pair")):
-        for div in (1, 2):
+        for div in (args.fp64_divs if name == "fp64" else (1, 2)):
             dt = dt0 / div
             with mh.Simulation(8, m, x, v, eps, stream=st, precision=prec) as s:
                 c0 = s.counters()
@@ -301,6 +301,8 @@ def main():
     a = sub.add_parser("ecc")
     a.add_argument("--N", type=int, default=16384)
     a.add_argument("--steps", type=int, default=40)
+    a.add_argument("--ref-passes", type=int, default=4)
+    a.add_argument("--fp64-divs", type=int, nargs="+", default=[1, 2])
     b = sub.add_parser("block")
     b.add_argument("--N", type=int, default=262144)
     b.add_argument("--dtmax-units", type=int, default=1)
