@@ -276,14 +276,24 @@ k_dd_pair(const double2 *__restrict__ tr, const double *__restrict__ m, int N, d
 }
 
 // Many independent systems (batched form): CTA s holds system s (at most
-// kDDSysMax bodies, records off[s] .. off[s+1]-1) in shared memory; thread t
-// sums body off[s] + t over the system, into a single partial-sum slot.
+// kDDSysMax bodies, records off[s] .. off[s+1]-1) in shared memory; warp w
+// sums bodies 32 w .. 32 w + m - 1 of the system (m <= 32) over the whole
+// system, into a single partial-sum slot.  Where m leaves lanes idle (systems
+// below 32 bodies, or the second warp of one with 33 .. 64), each body gets a
+// group of g lanes (g the largest power of two with g m <= 32): lane l takes
+// body l / g over the sources j = l mod g, l mod g + g, ..., and the g partial
+// sums meet in a fixed xor-shuffle tree of double-word additions.  A warp
+// instruction costs the FP64 pipe the same with 3 lanes live as with 32, so
+// the groups cut the pair iterations of a system of m < 32 bodies per warp by
+// g, for log2(g) tree levels; each body's summation order depends on the
+// system alone.
 template <int P, bool kTop2>
 __global__ void __launch_bounds__(kDDSysMax)
 k_dd_pair_sys(const double2 *__restrict__ tr, const double *__restrict__ m, const int64_t *__restrict__ off,
               double eps, double G, double2 *__restrict__ part)
 {
     constexpr int R = (P + 1) * 3;
+    constexpr int NA = kTop2 ? 2 : P + 1;
     __shared__ double2 sj[kDDSysMax * R];
     __shared__ double sm[kDDSysMax];
     const int64_t b0 = off[blockIdx.x];
@@ -291,16 +301,37 @@ k_dd_pair_sys(const double2 *__restrict__ tr, const double *__restrict__ m, cons
     for (int q = threadIdx.x; q < n * R; q += kDDSysMax) sj[q] = tr[(size_t)b0 * R + q];
     for (int q = threadIdx.x; q < n; q += kDDSysMax) sm[q] = m[b0 + q];
     __syncthreads();
-    const int t = threadIdx.x;
-    if (t >= n) return;
+    const int lane = threadIdx.x & 31, base = threadIdx.x & ~31;
+    if (base >= n) return;                          // the whole warp
+    const int mb = min(32, n - base);
+    int g = 1;
+    while (2 * g * mb <= 32) g *= 2;
+    const int k0 = lane / g, sub = lane - k0 * g;
+    const int i = base + (k0 < mb ? k0 : 0);        // lanes past the groups repeat body base
     const dd eps2 = two_prod(eps, eps);
-    dd acc[kTop2 ? 2 : P + 1][3];
+    dd acc[NA][3];
 #pragma unroll
-    for (int k = 0; k < (kTop2 ? 2 : P + 1); ++k)
+    for (int k = 0; k < NA; ++k)
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[k][c] = dd(0.0);
-    dd_pair_sum<P, kTop2>(sj, sm, n, t, sj + t * R, eps2, G, acc);
-    dd_store_sums<P, kTop2>(part + (size_t)(b0 + t) * R, acc);
+    const double2 *ti = sj + i * R;
+    for (int j = sub; j < n; j += g) {
+        if (j == i) continue;
+        if constexpr (kTop2)
+            dd_pair_top2<P>(sj + j * R, ti, sm[j], eps2, G, acc);
+        else
+            dd_pair_full<P>(sj + j * R, ti, sm[j], eps2, G, acc);
+    }
+    for (int o = 1; o < g; o *= 2)
+#pragma unroll
+        for (int k = 0; k < NA; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double h = __shfl_xor_sync(0xffffffffu, acc[k][c].hi, o);
+                const double l = __shfl_xor_sync(0xffffffffu, acc[k][c].lo, o);
+                acc[k][c] = acc[k][c] + dd(h, l);
+            }
+    if (sub == 0 && k0 < mb) dd_store_sums<P, kTop2>(part + (size_t)(b0 + i) * R, acc);
 }
 
 // ---- pair-symmetric evaluation ----
