@@ -105,7 +105,11 @@ typedef struct {
                            slots of (P+1)*3*Np doubles (C row chunks, G = 1 accumulation
                            chain; Np = N padded to 256), 14 slots (88 MB) at N = 65536
                            and order 8, in an order fixed per slot, so its results are
-                           bit-reproducible; block steps use the ordered kernel. */
+                           bit-reproducible.  Block steps: 1 evaluates all bodies this way
+                           (and gathers the active bodies' sums) in the block steps with at
+                           least half the bodies due, 2 in every block step, 0 never; the
+                           other block steps evaluate the active list with the ordered
+                           kernels. */
     int fp32_variant;   /* precision form, ordered-pair evaluation kernel: 0 (default) =
                            chosen per size class by timing each once (autotuner), or
                            fixed: 1 = one i-body per thread, 2 = two, 3 = two in packed

@@ -668,6 +668,53 @@ void mh_destroy(mh_sim *sim)
     delete sim;
 }
 
+// Block steps with at least half the bodies due (or every block step with
+// symmetric = 2): the pair-symmetric kernel evaluates all N bodies in N^2/2
+// pair evaluations, against n_act N ordered ones for the active list alone.
+static bool block_use_sym(const mh_sim *sim, int64_t n_act)
+{
+    const mh_config &c = sim->cfg;
+    const DeviceState &s = sim->s;
+    if (c.symmetric == 0 || (c.precision == MH_PREC_FP32PAIR && c.fp32_variant != 0)) return false;
+    if (c.symmetric == 1 && (s.Np < kSymMinNp || 2 * n_act < s.N)) return false;
+    return plan_sym(s.p, s.Np, sim->device, c.precision == MH_PREC_FP32PAIR).nB > 0;
+}
+
+// The n_iter evaluate-correct passes of one block step through the shared-step
+// evaluation of all bodies (slots by body index), the active bodies' sums
+// gathered in slot order into one compact slot after them, and the block
+// corrector on that slot.
+static int block_passes_sym(mh_sim *sim, long long T_next, int64_t n_act, int64_t part_ld, int n_iter)
+{
+    DeviceState &s = sim->s;
+    const mh_config &c = sim->cfg;
+    const int nr = (s.p + 1) * 3;
+    const SymPlan sp = plan_sym(s.p, s.Np, sim->device, c.precision == MH_PREC_FP32PAIR);
+    const size_t sym_doubles = (size_t)(sp.slots + 1) * nr * s.Np;     // + the heavy bodies' slot
+    if (int rc = ensure_part(s, sym_doubles + (size_t)nr * part_ld, sim->stream)) return rc;
+    for (int it = 0; it < n_iter; ++it) {
+        int split = 0;
+        if (int rc = evaluate(sim, s.p, c.precision, &split)) return rc;
+        const size_t off = (size_t)split * nr * s.Np;
+        if (off + (size_t)nr * part_ld > s.part_doubles) {
+            set_error("mh_step: block step partial sums exceed their buffer");
+            return MH_EINVAL;
+        }
+        if (int rc = launch_gather_active(n_act, s.Np, nr, split, s.part, s.act, part_ld, s.part + off,
+                                          sim->stream))
+            return rc;
+        DeviceState sa = s;
+        sa.part = s.part + off;
+        const bool last = it == n_iter - 1;
+        if (int rc = launch_block_phase(sa, c, T_next, n_act, 1, last, 1, sim->stream, part_ld)) return rc;
+        if (!last) s.flip ^= 1;
+        sim->ctr.kernel_launches += 3;
+        // count the active bodies' interactions, as the ordered path does
+        sim->ctr.pair_interactions += ((double)n_act - (double)s.N) * (double)(s.N - 1);
+    }
+    return MH_OK;
+}
+
 static int block_advance(mh_sim *sim, double dt, int n_iter)
 {
     DeviceState &s = sim->s;
@@ -702,6 +749,14 @@ static int block_advance(mh_sim *sim, double dt, int n_iter)
         sim->ctr.pair_variant = ipt;
         // partial sums by active position, rows of the padded active count
         const int64_t part_ld = pad_to(n_act, 32);
+        if (block_use_sym(sim, n_act)) {
+            // every unordered pair once for all bodies, then the active bodies' sums
+            if (int rc = block_passes_sym(sim, T_next, n_act, part_ld, n_iter)) return rc;
+            sim->ctr.particle_steps += (double)n_act;
+            s.T_now = T_next;
+            if (T_next == target) break;
+            continue;
+        }
         // a few bodies due: one warp per (body, j-chunk) over all the sources
         const bool short_list = n_act <= kShortActive && c.split_j == 0;
         for (int it = 0; it < n_iter; ++it) {

@@ -216,6 +216,8 @@ int launch_reduce_slots(const DeviceState &s, int nr, int split, cudaStream_t st
 // Slot 0 of part (n positions, rows nr of stride ld) <- sum of its first `split`
 // slots, one warp per (row, position), in a fixed order.
 int launch_reduce_slots_warp(int64_t n, int64_t ld, int nr, int split, double *part, cudaStream_t st);
+int launch_gather_active(int64_t n_act, int64_t Np, int nr, int split, const double *part, const int *act,
+                         int64_t ld_out, double *out, cudaStream_t st);
 int launch_reduce_out(int64_t n, int64_t ld_part, int nr, int split, const double *part, double *out,
                       cudaStream_t st);
 int launch_split32(int64_t N, int P, const double *traj, const double *m, double G, float *rows,

@@ -675,6 +675,23 @@ __global__ void k_reduce_slots_warp(int64_t n, int64_t ld, int nr, int split, do
     if (lane == 0) part[(int64_t)r * ld + i] = s;
 }
 
+// Block step evaluated for all bodies (slots by body index, rows of Np): the
+// active bodies' sums, out[r][a] = sum over the slots q, in slot order, of
+// part[q][r][act[a]], rows of ld_out (the active count padded), one thread per
+// (row, active body).
+__global__ void k_gather_active(int64_t n_act, int64_t Np, int nr, int split, const double *__restrict__ part,
+                                const int *__restrict__ act, int64_t ld_out, double *__restrict__ out)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nr * n_act) return;
+    const int r = (int)(t / n_act);
+    const int64_t a = t - (int64_t)r * n_act;
+    const int64_t i = act[a];
+    double s = 0.0;
+    for (int q = 0; q < split; ++q) s += part[((int64_t)q * nr + r) * Np + i];
+    out[(int64_t)r * ld_out + a] = s;
+}
+
 // d0 rows [lo, hi) <- sum over S partial slots of rows [lo, hi) (slot row count nr).
 __global__ void k_init_reduce(int64_t N, int64_t ld, int nr, int lo, int hi, int split,
                               const double *part, double *d0)
@@ -900,6 +917,15 @@ int launch_reduce_slots(const DeviceState &s, int nr, int split, cudaStream_t st
     const int64_t n = (int64_t)nr * s.N;
     k_reduce_slots<<<blocks_for(n, 32), 32, 0, st>>>(s.N, s.Np, nr, split, s.part);
     MH_LAUNCHED("k_reduce_slots");
+    return MH_OK;
+}
+
+int launch_gather_active(int64_t n_act, int64_t Np, int nr, int split, const double *part, const int *act,
+                         int64_t ld_out, double *out, cudaStream_t st)
+{
+    const int64_t n = (int64_t)nr * n_act;
+    k_gather_active<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n_act, Np, nr, split, part, act, ld_out, out);
+    MH_LAUNCHED("k_gather_active");
     return MH_OK;
 }
 

@@ -44,13 +44,18 @@ def test_block_levels_at_creation(mh, orc, order):
     assert len(set(lv.tolist())) >= 3
 
 
+@pytest.mark.parametrize("symmetric", [1, 2])
 @pytest.mark.parametrize("order", [6, 8])
-def test_block_step_parity_fp64(mh, orc, order):
+def test_block_step_parity_fp64(mh, orc, order, symmetric):
+    """Two dt_max of block steps against the oracle from the same start.
+    symmetric = 2 sends every block step through the pair-symmetric evaluation
+    of all bodies and the gather of the active bodies' sums (at 700 bodies the
+    default takes the active-list kernels)."""
     m, x, v = I.smbh_disc(seed=32, N=700)
     blk = dict(dt_max=2.0 ** -5, k_max=10, eta=0.05)
     eps = 1e-4
     B = orc.BlockState(order, m, x, v, eps, blk["dt_max"], blk["k_max"], blk["eta"])
-    with mh.Simulation(order, m, x, v, eps, block=blk) as sim:
+    with mh.Simulation(order, m, x, v, eps, block=blk, symmetric=symmetric) as sim:
         sim.set_state(x, v, B.derivs, level=B.level)         # identical start
         B.advance(2 * blk["dt_max"], 3)
         sim.step(2 * blk["dt_max"], 3)
@@ -75,13 +80,15 @@ def fp32_block_case(orc):
     return m, x, v, blk, eps, start, B
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2, 3, 0])
 def test_block_step_fp32_precision_form(mh, orc, fp32_block_case, variant):
     """Precision form with block steps: accelerations within 2e-6 of the oracle
     after two dt_max of block steps from the same start, for each evaluation
-    kernel (one i-body per thread, two, two in packed FP32x2 lanes)."""
+    kernel (one i-body per thread, two, two in packed FP32x2 lanes; 0: the
+    pair-symmetric kernel for every block step, symmetric = 2)."""
     m, x, v, blk, eps, (d_start, lv_start), B = fp32_block_case
-    with mh.Simulation(8, m, x, v, eps, block=blk, precision=mh.MH_PREC_FP32PAIR, fp32_variant=variant) as sim:
+    with mh.Simulation(8, m, x, v, eps, block=blk, precision=mh.MH_PREC_FP32PAIR, fp32_variant=variant,
+                       symmetric=2 if variant == 0 else 1) as sim:
         sim.set_state(x, v, d_start, level=lv_start)
         E0 = sim.energy()
         sim.step(2 * blk["dt_max"], 3)
@@ -114,6 +121,35 @@ def test_block_fp32_energy_with_comparable_masses(mh, order):
             dE[prec] = sim.energy() / E0 - 1
     assert abs(dE[mh.MH_PREC_FP64]) > 1e-13                  # a resolved, non-trivial energy error
     assert abs(dE[mh.MH_PREC_FP32PAIR] - dE[mh.MH_PREC_FP64]) < 1e-9
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_block_symmetric_large_steps_match_active_list(mh, precision):
+    """The block-step workload's disc cut to 4096 stars of comparable mass,
+    two dt_max: by default the block steps with at least half the bodies due
+    take the pair-symmetric evaluation of all bodies (the others the
+    active-list kernels); with symmetric = 0 every step takes the active-list
+    kernels.  Levels agree, FP64 states to 1e-12 (two summation orders of the
+    same sums), precision-form states to 1e-9 (FP32 sums over different
+    tiles), each row against the larger of its own size and 1e-3 of the
+    disc's (the SMBH sits 5e-5 from the origin, its position the sum of
+    cancelling pulls); the counters count the same particle steps and pair
+    interactions."""
+    m, x, v = I.smbh_disc(seed=3, N=4096)
+    blk = dict(dt_max=2.0 ** -5, k_max=12, eta=0.05)
+    out = {}
+    for sym in (1, 0):
+        with mh.Simulation(8, m, x, v, 1e-4, precision=precision, block=blk, symmetric=sym) as sim:
+            sim.step(2 * blk["dt_max"], 3)
+            out[sym] = (sim.sync(), sim.levels(), sim.counters())
+    (_, x1, v1, _), lv1, c1 = out[1]
+    (_, x0, v0, _), lv0, c0 = out[0]
+    assert np.array_equal(lv1, lv0)
+    assert c1["particle_steps"] == c0["particle_steps"]
+    assert c1["pair_interactions"] == c0["pair_interactions"]
+    tol = 1e-12 if precision == 0 else 1e-9
+    assert rel_rows(x1, x0, 1e-3) < tol
+    assert rel_rows(v1, v0, 1e-3) < 10 * tol
 
 
 def test_block_mode_rejects_bad_dt(mh):
