@@ -103,7 +103,17 @@ def run_block(args):
                 lv = s.levels()
                 E0 = s.energy()
                 c0 = s.counters()
-                sec = _timed(torch, st, lambda: s.step(span, 3))
+                if args.chunk_dtmax > 0:
+                    # progress lines every chunk_dtmax x dt_max (long runs)
+                    sec, done = 0.0, 0
+                    while done < args.dtmax_units:
+                        k = min(args.chunk_dtmax, args.dtmax_units - done)
+                        sec += _timed(torch, st, lambda: s.step(k * blk["dt_max"], 3))
+                        done += k
+                        print(json.dumps({"progress": name, "order": order, "dtmax_done": done, "seconds": sec,
+                                          "dE_rel": s.energy() / E0 - 1}), flush=True)
+                else:
+                    sec = _timed(torch, st, lambda: s.step(span, 3))
                 c1 = s.counters()
                 E1, e = s.diagnostics(central=0)
             out[name] = {"time_s": sec, "particle_steps": c1["particle_steps"] - c0["particle_steps"],
@@ -306,6 +316,7 @@ def main():
     b = sub.add_parser("block")
     b.add_argument("--N", type=int, default=262144)
     b.add_argument("--dtmax-units", type=int, default=1)
+    b.add_argument("--chunk-dtmax", type=int, default=0)
     b.add_argument("--orders", type=int, nargs="+", default=[8, 6])
     b.add_argument("--forms", nargs="+", default=["fp32pair", "fp64"], choices=["fp32pair", "fp64"])
     c = sub.add_parser("batch")
