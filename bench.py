@@ -74,7 +74,7 @@ TRAFFIC = {"files": ["paper_2006_02501_gb300/csrc/pair_sym.cu", "paper_2006_0250
 # evaluation kernel at 4096 bodies, k_dd_pair_sym<3> (each unordered pair once),
 # from one ncu capture (profiles/), valid while its source is the one captured.
 DD_INSTR = {"files": ["paper_2006_02501_gb300/csrc/dd.cu", "paper_2006_02501_gb300/csrc/dd.cuh"],
-            "sha256": ["4dc44733c8df3b55879c9503fc475347c1590d505a50023bcb36156f81cbc798",
+            "sha256": ["35a3a503fc226f03d335d5dbb94d40af14ca79471c0ad7aec442c2df68240110",
                        "f43f2591663c27103bf9ee43e6dda962e4fc0d99eef95b3953edd99ba0cb6c9a"],
             # profiles/k_dd_pair_sym_disc_N4096_order8.md: 15.85e9 FP64 thread
             # instructions for 4096 x 4095 pair interactions

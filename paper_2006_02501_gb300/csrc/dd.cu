@@ -15,9 +15,13 @@
 // Layout in device memory (each double-double is a double2 {hi, lo}):
 //   x, v   N x 3          d   N x 2p x 3 (a^(0..2p-1))
 //   tr     N x (P+1) x 3  trajectory fed to an evaluation (x, v, a, a-dot, ...)
-//   part   S x N x (P+1) x 3  per-j-chunk partial sums, added by the consumer in
-//                         chunk order, so results do not depend on scheduling.
+//   part   S x N x (P+1) x 3  per-j-chunk (or per-distance) partial sums, added
+//                         by the consumer in slot order, so results do not
+//                         depend on scheduling.
 // Kernels:
+//   k_dd_pair_sym<P>  from 2048 bodies up: each unordered pair of bodies once,
+//                     both bodies' terms from one evaluation, items of two
+//                     64-body blocks, one partial-sum slot per (distance, side).
 //   k_dd_pair<P, false>  one i per thread over one j-chunk, j records staged
 //                     in shared memory; FP64-pipe bound (double-double costs
 //                     about 20 FP64 operations per FP64 operation of the plain
