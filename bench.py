@@ -64,7 +64,7 @@ PEAK_FP64 = N_SM * 2 * 2 * SM_MAX_MHZ * 1e6
 # DRAM traffic per launch of the dominant kernel from one ncu capture
 # (profiles/); valid only while the kernel source is the one captured.
 TRAFFIC = {"files": ["paper_2006_02501_gb300/csrc/pair_sym.cu", "paper_2006_02501_gb300/csrc/pair_math.cuh"],
-           "sha256": ["6da5a1f3a83b1867d15a891bb0483e85bf9953b21949157a233da9651300073b",
+           "sha256": ["9bb18f03603bf070ab67a7690021637658f34ee289fa7f8943c02ba8300861e2",
                       "7b05f4cd731085ffd18547e017c5352bbda74f8e674505c0fb411285746659be"],
            # profiles/k_pair_fp64_sym_disc_N65536_order8_dram.md: 11.32 MB read + 38.03 MB written
            "bytes_per_launch": 11.32e6 + 38.03e6}

@@ -202,8 +202,9 @@ int mh_step(mh_sim *sim, double dt, int n_iter);
  * converged step is symmetric in time.  The prediction uses dt = H-; the next
  * step's H- is H+ of this step's last evaluation (at creation and after
  * mh_set_state, Eq. 24 at the given positions).  Advances nsteps steps; dt and
- * the time stay on the device (mh_sync reports t).  Needs the pair-symmetric
- * FP64 evaluation (its partial sums within 8 GiB); 1 <= n_iter <= 64. */
+ * the time stay on the device (mh_sync reports t).  The Eq. 24 minimum is taken
+ * inside the FP64 evaluation kernels (pair-symmetric or ordered pairs);
+ * 1 <= n_iter <= 64. */
 int mh_step_timesym(mh_sim *sim, int64_t nsteps, int n_iter, int backward);
 
 /* Copy the current state to host buffers (waits for queued work). */

@@ -895,9 +895,9 @@ int launch_sym32(const SymPlan &pl, const SymSync &sy, const float *jrec32, int6
 // at once (distance order); otherwise the CTAs take items in row order, and rows
 // at the end of a launch that is only just above one wave wait for the first
 // rows (their blocks near the wrap-around come last in that order): count one
-// wave more.  FP64: one row per item (4 warps), 4 chains.  FP32-pair: K rows per
-// item (K = kmax or 4, whichever wastes less of the last wave; a CTA sweeps K
-// blocks per step), one chain.
+// wave more.  FP64: K = sym64_rows rows per item (4 warps each), one chain.
+// FP32-pair: K rows per item (K = kmax or 4, whichever wastes less of the last
+// wave; a CTA sweeps K blocks per step), one chain.
 SymPlan plan_sym_slots(int64_t ld, int slots, bool fp32, int kmax)
 {
     SymPlan pl{};
